@@ -1,0 +1,282 @@
+"""Benchmark of the MHD + H/H2 chemistry time step (arXiv:1608.08748) on GB300.
+
+Workload (one "step" = one full time step of the method over the whole box):
+  decaying supersonic MHD turbulence with hydrogen chemistry, 128^3 periodic cells, FP64,
+  n = 100 cm^-3, T = 100 K, rms Mach 5, beta 1, seed 1, CFL 0.4 (synthetic initial state).
+Metric: Mcell-updates/s = cells x steps / device time of the timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank advances its own box (independent replicas, no collective on the
+data path) and the line reports the sum over ranks with the slowest rank's time.
+`--impl reference` times the FP64 CPU oracle (the plain implementation the tests check against) on
+the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CFL = 0.4
+N_GRID = 128
+WORKLOAD = "mhd_turbulence_h2chem_128^3_fp64"
+METRIC = "Mcell-updates/s"
+# FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# algorithmic FP64 flops of one Eulerian face solve (counted from the kernel source: PPM of 6
+# variables for 2 cells, Roe average, eigenvectors, 36 parabola averages, L q, R s, fluxes;
+# add/sub/mul/div/sqrt one flop each, compares not counted)
+FLOPS_PER_EULER_FACE = 1248
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def sample_clocks(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return
+    def reader():
+        for line in p.stdout:
+            out.append(line.strip())
+    th = threading.Thread(target=reader, daemon=True)
+    th.start()
+    stop.wait()
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    th.join(timeout=5)
+
+
+def summarize_clocks(lines, gpu_index):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9 or f[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def oracle_rate(n, steps, warm=1):
+    """Oracle Mcell-updates/s on an n^3 box of the same turbulence set-up; returns (rate, cores)."""
+    from oracle import oracle as O
+    from paper_1608_08748_gb300 import inputs as I
+    ic = I.turbulence(n, mach=5.0, beta=1.0, seed=1)
+    s = O.run(ic)
+    for _ in range(warm):
+        s.step(CFL)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.step(CFL)
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return n ** 3 * steps / dt / 1e6, cores, dt
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1608_08748_gb300 import inputs as I
+    n = 64  # bounded sample of the 128^3 workload: same set-up on a 64^3 box
+    ic = I.turbulence(n, mach=5.0, beta=1.0, seed=1)
+    s = O.run(ic)
+    for _ in range(args.warmup):
+        s.step(CFL)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(CFL)
+    dt = time.perf_counter() - t0
+    value = n ** 3 * args.steps / dt / 1e6
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3, "cfl": CFL,
+                                        "sample": f"{n}^3 box of the same set-up"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                         "sample": f"{n}^3 turbulence box, {args.steps} steps after {args.warmup} warm-up"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1608_08748_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    import paper_1608_08748_gb300 as M
+    from paper_1608_08748_gb300 import inputs as I
+
+    ic = I.turbulence(N_GRID, mach=5.0, beta=1.0, seed=1 + rank)
+    cells = N_GRID ** 3
+    sim = M.from_ic(ic)
+    stream = torch.cuda.Stream()
+    sim.set_stream(stream.cuda_stream)
+    for _ in range(args.warmup):
+        sim.step(CFL, sync=False)
+    sim.sync()
+
+    stop = threading.Event()
+    clk = []
+    th = threading.Thread(target=sample_clocks, args=(stop, clk), daemon=True)
+    th.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim.step(CFL, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stop.set()
+    th.join(timeout=10)
+    sim.sync()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * cells * args.steps / (ms * 1e-3) / 1e6
+    launches = sim.L.mhd_launches_per_step(sim.h) * args.steps
+
+    # end to end through the C-ABI with host buffers: per step, upload the state from pinned host
+    # memory, one step, read the state back
+    host = {k: torch.empty((3,) + ic["rho"].shape if k in ("mom", "B") else ic["rho"].shape,
+                           dtype=torch.float64).pin_memory() for k in ["rho", "mom", "E", "B", "rho_h2"]}
+    st0 = sim.get_state()
+    for k in host:
+        host[k].copy_(torch.from_numpy(st0[k]))
+    hnp = {k: v.numpy() for k, v in host.items()}
+    e2e_steps = max(3, min(args.steps, 10))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_state(hnp["rho"], hnp["mom"], hnp["E"], hnp["B"], hnp["rho_h2"])
+        sim.step(CFL, sync=False)
+        sim.get_state(out=hnp)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    field_bytes = 9 * cells * 8
+    e2e = {"value": world * cells * e2e_steps / e2e_s / 1e6, "unit": METRIC,
+           "h2d_bytes_per_step": field_bytes, "d2h_bytes_per_step": field_bytes}
+
+    # per-kernel device times (event pairs around each launch, separate pass, same workload)
+    import ctypes
+    prof_steps = 4
+    kms = (ctypes.c_double * 8)()
+    kn = (ctypes.c_int64 * 8)()
+    sim.L.mhd_profile.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    rc = sim.L.mhd_profile(sim.h, CFL, prof_steps, kms, kn)
+    names = ["prim", "euler_face", "edges", "euler_update", "lag_face", "lag_update", "post", "small"]
+    kernels = {nm: {"ms_total": kms[c], "launches": int(kn[c])} for c, nm in enumerate(names)} if rc == 0 else {}
+    tot = sum(v["ms_total"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["ms_total"] / tot
+    roofline = None
+    if kernels:
+        faces_per_launch = (N_GRID + 1) * N_GRID * N_GRID
+        avg_launch_s = kernels["euler_face"]["ms_total"] / kernels["euler_face"]["launches"] * 1e-3
+        achieved = FLOPS_PER_EULER_FACE * faces_per_launch / avg_launch_s / 1e12
+        roofline = {"bound": "alu", "kernel": "k_euler_face (FP64)", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "traffic": None, "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, cores, secs = oracle_rate(48, 8)
+        cpu = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle",
+               "sample": f"48^3 box of the same turbulence set-up, 8 steps ({secs:.1f} s)"}
+    d = sim.diagnostics()
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3, "cfl": CFL, "chemistry": True,
+                   "l2": "inputs larger than L2 (about 0.9 GB of fields and scratch per box)",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": summarize_clocks(clk, local),
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "kernels": kernels,
+        "sim_time_after": d["t"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * mhd.h -- C ABI of libmhd.so, the GB300 (sm_103a) implementation of one time step of the MHD +
+ * H/H2 chemistry method of Kulikov, Chernykh & Protasov, "A new code for numerical simulation of
+ * MHD astrophysical flows with chemistry" (arXiv:1608.08748).
+ *
+ * One call of mhd_step() advances the state by one step of the operator-split scheme of Sec. 2:
+ *   tau from the CFL rule (Sec. 2.3) -> Eulerian stage, three SSP-RK3 substages (Sec. 2.2) of the
+ *   characteristic Riemann solver on piecewise-parabolic data (Sec. 2.1, 2.4, App. A) with Flux-CT
+ *   inside each substage (Sec. 2.5, App. C) -> Lagrangian advection stage, three SSP-RK3 substages
+ *   (Sec. 2.6) -> H/H2 chemistry (Sec. 2.7, App. D reactions 1-4) -> regularisation (Sec. 2.9).
+ * Every step runs in CUDA kernels of this library; there is no CPU path.
+ *
+ * Conventions
+ *   Grid: nx * ny * nz cells of width dx on every axis.  Fields are C-order arrays [k][j][i]
+ *   (x fastest), nx*ny*nz elements each.  Boundaries are periodic unless set to outflow
+ *   (zero-gradient) per axis with mhd_set_option.
+ *   Code units: the closure has no 4 pi (total pressure p + B^2/2, energy rho eps + rho v^2/2 +
+ *   B^2/2, Sec. 2).  With chemistry on, rho is in m_H cm^-3, lengths in pc, velocities in km/s.
+ *   Magnetic field: the library stores face-centred b_x(i-1/2,j,k), b_y(i,j-1/2,k),
+ *   b_z(i,j,k-1/2) (Sec. 2.5); cell-centred B is the mean of the two faces.
+ *   Ownership: the library allocates and owns all device memory of a simulation; buffers passed in
+ *   are only read or written during the call and never retained.
+ *   Errors: every int-returning call returns MHD_OK (0) or a negative MHD_E* code; mhd_last_error()
+ *   returns a message for the last failure on the calling thread.
+ *   Threading: one mhd_sim must not be used from two threads at once; distinct sims are
+ *   independent.  All work of a sim is issued on its CUDA stream (mhd_set_stream).
+ */
+#ifndef MHD_H
+#define MHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum mhd_status {
+  MHD_OK = 0,
+  MHD_PENDING = 1,       /* serving: request not finished yet */
+  MHD_EINVAL = -1,       /* bad argument or option */
+  MHD_ENOMEM = -2,       /* device allocation failed */
+  MHD_ECUDA = -3,        /* a CUDA call failed (message in mhd_last_error) */
+  MHD_ENONPHYS = -4,     /* rho <= 0, rho eps <= 0 or a non-finite value after a step (Sec. 2 closure);
+                            the state is left as the failing step produced it */
+  MHD_ETIMEOUT = -5,     /* a bounded wait gave up */
+  MHD_ENOTFOUND = -6,    /* serving: unknown request id */
+  MHD_ECAPACITY = -7     /* serving: request can never fit the memory budget */
+};
+
+enum mhd_option {
+  MHD_OPT_BC_X = 1,          /* 0 periodic (default), 1 outflow (zero-gradient ghost cells/faces) */
+  MHD_OPT_BC_Y = 2,
+  MHD_OPT_BC_Z = 3,
+  MHD_OPT_CHEM = 4,          /* 0 off (scalar gamma), 1 H/H2 network of App. D reactions 1-4 with
+                                gamma_eff = (5 n_H + 7 n_H2) / (3 n_H + 5 n_H2) (Sec. 4.3) */
+  MHD_OPT_PRECISION = 5,     /* 0 FP64 throughout (default); 1 FP32 bulk (reconstruction, fluxes,
+                                updates, state) with FP64 CFL reduction, chemistry and sums */
+  MHD_OPT_REGUL_MODE = 7,    /* Sec. 2.9: 0 rho eps := max(rho eps, rho E - rho v^2/2 - B^2/2) where
+                                the thermal fraction f >= 1e-3 (default); 1 unconditional overwrite;
+                                2 the sentence's literal branch order */
+  MHD_OPT_CHEM_LSHIELD = 8,  /* shielding length for column densities N = n L, code length units
+                                (0: one cell, the default) */
+  MHD_OPT_CHEM_BDOP = 9,     /* Doppler parameter b of f_shield in km/s (default 3) */
+  MHD_OPT_CHEM_XNORM = 10,   /* N_H2 normaliser of f_shield in cm^-2 (default 5e14) */
+  MHD_OPT_CHEM_TAUD = 11,    /* dust optical depth per unit column, cm^2 (default 1e-21) */
+  MHD_OPT_GRAPH = 14         /* 1 (default): replay each step from a captured CUDA graph; 0: launch */
+};
+
+enum mhd_dtype { MHD_F64 = 0, MHD_F32 = 1 };
+
+/* Field set for set/get.  All pointers host or all device (on_device), dtype MHD_F64 or MHD_F32.
+   mom and B are three arrays each (x, y, z); B is cell-centred.  rho_h2 may be NULL (then zero on
+   input, skipped on output). */
+typedef struct mhd_fields {
+  void* rho;
+  void* mom[3];
+  void* E;
+  void* B[3];
+  void* rho_h2;
+  int dtype;
+  int on_device;
+} mhd_fields;
+
+/* FP64 diagnostics (deterministic fixed-tree sums over all cells) */
+typedef struct mhd_diag {
+  double sum_rho, sum_mom[3], sum_E, sum_b[3]; /* sum_b over the stored faces */
+  double max_div_b_h;   /* max over cells of |sum_d (b_d(i_d + 1/2) - b_d(i_d - 1/2))| = h |div b| */
+  double t;             /* simulated time */
+  double tau_next;      /* tau / CFL of the current state: dx / max denominator (Sec. 2.3) */
+  int64_t steps;        /* steps taken since the last set_state */
+  int64_t vel_branch;   /* cells that took the velocity branch of the regularisation, cumulative */
+  int32_t error_flags;  /* bit 0: non-physical state seen by the last step's checks */
+} mhd_diag;
+
+typedef struct mhd_sim mhd_sim;
+
+/* Create a simulation of nx*ny*nz cells of width dx with adiabatic index gamma (used when
+   chemistry is off).  Allocates all device memory on the current CUDA device.  NULL on error. */
+mhd_sim* mhd_create(int nx, int ny, int nz, double gamma, double dx);
+void mhd_destroy(mhd_sim* s);
+const char* mhd_last_error(void);
+
+int mhd_set_option(mhd_sim* s, int key, double value);
+/* Issue all work on this cudaStream_t (default: a stream the library creates). */
+int mhd_set_stream(mhd_sim* s, void* cuda_stream);
+
+/* Load a cell-centred state (Sec. 2 closure).  Faces are built as the mean of the two
+   neighbouring cell values; rho eps = rho E - |m|^2 / (2 rho) - |B_cell(faces)|^2 / 2.
+   Resets t and the step counter and computes the first tau. */
+int mhd_set_state(mhd_sim* s, const mhd_fields* in);
+/* Load exact face values (e.g. a divergence-free field): b_d at face i_d - 1/2, float64, C order;
+   recomputes rho eps from rho E with the new field. */
+int mhd_set_face_B(mhd_sim* s, const double* bx, const double* by, const double* bz, int on_device);
+/* Copy the state out into caller buffers (B cell-centred). */
+int mhd_get_state(mhd_sim* s, mhd_fields* out);
+/* Full state for checkpoint/resume: rho eps and the face fields (float64). */
+int mhd_get_full(mhd_sim* s, double* eint, double* bx, double* by, double* bz, int on_device);
+int mhd_set_full(mhd_sim* s, const double* eint, const double* bx, const double* by,
+                 const double* bz, int on_device);
+
+/* One full step with tau = CFL-limited (Sec. 2.3).  dt_taken may be NULL: then the call only
+   enqueues work and does not synchronise (errors of the step surface at the next synchronising
+   call).  With dt_taken != NULL it waits for the step and reports MHD_ENONPHYS. */
+int mhd_step(mhd_sim* s, double cfl, double* dt_taken);
+/* Steps until t_end (the last step truncated to t_end) or max_steps. */
+int mhd_advance(mhd_sim* s, double cfl, double t_end, int max_steps, int* steps_done);
+/* Wait for all queued work of this sim; returns MHD_ENONPHYS if a step flagged it. */
+int mhd_sync(mhd_sim* s);
+int mhd_diagnostics(mhd_sim* s, mhd_diag* out);
+
+/* One stage alone with a given tau (per-stage parity checks): 1 Eulerian + Flux-CT, 2 Lagrangian,
+   3 chemistry, 4 regularisation. */
+int mhd_stage(mhd_sim* s, int which, double tau);
+
+/* Kernel classes reported by mhd_profile (index into its output arrays). */
+enum mhd_kernel_class {
+  MHD_K_PRIM = 0,        /* primitives of every cell (Eulerian substage) */
+  MHD_K_EULER_FACE = 1,  /* Eulerian face Riemann solve, all three directions */
+  MHD_K_EDGES = 2,       /* App. C edge EMFs */
+  MHD_K_EULER_UPDATE = 3,/* finite-volume + Flux-CT + RK update */
+  MHD_K_LAG_FACE = 4,    /* Lagrangian face fluxes, all three directions */
+  MHD_K_LAG_UPDATE = 5,  /* Lagrangian update */
+  MHD_K_POST = 6,        /* chemistry + regularisation + CFL of the new state */
+  MHD_K_SMALL = 7,       /* single-thread bookkeeping kernels and the RK register copies */
+  MHD_K_NCLASSES = 8
+};
+
+/* Run `steps` full steps launch by launch (no graph) with a CUDA event pair around every kernel on
+   the sim's stream; out_ms[c] = total milliseconds of class c over the steps, out_launches[c] = its
+   number of launches.  The steps advance the state like mhd_step.  Arrays have MHD_K_NCLASSES
+   entries. */
+int mhd_profile(mhd_sim* s, double cfl, int steps, double* out_ms, int64_t* out_launches);
+/* Number of kernel launches (not counting the copies of the RK register) in one mhd_step. */
+int mhd_launches_per_step(mhd_sim* s);
+
+/* Bytes of device memory one sim of this size uses (precision 0 FP64 / 1 FP32, chem 0/1). */
+size_t mhd_bytes_needed(int nx, int ny, int nz, int precision, int chem);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_H */

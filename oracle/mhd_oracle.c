@@ -41,7 +41,8 @@
  *       unconditional overwrite; the sentence's literal branch order).
  *   A15 H2 updated by the Sec. 2.7 formula with C = k1' n n_H, D = k2 n_H + k3 n_H2 + k4;
  *       n_H := n - 2 n_H2; column densities N_X = n_X L_shield.
- *   A16 outflow = zero-gradient copy of ghost cells and ghost faces; periodic otherwise.
+ *   A16 outflow = zero-gradient copy of ghost cells (their primitives, cell-centred B included)
+ *       and of ghost faces; periodic otherwise.
  *   A17 set_state builds faces as the mean of the two neighbouring cell-centred values.
  *   A18 tau = min(tau_CFL, t_end - t) when a target time is given.
  *   A19 code units: 1 pc, m_H cm^-3, 1 km/s.
@@ -557,14 +558,15 @@ int osim_get_full(osim* s, double* eint, double* bx, double* by, double* bz) {
 }
 
 /* ---------------------------------------------------------------- primitives on the ext. grid */
-/* requires valid ghosts of rho, m, eint, rh2 and b; fills w[] for every extended cell that has
-   its upper faces inside the extended grid */
+/* primitives of the interior cells (needs valid ghost faces for the cell-centred B), then the
+   ghost layers as zero-gradient / periodic copies of the cell-centred primitives (A16) */
 static void compute_primitives(osim* s) {
+  const int* n = s->n;
 #pragma omp parallel for schedule(static) num_threads(s->threads)
-  for (int ke = 0; ke < s->ne[2] - 1; ++ke)
-    for (int je = 0; je < s->ne[1] - 1; ++je)
-      for (int ie = 0; ie < s->ne[0] - 1; ++ie) {
-        size_t c = IX(s, ie, je, ke);
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        size_t c = IX(s, i + NG, j + NG, k + NG);
         double r = s->rho[c];
         double B[3];
         cell_B(s, c, B);
@@ -579,6 +581,7 @@ static void compute_primitives(osim* s) {
         s->w[7][c] = (g - 1.0) * s->eint[c];
         s->w[8][c] = g;
       }
+  for (int q = 0; q < 9; ++q) fill_ghosts(s, s->w[q]);
 }
 
 /* ---------------------------------------------------------------- Sec. 2.3 */

@@ -1,0 +1,399 @@
+// mhd_device.cuh -- device arithmetic of one time step of the MHD + H/H2 chemistry method of
+// arXiv:1608.08748 (Kulikov, Chernykh & Protasov).  Templated on the bulk type T (double for the
+// FP64 path, float for the FP32-bulk path); the CFL reduction and the chemistry are FP64 always.
+//
+// The formulas follow the paper section by section and are written with a fixed operation order
+// (no reassociation, no contraction in the FP64 build) so that the FP64 path reproduces a plain
+// evaluation of the same equations up to the last bit wherever the math library is not involved.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace mhd {
+
+// ------------------------------------------------------------------------------------------------
+// Geometry and parameters (passed by value to every kernel)
+struct Geom {
+  int n[3];          // cells per axis
+  int bc[3];         // 0 periodic, 1 outflow (zero-gradient)
+  long long N;       // cells
+  long long NF;      // (nx+1)(ny+1)(nz+1): size of face / edge scratch arrays
+};
+
+struct Phys {
+  double gamma;      // scalar adiabatic index (chemistry off)
+  double dx, ih;     // cell width and 1/dx
+  int chem;          // H/H2 network on
+  int regul_mode;    // Sec. 2.9 reading: 0 max form, 1 unconditional, 2 literal branch order
+  double lshield;    // shielding length, code units
+  double bdop, xnorm, taud;
+};
+
+// Device-resident scalars of a simulation: tau never crosses to the host inside a step.
+struct Scalars {
+  double cfl, t_end;       // set by the host with a kernel launch (graph-safe)
+  double tau, tau_h;       // this step's tau and tau / dx
+  double t;                // simulated time
+  unsigned long long dmax; // bits of max CFL denominator of the current state (positive double)
+  unsigned long long vel_branch;
+  long long steps;
+  int flags;               // bit 0: non-physical state, bit 1: tau <= 0
+  int fixed_tau;           // 1: tau was given by the host (stage calls)
+};
+
+template <typename T>
+struct State {
+  T* rho;
+  T* m[3];
+  T* E;
+  T* eint;
+  T* rh2;  // may be unused when chemistry is off
+  T* b[3];
+};
+
+// ------------------------------------------------------------------------------------------------
+// indexing: cells [k][j][i]; face / edge scratch arrays on the (n+1)^3 lattice
+__device__ __forceinline__ int wrap(int i, int n, int bc) {
+  if (bc == 0) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+__device__ __forceinline__ long long cidx(const Geom& g, int i, int j, int k) {
+  return ((long long)k * g.n[1] + j) * g.n[0] + i;
+}
+__device__ __forceinline__ long long fidx(const Geom& g, int i, int j, int k) {
+  return ((long long)k * (g.n[1] + 1) + j) * (g.n[0] + 1) + i;
+}
+// cell index of (c[0], c[1], c[2]) after the boundary map on each axis
+__device__ __forceinline__ long long cmap(const Geom& g, int c0, int c1, int c2) {
+  return cidx(g, wrap(c0, g.n[0], g.bc[0]), wrap(c1, g.n[1], g.bc[1]), wrap(c2, g.n[2], g.bc[2]));
+}
+
+// ------------------------------------------------------------------------------------------------
+// Sec. 2.1: local parabola.  Delta q = q^R - q^L (the parabola's endpoints q(0) = q^L, q(1) = q^R).
+template <typename T>
+struct Para {
+  T L, R, d, q6;
+};
+
+template <typename T>
+__device__ __forceinline__ T slope_m(T qm, T q0, T qp) {
+  T dq = T(0.5) * (qp - qm);
+  T dp = qp - q0, dn = q0 - qm;
+  if (dp * dn > T(0)) {
+    T a = fabs(dq), b = T(2) * fabs(dp), c = T(2) * fabs(dn);
+    T mn = a < b ? a : b;
+    mn = mn < c ? mn : c;
+    return copysign(mn, dq);
+  }
+  return T(0);
+}
+
+// Steps 1-5 from q_{i-2} .. q_{i+2}; Step 4 weights in the reading where hbar weighs the
+// flattened values q -+ delta_m q / 4 (the amendment acts in discontinuities).
+template <typename T>
+__device__ __forceinline__ Para<T> ppm(T qm2, T qm1, T qc, T qp1, T qp2) {
+  const T SIXTH = T(1.0 / 6.0);
+  T dmm = slope_m(qm2, qm1, qc);
+  T dm0 = slope_m(qm1, qc, qp1);
+  T dmp = slope_m(qc, qp1, qp2);
+  T qL = T(0.5) * (qm1 + qc) - (dm0 - dmm) * SIXTH;
+  T qR = T(0.5) * (qc + qp1) - (dmp - dm0) * SIXTH;
+  T dq = qR - qL;
+  T q6 = T(6) * (qc - T(0.5) * (qL + qR));
+  if ((qL - qc) * (qc - qR) <= T(0)) {
+    qL = qc;
+    qR = qc;
+  } else if (dq * q6 > dq * dq) {
+    qL = T(3) * qc - T(2) * qR;
+  } else if (dq * q6 < -(dq * dq)) {
+    qR = T(3) * qc - T(2) * qL;
+  }
+  T qLp = qc - T(0.25) * dm0, qRp = qc + T(0.25) * dm0;
+  T Dp = qp2 - T(2) * qp1 + qc;
+  T Dm = qc - T(2) * qm1 + qm2;
+  T dq2 = qp1 - qm1;
+  T ap = fabs(qp1), am = fabs(qm1);
+  T mn = ap < am ? ap : am;
+  T sum = ap + am;
+  mn = mn < sum ? mn : sum;
+  T hb = T(0);
+  if (!(fabs(dq2) - T(0.01) * mn <= T(0) || Dp * Dm > T(0))) {
+    T eta = -(Dp - Dm) / (T(3) * dq2);
+    hb = T(20) * (eta - T(0.05));
+  } else {
+    hb = T(20) * (T(0) - T(0.05));
+  }
+  hb = hb < T(1) ? hb : T(1);
+  hb = hb > T(0) ? hb : T(0);
+  qL = hb * qLp + (T(1) - hb) * qL;
+  qR = hb * qRp + (T(1) - hb) * qR;
+  Para<T> P;
+  P.L = qL;
+  P.R = qR;
+  P.d = qR - qL;
+  P.q6 = T(6) * (qc - T(0.5) * (qL + qR));
+  return P;
+}
+
+// Sec. 2.4: parabola averages over the domain of dependence of a wave of |speed| y h / tau
+template <typename T>
+__device__ __forceinline__ T avg_right_end(const Para<T>& P, T y) {
+  const T TWO_THIRDS = T(2.0 / 3.0);
+  return P.R - T(0.5) * y * (P.d - P.q6 * (T(1) - TWO_THIRDS * y));
+}
+template <typename T>
+__device__ __forceinline__ T avg_left_end(const Para<T>& P, T y) {
+  const T TWO_THIRDS = T(2.0 / 3.0);
+  return P.L + T(0.5) * y * (P.d + P.q6 * (T(1) - TWO_THIRDS * y));
+}
+
+// ------------------------------------------------------------------------------------------------
+// Sec. 2.4 + App. A: Roe-type face state, eigenvectors and the characteristic Riemann solution.
+// wl/wr = (rho, p, gamma, B_t1, B_t2, sqrt(rho)) of the left/right cell; Bn the face field.
+// qs = (V_n, V_t1, V_t2, B_t1, B_t2, P).
+template <typename T>
+__device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, const Para<T> pl[6],
+                                        const Para<T> pr[6], T tau_h, T qs[6]) {
+  const T INV_SQRT2 = T(0.70710678118654752440);
+  T sl = wl[5], sr = wr[5];
+  T den = sl + sr;
+  T rho = (sl * wl[0] + sr * wr[0]) / den;
+  T p = (sl * wl[1] + sr * wr[1]) / den;
+  T gam = (sl * wl[2] + sr * wr[2]) / den;
+  T Bt1 = (sl * wr[3] + sr * wl[3]) / den;  // crossed weights for B
+  T Bt2 = (sl * wr[4] + sr * wl[4]) / den;
+
+  T c2 = gam * p / rho;
+  T ca2 = Bn * Bn / rho;
+  T b2 = (Bn * Bn + Bt1 * Bt1 + Bt2 * Bt2) / rho;
+  T s = c2 + b2;
+  T disc = s * s - T(4) * c2 * ca2;
+  if (disc < T(0)) disc = T(0);
+  T sq = sqrt(disc);
+  T cf2 = T(0.5) * (s + sq);
+  T cs2 = T(0.5) * (s - sq);
+  if (cs2 < T(0)) cs2 = T(0);
+  T c = sqrt(c2), cf = sqrt(cf2), cs = sqrt(cs2), ca = sqrt(ca2);
+  T af, as;
+  if (cf2 - cs2 > T(1e-12) * s) {
+    T a1 = c2 - cs2, a2 = cf2 - c2;
+    if (a1 < T(0)) a1 = T(0);
+    if (a2 < T(0)) a2 = T(0);
+    af = sqrt(a1 / (cf2 - cs2));
+    as = sqrt(a2 / (cf2 - cs2));
+  } else {
+    af = INV_SQRT2;
+    as = INV_SQRT2;
+  }
+  T bp2 = Bt1 * Bt1 + Bt2 * Bt2;
+  T by, bz;
+  if (bp2 > T(1e-24) * rho * s) {
+    T bp = sqrt(bp2);
+    by = Bt1 / bp;
+    bz = Bt2 / bp;
+  } else {
+    by = INV_SQRT2;
+    bz = INV_SQRT2;
+  }
+  T sg = Bn >= T(0) ? T(1) : T(-1);
+  T sqr = sqrt(rho);
+  T gp = gam * p, sc = sqr * c, sr2 = sqrt(T(0.5) * rho);
+  T i2c2 = T(1) / (T(2) * c2), i2sc = T(1) / (T(2) * sc), i2rc2 = T(1) / (T(2) * rho * c2);
+  T isr2 = T(1) / sqrt(T(2) * rho);
+
+#pragma unroll
+  for (int m = 0; m < 6; ++m) qs[m] = T(0);
+
+  // one wave at a time: s_k = L_k . qbar_k, q* += R_{:,k} s_k (k ascending, as R s)
+  T qb[6];
+  T sk;
+  // wave 1: +c_f, left cell, right end
+  {
+    T y = cf * tau_h;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) qb[m] = avg_right_end(pl[m], y);
+    sk = T(0);
+    sk = sk + af * cf * i2c2 * qb[0];
+    sk = sk + -as * cs * by * sg * i2c2 * qb[1];
+    sk = sk + -as * cs * bz * sg * i2c2 * qb[2];
+    sk = sk + as * by * i2sc * qb[3];
+    sk = sk + as * bz * i2sc * qb[4];
+    sk = sk + af * i2rc2 * qb[5];
+    qs[0] = qs[0] + af * cf * sk;
+    qs[1] = qs[1] + -as * cs * by * sg * sk;
+    qs[2] = qs[2] + -as * cs * bz * sg * sk;
+    qs[3] = qs[3] + as * sc * by * sk;
+    qs[4] = qs[4] + as * sc * bz * sk;
+    qs[5] = qs[5] + af * gp * sk;
+  }
+  // wave 2: -c_f, right cell, left end
+  {
+    T y = cf * tau_h;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) qb[m] = avg_left_end(pr[m], y);
+    sk = T(0);
+    sk = sk + -af * cf * i2c2 * qb[0];
+    sk = sk + as * cs * by * sg * i2c2 * qb[1];
+    sk = sk + as * cs * bz * sg * i2c2 * qb[2];
+    sk = sk + as * by * i2sc * qb[3];
+    sk = sk + as * bz * i2sc * qb[4];
+    sk = sk + af * i2rc2 * qb[5];
+    qs[0] = qs[0] + -af * cf * sk;
+    qs[1] = qs[1] + as * cs * by * sg * sk;
+    qs[2] = qs[2] + as * cs * bz * sg * sk;
+    qs[3] = qs[3] + as * sc * by * sk;
+    qs[4] = qs[4] + as * sc * bz * sk;
+    qs[5] = qs[5] + af * gp * sk;
+  }
+  // wave 3: +c_s, left cell
+  {
+    T y = cs * tau_h;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) qb[m] = avg_right_end(pl[m], y);
+    sk = T(0);
+    sk = sk + as * cs * i2c2 * qb[0];
+    sk = sk + af * cf * by * sg * i2c2 * qb[1];
+    sk = sk + af * cf * bz * sg * i2c2 * qb[2];
+    sk = sk + -af * by * i2sc * qb[3];
+    sk = sk + -af * bz * i2sc * qb[4];
+    sk = sk + as * i2rc2 * qb[5];
+    qs[0] = qs[0] + as * cs * sk;
+    qs[1] = qs[1] + af * cf * by * sg * sk;
+    qs[2] = qs[2] + af * cf * bz * sg * sk;
+    qs[3] = qs[3] + -af * sc * by * sk;
+    qs[4] = qs[4] + -af * sc * bz * sk;
+    qs[5] = qs[5] + as * gp * sk;
+  }
+  // wave 4: -c_s, right cell
+  {
+    T y = cs * tau_h;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) qb[m] = avg_left_end(pr[m], y);
+    sk = T(0);
+    sk = sk + -as * cs * i2c2 * qb[0];
+    sk = sk + -af * cf * by * sg * i2c2 * qb[1];
+    sk = sk + -af * cf * bz * sg * i2c2 * qb[2];
+    sk = sk + -af * by * i2sc * qb[3];
+    sk = sk + -af * bz * i2sc * qb[4];
+    sk = sk + as * i2rc2 * qb[5];
+    qs[0] = qs[0] + -as * cs * sk;
+    qs[1] = qs[1] + -af * cf * by * sg * sk;
+    qs[2] = qs[2] + -af * cf * bz * sg * sk;
+    qs[3] = qs[3] + -af * sc * by * sk;
+    qs[4] = qs[4] + -af * sc * bz * sk;
+    qs[5] = qs[5] + as * gp * sk;
+  }
+  // wave 5: +c_a, left cell (no v_n, p components)
+  {
+    T y = ca * tau_h;
+#pragma unroll
+    for (int m = 1; m < 5; ++m) qb[m] = avg_right_end(pl[m], y);
+    sk = T(0);
+    sk = sk + -bz * sg * INV_SQRT2 * qb[1];
+    sk = sk + by * sg * INV_SQRT2 * qb[2];
+    sk = sk + bz * isr2 * qb[3];
+    sk = sk + -by * isr2 * qb[4];
+    qs[1] = qs[1] + -bz * INV_SQRT2 * sg * sk;
+    qs[2] = qs[2] + by * INV_SQRT2 * sg * sk;
+    qs[3] = qs[3] + sr2 * bz * sk;
+    qs[4] = qs[4] + -sr2 * by * sk;
+  }
+  // wave 6: -c_a, right cell
+  {
+    T y = ca * tau_h;
+#pragma unroll
+    for (int m = 1; m < 5; ++m) qb[m] = avg_left_end(pr[m], y);
+    sk = T(0);
+    sk = sk + -bz * sg * INV_SQRT2 * qb[1];
+    sk = sk + by * sg * INV_SQRT2 * qb[2];
+    sk = sk + -bz * isr2 * qb[3];
+    sk = sk + by * isr2 * qb[4];
+    qs[1] = qs[1] + -bz * INV_SQRT2 * sg * sk;
+    qs[2] = qs[2] + by * INV_SQRT2 * sg * sk;
+    qs[3] = qs[3] + -sr2 * bz * sk;
+    qs[4] = qs[4] + sr2 * by * sk;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Sec. 2.3: CFL denominator |v| + b + c + c_a + c_s + c_f, the largest over the three choices of
+// the longitudinal axis (b^2 = B^2 / rho).  FP64.
+__device__ __forceinline__ double cfl_denominator(double rho, double vx, double vy, double vz,
+                                                  double Bx, double By, double Bz, double p,
+                                                  double gam) {
+  double c2 = gam * p / rho;
+  double b2 = (Bx * Bx + By * By + Bz * Bz) / rho;
+  double v = sqrt(vx * vx + vy * vy + vz * vz);
+  double b = sqrt(b2), c = sqrt(c2);
+  const double Bd[3] = {Bx, By, Bz};
+  double Dmax = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double ca2 = Bd[d] * Bd[d] / rho;
+    double s = c2 + b2;
+    double disc = s * s - 4.0 * c2 * ca2;
+    if (disc < 0.0) disc = 0.0;
+    double sq = sqrt(disc);
+    double cf = sqrt(0.5 * (s + sq));
+    double cs2 = 0.5 * (s - sq);
+    if (cs2 < 0.0) cs2 = 0.0;
+    double cs = sqrt(cs2), ca = sqrt(ca2);
+    double D = v + b + c + ca + cs + cf;
+    if (D > Dmax) Dmax = D;
+  }
+  return Dmax;
+}
+
+// Sec. 4.3 effective adiabatic index of the H/H2 mixture (no electrons)
+__device__ __forceinline__ double gamma_eff(double rho, double rh2) {
+  double nH = rho - rh2, nH2 = 0.5 * rh2;
+  return (5.0 * nH + 7.0 * nH2) / (3.0 * nH + 5.0 * nH2);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Sec. 2.7 + App. D: one cell of the H/H2 network (reactions 1-4), backward-differentiation
+// update of n_H2 with rates frozen over the step; returns the new rho_H2.  FP64.
+struct ChemConst {
+  static constexpr double KB = 1.380649e-16;         // erg / K
+  static constexpr double MH = 1.6735575e-24;        // g
+  static constexpr double PC = 3.0856775814913673e18; // cm
+  static constexpr double KMS = 1.0e5;               // cm / s
+};
+
+__device__ __forceinline__ double chem_cell(const Phys& ph, double rho, double eint, double rh2,
+                                            double tau) {
+  const double P0 = ChemConst::MH * ChemConst::KMS * ChemConst::KMS;  // code pressure, erg cm^-3
+  const double T0 = ChemConst::PC / ChemConst::KMS;                  // code time, s
+  double nH = rho - rh2, nH2 = 0.5 * rh2, n = rho;
+  double g = gamma_eff(rho, rh2);
+  double p = (g - 1.0) * eint * P0;
+  double T = p / ((nH + nH2) * ChemConst::KB);
+  // App. D rates
+  double t2 = T / 100.0;
+  double s2 = sqrt(t2);
+  double k1p = 3e-17 * s2 / (((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2));
+  double k2 = T > 7390.0 ? 6.11e-14 * exp(-2.93e4 / T) : 2.67e-15 * exp(-((6750.0 / T) * (6750.0 / T)));
+  double k3 = T > 7291.0 ? 5.22e-14 * exp(-3.22e4 / T)
+                         : 3.17e-15 * exp(-(4060.0 / T) - (7500.0 / T) * (7500.0 / T));
+  double Ls = (ph.lshield > 0.0 ? ph.lshield : ph.dx) * ChemConst::PC;
+  double NH = nH * Ls, NH2 = nH2 * Ls;
+  double fdust = exp(-(ph.taud * (NH + NH2)));
+  double x = NH2 / ph.xnorm;
+  double u = 1.0 + x / ph.bdop;
+  double sx = sqrt(1.0 + x);
+  double fsh = 0.965 / (u * u) + 0.035 / sx * exp(-8.5e-4 * sx);
+  double k4 = (3.3 * 1.7e-11) * fsh * fdust;
+  double C = k1p * n * nH;
+  double D = (k2 * nH + k3 * nH2) + k4;
+  double ts = tau * T0;
+  double nH2n = nH2 + ts * (C - D * nH2) / (1.0 + ts * D);
+  if (nH2n < 0.0) nH2n = 0.0;
+  if (nH2n > 0.5 * n) nH2n = 0.5 * n;
+  return 2.0 * nH2n;
+}
+
+}  // namespace mhd

@@ -1,0 +1,221 @@
+"""Python binding of libmhd.so (include/mhd.h): ctypes argument marshalling only.
+
+Every step of the time step runs in the CUDA kernels of libmhd.so; this module converts arrays to
+pointers and return codes to exceptions.  Host data are numpy arrays; device data are torch CUDA
+tensors (their data pointers are passed with on_device = 1).  If the library is missing the import
+of a Sim raises: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OPT = {"bc_x": 1, "bc_y": 2, "bc_z": 3, "chem": 4, "precision": 5, "regul_mode": 7,
+       "chem_lshield": 8, "chem_bdop": 9, "chem_xnorm": 10, "chem_taud": 11, "graph": 14}
+STATUS = {0: "MHD_OK", 1: "MHD_PENDING", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA",
+          -4: "MHD_ENONPHYS", -5: "MHD_ETIMEOUT", -6: "MHD_ENOTFOUND", -7: "MHD_ECAPACITY"}
+F64, F32 = 0, 1
+
+
+class MHDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Fields(C.Structure):
+    _fields_ = [("rho", C.c_void_p), ("mom", C.c_void_p * 3), ("E", C.c_void_p),
+                ("B", C.c_void_p * 3), ("rho_h2", C.c_void_p), ("dtype", C.c_int),
+                ("on_device", C.c_int)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("sum_rho", C.c_double), ("sum_mom", C.c_double * 3), ("sum_E", C.c_double),
+                ("sum_b", C.c_double * 3), ("max_div_b_h", C.c_double), ("t", C.c_double),
+                ("tau_next", C.c_double), ("steps", C.c_int64), ("vel_branch", C.c_int64),
+                ("error_flags", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libmhd.so (built in-tree by paper_1608_08748_gb300.build)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmhd.so not built ({path}); run paper_1608_08748_gb300.build.build()")
+        L = C.CDLL(path)
+        vp, d, i = C.c_void_p, C.c_double, C.c_int
+        L.mhd_create.restype = vp
+        L.mhd_create.argtypes = [i, i, i, d, d]
+        L.mhd_destroy.argtypes = [vp]
+        L.mhd_last_error.restype = C.c_char_p
+        L.mhd_set_option.argtypes = [vp, i, d]
+        L.mhd_set_stream.argtypes = [vp, vp]
+        L.mhd_set_state.argtypes = [vp, C.POINTER(Fields)]
+        L.mhd_set_face_B.argtypes = [vp, vp, vp, vp, i]
+        L.mhd_get_state.argtypes = [vp, C.POINTER(Fields)]
+        L.mhd_get_full.argtypes = [vp, vp, vp, vp, vp, i]
+        L.mhd_set_full.argtypes = [vp, vp, vp, vp, vp, i]
+        L.mhd_step.argtypes = [vp, d, C.POINTER(d)]
+        L.mhd_advance.argtypes = [vp, d, d, i, C.POINTER(i)]
+        L.mhd_sync.argtypes = [vp]
+        L.mhd_stage.argtypes = [vp, i, d]
+        L.mhd_diagnostics.argtypes = [vp, C.POINTER(Diag)]
+        L.mhd_bytes_needed.restype = C.c_size_t
+        L.mhd_bytes_needed.argtypes = [i, i, i, i, i]
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise MHDError(rc, lib().mhd_last_error().decode())
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, on_device, keepalive) of a numpy array or torch tensor of the given dtype."""
+    if _is_torch(x):
+        import torch
+        want = torch.float64 if dtype == F64 else torch.float32
+        if x.dtype != want or not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous and of the requested dtype")
+        return x.data_ptr(), int(x.is_cuda), x
+    want = np.float64 if dtype == F64 else np.float32
+    a = np.ascontiguousarray(x, dtype=want)
+    return a.ctypes.data, 0, a
+
+
+class Sim:
+    """One simulation box on the current CUDA device (all memory owned by libmhd.so)."""
+
+    def __init__(self, nx, ny, nz, gamma, dx, **options):
+        self.L = lib()
+        self.shape = (nz, ny, nx)
+        self.h = self.L.mhd_create(nx, ny, nz, float(gamma), float(dx))
+        if not self.h:
+            raise MHDError(-1, self.L.mhd_last_error().decode())
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mhd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_option(self, key, value):
+        _check(self.L.mhd_set_option(self.h, OPT[key], float(value)))
+
+    def set_stream(self, stream_ptr):
+        _check(self.L.mhd_set_stream(self.h, stream_ptr))
+
+    def _fields(self, rho, mom, E, B, rho_h2, dtype):
+        keep = []
+        f = Fields()
+        vals = []
+        on_dev = set()
+        for x in [rho, mom[0], mom[1], mom[2], E, B[0], B[1], B[2], rho_h2]:
+            if x is None:
+                vals.append(None)
+                continue
+            p, dev, k = _ptr(x, dtype)
+            keep.append(k)
+            on_dev.add(dev)
+            vals.append(p)
+        if len(on_dev) > 1:
+            raise ValueError("all fields must be on the host or all on the device")
+        f.rho = vals[0]
+        for q in range(3):
+            f.mom[q] = vals[1 + q]
+            f.B[q] = vals[5 + q]
+        f.E = vals[4]
+        f.rho_h2 = vals[8]
+        f.dtype = dtype
+        f.on_device = on_dev.pop() if on_dev else 0
+        return f, keep
+
+    def set_state(self, rho, mom, E, B, rho_h2=None, dtype=None):
+        if dtype is None:
+            dtype = F32 if getattr(rho, "dtype", None) in (np.float32,) or str(getattr(rho, "dtype", "")) == "torch.float32" else F64
+        f, keep = self._fields(rho, mom, E, B, rho_h2, dtype)
+        _check(self.L.mhd_set_state(self.h, C.byref(f)))
+
+    def set_face_B(self, bx, by, bz):
+        ptrs = [_ptr(x, F64) for x in (bx, by, bz)]
+        _check(self.L.mhd_set_face_B(self.h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[0][1]))
+
+    def get_state(self, dtype=F64, out=None):
+        """Copy the state out: numpy arrays by default, or into `out` (dict of arrays/tensors)."""
+        npdt = np.float64 if dtype == F64 else np.float32
+        if out is None:
+            out = {"rho": np.empty(self.shape, npdt), "mom": np.empty((3,) + self.shape, npdt),
+                   "E": np.empty(self.shape, npdt), "B": np.empty((3,) + self.shape, npdt),
+                   "rho_h2": np.empty(self.shape, npdt)}
+        f, keep = self._fields(out["rho"], out["mom"], out["E"], out["B"], out.get("rho_h2"), dtype)
+        _check(self.L.mhd_get_state(self.h, C.byref(f)))
+        return out
+
+    def get_full(self):
+        out = [np.empty(self.shape) for _ in range(4)]
+        _check(self.L.mhd_get_full(self.h, *[o.ctypes.data for o in out], 0))
+        return {"eint": out[0], "bface": np.stack(out[1:])}
+
+    def set_full(self, eint, bface):
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (eint, bface[0], bface[1], bface[2])]
+        _check(self.L.mhd_set_full(self.h, *[x.ctypes.data for x in a], 0))
+
+    def step(self, cfl, sync=True):
+        if sync:
+            dt = C.c_double(0.0)
+            _check(self.L.mhd_step(self.h, float(cfl), C.byref(dt)))
+            return dt.value
+        _check(self.L.mhd_step(self.h, float(cfl), None))
+        return None
+
+    def advance(self, cfl, t_end, max_steps=1 << 30):
+        n = C.c_int(0)
+        _check(self.L.mhd_advance(self.h, float(cfl), float(t_end), int(max_steps), C.byref(n)))
+        return n.value
+
+    def sync(self):
+        _check(self.L.mhd_sync(self.h))
+
+    def stage(self, which, tau):
+        _check(self.L.mhd_stage(self.h, int(which), float(tau)))
+
+    def diagnostics(self):
+        d = Diag()
+        _check(self.L.mhd_diagnostics(self.h, C.byref(d)))
+        return {"rho": d.sum_rho, "mx": d.sum_mom[0], "my": d.sum_mom[1], "mz": d.sum_mom[2],
+                "E": d.sum_E, "bx": d.sum_b[0], "by": d.sum_b[1], "bz": d.sum_b[2],
+                "max_div_b_h": d.max_div_b_h, "t": d.t, "tau_next": d.tau_next, "steps": d.steps,
+                "vel_branch": d.vel_branch, "error_flags": d.error_flags}
+
+
+def bytes_needed(nx, ny, nz, precision=0, chem=1):
+    return lib().mhd_bytes_needed(nx, ny, nz, precision, chem)
+
+
+def from_ic(ic, **options):
+    """Sim loaded from an initial-condition dict of paper_1608_08748_gb300.inputs."""
+    nz, ny, nx = ic["rho"].shape
+    opts = dict(ic.get("options", {}))
+    opts.update(options)
+    s = Sim(nx, ny, nz, ic["gamma"], ic["dx"], **opts)
+    s.set_state(ic["rho"], ic["mom"], ic["E"], ic["B"], ic.get("rho_h2"))
+    if "bface" in ic:
+        s.set_face_B(*ic["bface"])
+    return s
