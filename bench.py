@@ -33,10 +33,14 @@ WORKLOAD = "mhd_turbulence_h2chem_128^3_fp64"
 METRIC = "Mcell-updates/s"
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# algorithmic FP64 flops of one Eulerian face solve (counted from the kernel source: PPM of 6
-# variables for 2 cells, Roe average, eigenvectors, 36 parabola averages, L q, R s, fluxes;
-# add/sub/mul/div/sqrt one flop each, compares not counted)
-FLOPS_PER_EULER_FACE = 1248
+# algorithmic FP64 flops of one Eulerian face solve, counted from the kernel source: 12 PPM
+# parabolas (6 variables x 2 cells, ~70 each), Roe average and eigenvectors (~60), 36 parabola
+# averages with L q and R s (~400), fluxes (~25); add/sub/mul/div/sqrt one flop each, compares
+# not counted
+FLOPS_PER_EULER_FACE = 1350
+# DRAM bytes (read + write) of one k_euler_face launch at 128^3 from the ncu capture summarised in
+# profiles/k_euler_face_turbulence_128_fp64.md (set to None when the kernel changes)
+EULER_FACE_TRAFFIC_BYTES = 248.5e6
 
 
 def rank_info():
@@ -234,7 +238,7 @@ def run_ours(args):
         achieved = FLOPS_PER_EULER_FACE * faces_per_launch / avg_launch_s / 1e12
         roofline = {"bound": "alu", "kernel": "k_euler_face (FP64)", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "traffic": None, "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
+                    "traffic": EULER_FACE_TRAFFIC_BYTES, "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
 
     if rank != 0:
         return
