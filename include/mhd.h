@@ -154,6 +154,31 @@ int mhd_profile(mhd_sim* s, double cfl, int steps, double* out_ms, int64_t* out_
 /* Number of kernel launches (not counting the copies of the RK register) in one mhd_step. */
 int mhd_launches_per_step(mhd_sim* s);
 
+/* FP64 diagnostics of caller-owned device arrays without any device allocation.  (The paper has
+   no counterpart: this is a service of the library.)  It is for callers that cannot allocate
+   device memory at the point of the call: code running while a stream is captured into a CUDA
+   graph in global capture mode (cudaMalloc/cudaFree are illegal there), serving processes whose
+   HBM budget is fully committed to resident state, and monitors inside another application's
+   time loop that must not touch its allocator.
+   Inputs: rho, mx, my, mz, E (cells) and bx, by, bz (b_d at face i_d - 1/2) as device float64
+   arrays of nx*ny*nz elements, C order; bc_x/y/z 0 periodic or 1 outflow (for the upper faces of
+   the divergence).  Output: out, a device pointer to 9 doubles, filled with sum rho, sum m_x,
+   sum m_y, sum m_z, sum rho E, sum b_x, sum b_y, sum b_z and max |sum_d (b_d(i_d+1/2) -
+   b_d(i_d-1/2))|: the same values, with the same reduction order, as mhd_diagnostics.
+   The work is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream) and the call
+   returns without waiting.  The block partials live in one fixed device array of
+   MHD_NOALLOC_MAX_CELLS / 256 * 9 doubles (1.125 MiB) that every GPU which loads the library holds
+   until the process exits; nx*ny*nz above MHD_NOALLOC_MAX_CELLS returns MHD_EINVAL.  The first
+   call on a device looks up that array's device address (cudaGetSymbolAddress), so make the first
+   call on each device before any stream capture.  Every call shares the array: calls that may
+   overlap on the GPU (different streams, or different host threads) race and must be serialised
+   by the caller. */
+#define MHD_NOALLOC_MAX_CELLS 4194304LL
+int mhd_diagnostics_noalloc(const double* rho, const double* mx, const double* my,
+                            const double* mz, const double* E, const double* bx, const double* by,
+                            const double* bz, int nx, int ny, int nz, int bc_x, int bc_y,
+                            int bc_z, double* out, void* stream);
+
 /* Bytes of device memory one sim of this size uses (precision 0 FP64 / 1 FP32, chem 0/1). */
 size_t mhd_bytes_needed(int nx, int ny, int nz, int precision, int chem);
 

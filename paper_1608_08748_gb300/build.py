@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmhd.so")
-SOURCES = ["mhd.cu"]
+SOURCES = ["mhd.cu", "mhd_noalloc.cu"]
 HEADERS = ["mhd_device.cuh", "mhd_kernels.cuh"]
 
 # --fmad=false: the FP64 path rounds every product and sum separately, in the order the formulas

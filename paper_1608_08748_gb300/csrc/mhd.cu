@@ -47,6 +47,11 @@ struct Buffers {
 
 }  // namespace
 
+namespace mhd_rt {
+// record the message mhd_last_error() returns on this thread; returns code
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace mhd_rt
+
 struct mhd_sim {
   Geom g;
   Phys ph;
