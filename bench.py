@@ -43,6 +43,21 @@ FLOPS_PER_EULER_FACE = 1350
 EULER_FACE_TRAFFIC_BYTES = 248.5e6
 
 
+def reduce_max(x, dist=None, device="cpu"):
+    """Largest value of x over all ranks (the slowest rank's time); x itself without a group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, cells_per_rank, steps, seconds):
+    """Whole-job Mcell-updates/s: every rank advances its own box of cells_per_rank cells."""
+    return world * cells_per_rank * steps / seconds / 1e6
+
+
 def rank_info():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -183,12 +198,8 @@ def run_ours(args):
     stop.set()
     th.join(timeout=10)
     sim.sync()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * cells * args.steps / (ms * 1e-3) / 1e6
+    ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+    value = job_rate(world, cells, args.steps, ms * 1e-3)
     launches = sim.L.mhd_launches_per_step(sim.h) * args.steps
 
     # end to end through the C-ABI with host buffers: per step, upload the state from pinned host
@@ -209,13 +220,9 @@ def run_ours(args):
         sim.step(CFL, sync=False)
         sim.get_state(out=hnp)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
     field_bytes = 9 * cells * 8
-    e2e = {"value": world * cells * e2e_steps / e2e_s / 1e6, "unit": METRIC,
+    e2e = {"value": job_rate(world, cells, e2e_steps, e2e_s), "unit": METRIC,
            "h2d_bytes_per_step": field_bytes, "d2h_bytes_per_step": field_bytes}
 
     # per-kernel device times (event pairs around each launch, separate pass, same workload)

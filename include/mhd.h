@@ -154,6 +154,33 @@ int mhd_profile(mhd_sim* s, double cfl, int steps, double* out_ms, int64_t* out_
 /* Number of kernel launches (not counting the copies of the RK register) in one mhd_step. */
 int mhd_launches_per_step(mhd_sim* s);
 
+/* ---- Batched execution (many boxes, one launch per kernel class) ------------------------------
+   A batch advances several simulations together: every kernel of the step is launched once over
+   a table of tiles that covers all their boxes (uneven sizes allowed), and the step is captured in
+   one CUDA graph.  Each box keeps its own tau (its own CFL reduction, Sec. 2.3) and its own device
+   memory; per-cell arithmetic does not depend on the batch, so a batched box evolves bit for bit
+   like the same box stepped alone.  All sims of a batch must have a loaded state, the same
+   precision and the same device.  The batch issues work on its own stream: call mhd_batch_sync
+   before using a member sim on its own again.  A sim may belong to several batches but must not
+   be stepped by two of them at once. */
+typedef struct mhd_batch mhd_batch;
+mhd_batch* mhd_batch_create(mhd_sim* const* sims, int n);  /* NULL on error (mhd_last_error) */
+void mhd_batch_destroy(mhd_batch* b);
+/* One step of every member (tau per member from its own state). */
+int mhd_batch_step(mhd_batch* b, double cfl);
+/* Wait for the batch's work; MHD_ENONPHYS if any member flagged a non-physical state. */
+int mhd_batch_sync(mhd_batch* b);
+/* Autotune the launch shape (threads per tile, grid size) of every kernel class on this batch by
+   timing `reps` full steps per candidate; the members' states are restored afterwards, so tuning
+   changes no results.  best_ms (may be NULL) receives the tuned per-step time. */
+int mhd_batch_tune(mhd_batch* b, double cfl, int reps, double* best_ms);
+/* Launch shape of one kernel class (MHD_K_* of mhd_profile; MHD_K_SMALL = the RK register copy):
+   threads per tile (64, 128, 256 or 512) and grid = grid_mult x SMs (0: one block per tile). */
+int mhd_batch_get_shape(mhd_batch* b, int kernel_class, int* block, int* grid_mult);
+int mhd_batch_set_shape(mhd_batch* b, int kernel_class, int block, int grid_mult);
+/* Per-class CUDA-event timings of `steps` batch steps (as mhd_profile). */
+int mhd_batch_profile(mhd_batch* b, double cfl, int steps, double* out_ms, int64_t* out_launches);
+
 /* FP64 diagnostics of caller-owned device arrays without any device allocation.  (The paper has
    no counterpart: this is a service of the library.)  It is for callers that cannot allocate
    device memory at the point of the call: code running while a stream is captured into a CUDA

@@ -10,12 +10,12 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmhd.so")
 SOURCES = ["mhd.cu", "mhd_noalloc.cu"]
-HEADERS = ["mhd_device.cuh", "mhd_kernels.cuh"]
+# FP32-bulk launchers: compiled separately with contraction on
+SOURCES_F32 = ["mhd_f32.cu"]
+HEADERS = ["mhd_device.cuh", "mhd_kernels.cuh", "mhd_runtime.cuh"]
 
-# --fmad=false: the FP64 path rounds every product and sum separately, in the order the formulas
-# are written (no contraction), like a plain evaluation of the same equations.
-NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "--fmad=false",
-              "-std=c++17", "-Xcompiler", "-fPIC", "-shared"]
+# mhd.cu (FP64 path) is compiled with --fmad=false: every product and sum is rounded separately,
+# in the order the formulas are written, like a plain evaluation of the same equations.
 
 
 def _stale() -> bool:
@@ -26,17 +26,41 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+
+
+def _compile(nvcc, src, obj, extra):
+    cmd = [nvcc] + ARCH + COMMON + extra + ["-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
+    return subprocess.Popen(cmd), cmd
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the translation units in parallel and link libmhd.so."""
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = os.environ.get("NVCC", "nvcc")
+    tag = f".{os.getpid()}"
+    jobs, objs = [], []
+    for f in SOURCES + SOURCES_F32:
+        obj = os.path.join(OUT_DIR, f.replace(".cu", tag + ".o"))
+        extra = ["--fmad=true"] if f in SOURCES_F32 else ["--fmad=false"]
+        p, cmd = _compile(nvcc, os.path.join(SRC, f), obj, extra)
+        if verbose:
+            print(" ".join(cmd))
+        jobs.append((p, cmd))
+        objs.append(obj)
+    for p, cmd in jobs:
+        if p.wait() != 0:
+            raise subprocess.CalledProcessError(p.returncode, cmd)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc] + NVCC_FLAGS + ["-I", os.path.join(ROOT, "include"), "-o", tmp] + \
-        [os.path.join(SRC, f) for f in SOURCES]
+    link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
+        print(" ".join(link))
+    subprocess.run(link, check=True)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

@@ -10,9 +10,10 @@
 #include <vector>
 
 #include "mhd.h"
-#include "mhd_kernels.cuh"
+#include "mhd_runtime.cuh"
 
 using namespace mhd;
+using namespace mhd_rt;
 
 namespace {
 
@@ -29,58 +30,12 @@ int fail(int code, const std::string& msg) {
     if (e_ != cudaSuccess) return fail(MHD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
-
-// SSP-RK3 (Sec. 2.2): Q = a Q^n + b Q + g tau R
-const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};
-const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
-const double RK_G[3] = {1.0, 0.25, 2.0 / 3.0};
-
-template <typename T>
-struct Buffers {
-  State<T> s, s0;
-  Prim<T> w;
-  FaceOut<T> fo[3];  // Eulerian face outputs; the Lagrangian fluxes reuse the same memory
-  T* e[3];
-  LagFlux<T> lf[3];
-};
-
 }  // namespace
 
 namespace mhd_rt {
 // record the message mhd_last_error() returns on this thread; returns code
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
 }  // namespace mhd_rt
-
-struct mhd_sim {
-  Geom g;
-  Phys ph;
-  int precision = 0;
-  int use_graph = 1;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  char* pool = nullptr;
-  size_t pool_bytes = 0;
-  char* staging = nullptr;  // 10 * N * 8 bytes for host transfers / dtype conversion
-  Scalars* sc = nullptr;
-  Scalars* sc_host = nullptr;  // pinned mirror
-  double* diag_part = nullptr;
-  double* diag_out = nullptr;
-  double* diag_host = nullptr;  // pinned, 9 doubles
-  int diag_blocks = 0;
-  Buffers<double> b64;
-  Buffers<float> b32;
-  cudaGraphExec_t gexec = nullptr;
-  bool graph_valid = false;
-  bool params_dirty = true;
-  double last_cfl = -1.0, last_tend = -1.0;
-  bool has_state = false;
-  // profiling: event pairs around every launch while mhd_profile runs
-  bool profiling = false;
-  std::vector<cudaEvent_t> prof_ev;
-  std::vector<int> prof_cls;
-};
 
 namespace {
 
@@ -92,8 +47,9 @@ size_t pool_size(const Geom& g, int precision, int chem) {
   return es * (cells * 29 + faces * 24) + 64 * 64;
 }
 
+// lay the box's arrays out in the pool and fill its descriptor
 template <typename T>
-void carve(mhd_sim* S, Buffers<T>& B) {
+void carve(mhd_sim* S, Box<T>& B) {
   char* p = S->pool;
   auto take = [&](size_t n) {
     T* r = reinterpret_cast<T*>(p);
@@ -117,11 +73,34 @@ void carve(mhd_sim* S, Buffers<T>& B) {
   B.w.g = take(N);
   B.w.sr = take(N);
   for (int d = 0; d < 3; ++d)
-    for (int v = 0; v < 7; ++v) {
-      B.fo[d].f[v] = take(NF);
-      B.lf[d].f[v] = B.fo[d].f[v];
-    }
+    for (int v = 0; v < 7; ++v) B.fo[d].f[v] = take(NF);
   for (int d = 0; d < 3; ++d) B.e[d] = take(NF);
+  B.g = S->g;
+  B.ph = S->ph;
+  B.sc = S->sc;
+  B.nv = S->ph.chem ? 7 : 6;
+}
+
+// (re)build the single-box executor after a change of options
+template <typename T>
+int rebuild_exec(mhd_sim* S, Box<T>& B, Exec<T>& X) {
+  B.g = S->g;
+  B.ph = S->ph;
+  B.sc = S->sc;
+  B.nv = S->ph.chem ? 7 : 6;
+  exec_free(X);
+  X.prof = &S->prof;
+  cudaError_t e = exec_init(X, std::vector<Box<T>>{B});
+  if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("executor set-up: ") + cudaGetErrorString(e));
+  return MHD_OK;
+}
+
+int ensure_exec(mhd_sim* S) {
+  if (S->exec_valid) return MHD_OK;
+  int rc = S->precision ? rebuild_exec(S, S->b32, S->x32) : rebuild_exec(S, S->b64, S->x64);
+  if (rc == MHD_OK) S->exec_valid = true;
+  S->graph_valid = false;
+  return rc;
 }
 
 int alloc_pool(mhd_sim* S) {
@@ -140,29 +119,10 @@ int alloc_pool(mhd_sim* S) {
   else
     carve(S, S->b64);
   S->graph_valid = false;
+  S->exec_valid = false;
   S->has_state = false;
-  return MHD_OK;
+  return ensure_exec(S);
 }
-
-// CUDA event pair around one launch (only while profiling)
-struct PScope {
-  mhd_sim* S;
-  PScope(mhd_sim* s_, int cls) : S(s_) {
-    if (!S->profiling) return;
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    cudaEventRecord(e, S->stream);
-    S->prof_ev.push_back(e);
-    S->prof_cls.push_back(cls);
-  }
-  ~PScope() {
-    if (!S->profiling) return;
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    cudaEventRecord(e, S->stream);
-    S->prof_ev.push_back(e);
-  }
-};
 
 void drop_graph(mhd_sim* S) {
   if (S->gexec) cudaGraphExecDestroy(S->gexec);
@@ -170,78 +130,22 @@ void drop_graph(mhd_sim* S) {
   S->graph_valid = false;
 }
 
-// ------------------------------------------------------------------------------------------------
-// stage launchers
-template <typename T>
-void launch_euler_stage(mhd_sim* S, Buffers<T>& B) {
-  const Geom& g = S->g;
-  cudaStream_t st = S->stream;
-  const size_t bytes = (size_t)g.N * sizeof(T);
-  for (int d = 0; d < 3; ++d) cudaMemcpyAsync(B.s0.m[d], B.s.m[d], bytes, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(B.s0.E, B.s.E, bytes, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(B.s0.eint, B.s.eint, bytes, cudaMemcpyDeviceToDevice, st);
-  for (int d = 0; d < 3; ++d) cudaMemcpyAsync(B.s0.b[d], B.s.b[d], bytes, cudaMemcpyDeviceToDevice, st);
-  const long long fx = (long long)(g.n[0] + 1) * g.n[1] * g.n[2];
-  const long long fy = (long long)g.n[0] * (g.n[1] + 1) * g.n[2];
-  const long long fz = (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
-  for (int r = 0; r < 3; ++r) {
-    { PScope p(S, MHD_K_PRIM); k_prim<T><<<nblk(g.N, 256), 256, 0, st>>>(g, S->ph, B.s, B.w); }
-    { PScope p(S, MHD_K_EULER_FACE); k_euler_face<T, 0><<<nblk(fx, 128), 128, 0, st>>>(g, S->sc, B.s, B.w, B.fo[0]); }
-    { PScope p(S, MHD_K_EULER_FACE); k_euler_face<T, 1><<<nblk(fy, 128), 128, 0, st>>>(g, S->sc, B.s, B.w, B.fo[1]); }
-    { PScope p(S, MHD_K_EULER_FACE); k_euler_face<T, 2><<<nblk(fz, 128), 128, 0, st>>>(g, S->sc, B.s, B.w, B.fo[2]); }
-    { PScope p(S, MHD_K_EDGES);
-      k_edges<T><<<nblk(g.NF, 256), 256, 0, st>>>(g, B.fo[0], B.fo[1], B.fo[2], B.e[0], B.e[1], B.e[2]); }
-    { PScope p(S, MHD_K_EULER_UPDATE);
-      k_euler_update<T><<<nblk(g.N, 256), 256, 0, st>>>(g, S->ph, S->sc, B.s, B.s0, B.w, B.fo[0], B.fo[1],
-                                                        B.fo[2], B.e[0], B.e[1], B.e[2], (T)RK_A[r],
-                                                        (T)RK_B[r], (T)RK_G[r]); }
-  }
-}
-
-template <typename T>
-void launch_lag_stage(mhd_sim* S, Buffers<T>& B) {
-  const Geom& g = S->g;
-  cudaStream_t st = S->stream;
-  const size_t bytes = (size_t)g.N * sizeof(T);
-  const int nv = S->ph.chem ? 7 : 6;
-  cudaMemcpyAsync(B.s0.rho, B.s.rho, bytes, cudaMemcpyDeviceToDevice, st);
-  for (int d = 0; d < 3; ++d) cudaMemcpyAsync(B.s0.m[d], B.s.m[d], bytes, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(B.s0.E, B.s.E, bytes, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(B.s0.eint, B.s.eint, bytes, cudaMemcpyDeviceToDevice, st);
-  if (S->ph.chem) cudaMemcpyAsync(B.s0.rh2, B.s.rh2, bytes, cudaMemcpyDeviceToDevice, st);
-  const long long fx = (long long)(g.n[0] + 1) * g.n[1] * g.n[2];
-  const long long fy = (long long)g.n[0] * (g.n[1] + 1) * g.n[2];
-  const long long fz = (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
-  for (int r = 0; r < 3; ++r) {
-    { PScope p(S, MHD_K_LAG_FACE); k_lag_face<T, 0><<<nblk(fx, 128), 128, 0, st>>>(g, S->sc, B.s, nv, B.lf[0]); }
-    { PScope p(S, MHD_K_LAG_FACE); k_lag_face<T, 1><<<nblk(fy, 128), 128, 0, st>>>(g, S->sc, B.s, nv, B.lf[1]); }
-    { PScope p(S, MHD_K_LAG_FACE); k_lag_face<T, 2><<<nblk(fz, 128), 128, 0, st>>>(g, S->sc, B.s, nv, B.lf[2]); }
-    { PScope p(S, MHD_K_LAG_UPDATE);
-      k_lag_update<T><<<nblk(g.N, 256), 256, 0, st>>>(g, S->ph, S->sc, B.s, B.s0, nv, B.lf[0], B.lf[1],
-                                                      B.lf[2], (T)RK_A[r], (T)RK_B[r], (T)RK_G[r]); }
-  }
-}
-
-template <typename T>
-void launch_step(mhd_sim* S, Buffers<T>& B) {
-  cudaStream_t st = S->stream;
-  { PScope p(S, MHD_K_SMALL); k_begin_step<<<1, 32, 0, st>>>(S->ph, S->sc); }
-  launch_euler_stage(S, B);
-  launch_lag_stage(S, B);
-  { PScope p(S, MHD_K_POST); k_post<T><<<nblk(S->g.N, 256), 256, 0, st>>>(S->g, S->ph, S->sc, B.s, 1, 1); }
-  { PScope p(S, MHD_K_SMALL); k_end_step<<<1, 32, 0, st>>>(S->sc); }
+void launch_sim_step(mhd_sim* S) {
+  if (S->precision)
+    launch_step(S->x32, S->stream);
+  else
+    launch_step(S->x64, S->stream);
 }
 
 int enqueue_step(mhd_sim* S) {
+  int rc = ensure_exec(S);
+  if (rc != MHD_OK) return rc;
   if (S->use_graph) {
     if (!S->graph_valid) {
       drop_graph(S);
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal));
-      if (S->precision)
-        launch_step(S, S->b32);
-      else
-        launch_step(S, S->b64);
+      launch_sim_step(S);
       cudaError_t e = cudaStreamEndCapture(S->stream, &graph);
       if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
       e = cudaGraphInstantiate(&S->gexec, graph, 0);
@@ -251,18 +155,17 @@ int enqueue_step(mhd_sim* S) {
     }
     CK(cudaGraphLaunch(S->gexec, S->stream));
   } else {
-    if (S->precision)
-      launch_step(S, S->b32);
-    else
-      launch_step(S, S->b64);
+    launch_sim_step(S);
     CK(cudaGetLastError());
   }
   return MHD_OK;
 }
 
 int set_params(mhd_sim* S, double cfl, double t_end, int fixed_tau, double tau) {
-  k_set_params<<<1, 32, 0, S->stream>>>(S->sc, cfl, t_end, fixed_tau, tau);
-  CK(cudaGetLastError());
+  int rc = ensure_exec(S);
+  if (rc != MHD_OK) return rc;
+  CK(S->precision ? launch_set_params(S->x32, S->stream, cfl, t_end, fixed_tau, tau)
+                  : launch_set_params(S->x64, S->stream, cfl, t_end, fixed_tau, tau));
   return MHD_OK;
 }
 
@@ -272,36 +175,14 @@ int read_scalars(mhd_sim* S) {
   return MHD_OK;
 }
 
-template <typename T>
-int launch_cfl(mhd_sim* S, Buffers<T>& B) {
-  CK(cudaMemsetAsync(&S->sc->dmax, 0, sizeof(unsigned long long), S->stream));
-  k_cfl<T><<<nblk(S->g.N, 256), 256, 0, S->stream>>>(S->g, S->ph, S->sc, B.s);
-  CK(cudaGetLastError());
+int refresh_cfl(mhd_sim* S) {
+  int rc = ensure_exec(S);
+  if (rc != MHD_OK) return rc;
+  CK(S->precision ? launch_cfl(S->x32, S->stream) : launch_cfl(S->x64, S->stream));
   return MHD_OK;
 }
-
-int refresh_cfl(mhd_sim* S) { return S->precision ? launch_cfl(S, S->b32) : launch_cfl(S, S->b64); }
 
 size_t dtype_size(int dt) { return dt == MHD_F32 ? 4 : 8; }
-
-template <typename T, typename In>
-int load_state(mhd_sim* S, Buffers<T>& B, const In* p[9]) {
-  const Geom& g = S->g;
-  k_load_cells<T, In><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s, p[0], p[1], p[2], p[3], p[4], p[8]);
-  k_faces_from_cells<T, In><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s, p[5], p[6], p[7]);
-  k_derive_eint<T><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s);
-  CK(cudaGetLastError());
-  return MHD_OK;
-}
-
-template <typename T, typename Out>
-int store_state(mhd_sim* S, Buffers<T>& B, Out* p[9]) {
-  const Geom& g = S->g;
-  k_store_state<T, Out><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s, p[0], p[1], p[2], p[3], p[4], p[5],
-                                                                p[6], p[7], p[8]);
-  CK(cudaGetLastError());
-  return MHD_OK;
-}
 
 int reset_scalars(mhd_sim* S) {
   CK(cudaMemsetAsync(S->sc, 0, sizeof(Scalars), S->stream));
@@ -393,6 +274,8 @@ void mhd_destroy(mhd_sim* S) {
   if (!S) return;
   if (S->stream) cudaStreamSynchronize(S->stream);
   drop_graph(S);
+  exec_free(S->x64);
+  exec_free(S->x32);
   if (S->pool) cudaFree(S->pool);
   if (S->staging) cudaFree(S->staging);
   if (S->sc) cudaFree(S->sc);
@@ -450,6 +333,7 @@ int mhd_set_option(mhd_sim* S, int key, double v) {
       return fail(MHD_EINVAL, "unknown option key " + std::to_string(key));
   }
   S->graph_valid = false;  // kernel arguments are baked into the captured graph
+  S->exec_valid = false;   // and the box descriptor into the executor
   return MHD_OK;
 }
 
@@ -487,13 +371,12 @@ int mhd_set_state(mhd_sim* S, const mhd_fields* in) {
   if (in->dtype == MHD_F64) {
     const double* p[9];
     for (int q = 0; q < 9; ++q) p[q] = (const double*)dev[q];
-    rc = S->precision ? load_state(S, S->b32, p) : load_state(S, S->b64, p);
+    CK(S->precision ? load_state(S, S->b32, p) : load_state(S, S->b64, p));
   } else {
     const float* p[9];
     for (int q = 0; q < 9; ++q) p[q] = (const float*)dev[q];
-    rc = S->precision ? load_state(S, S->b32, p) : load_state(S, S->b64, p);
+    CK(S->precision ? load_state(S, S->b32, p) : load_state(S, S->b64, p));
   }
-  if (rc != MHD_OK) return rc;
   if ((rc = reset_scalars(S)) != MHD_OK) return rc;
   if ((rc = refresh_cfl(S)) != MHD_OK) return rc;
   CK(cudaStreamSynchronize(S->stream));
@@ -515,15 +398,7 @@ int mhd_set_face_B(mhd_sim* S, const double* bx, const double* by, const double*
       dev[q] = dst;
     }
   }
-  const Geom& g = S->g;
-  if (S->precision) {
-    k_faces_copy<float><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, S->b32.s, dev[0], dev[1], dev[2]);
-    k_derive_eint<float><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, S->b32.s);
-  } else {
-    k_faces_copy<double><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, S->b64.s, dev[0], dev[1], dev[2]);
-    k_derive_eint<double><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, S->b64.s);
-  }
-  CK(cudaGetLastError());
+  CK(S->precision ? set_faces(S, S->b32, dev) : set_faces(S, S->b64, dev));
   int rc = refresh_cfl(S);
   if (rc != MHD_OK) return rc;
   CK(cudaStreamSynchronize(S->stream));
@@ -544,17 +419,15 @@ int mhd_get_state(mhd_sim* S, mhd_fields* out) {
     else
       dev[q] = out->on_device ? dst[q] : (void*)(S->staging + (size_t)q * S->g.N * 8);
   }
-  int rc;
   if (out->dtype == MHD_F64) {
     double* p[9];
     for (int q = 0; q < 9; ++q) p[q] = (double*)dev[q];
-    rc = S->precision ? store_state(S, S->b32, p) : store_state(S, S->b64, p);
+    CK(S->precision ? store_state(S, S->b32, p) : store_state(S, S->b64, p));
   } else {
     float* p[9];
     for (int q = 0; q < 9; ++q) p[q] = (float*)dev[q];
-    rc = S->precision ? store_state(S, S->b32, p) : store_state(S, S->b64, p);
+    CK(S->precision ? store_state(S, S->b32, p) : store_state(S, S->b64, p));
   }
-  if (rc != MHD_OK) return rc;
   if (!out->on_device)
     for (int q = 0; q < 9; ++q)
       if (dst[q]) CK(cudaMemcpyAsync(dst[q], dev[q], bytes, cudaMemcpyDeviceToHost, S->stream));
@@ -568,12 +441,7 @@ int mhd_get_full(mhd_sim* S, double* eint, double* bx, double* by, double* bz, i
   double* dst[4] = {eint, bx, by, bz};
   double* dev[4];
   for (int q = 0; q < 4; ++q) dev[q] = on_device ? dst[q] : (double*)(S->staging + q * bytes);
-  const Geom& g = S->g;
-  if (S->precision)
-    k_store_full<float><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, S->b32.s, dev[0], dev[1], dev[2], dev[3]);
-  else
-    k_store_full<double><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, S->b64.s, dev[0], dev[1], dev[2], dev[3]);
-  CK(cudaGetLastError());
+  CK(S->precision ? store_full(S, S->b32, dev) : store_full(S, S->b64, dev));
   if (!on_device)
     for (int q = 0; q < 4; ++q) CK(cudaMemcpyAsync(dst[q], dev[q], bytes, cudaMemcpyDeviceToHost, S->stream));
   CK(cudaStreamSynchronize(S->stream));
@@ -595,12 +463,7 @@ int mhd_set_full(mhd_sim* S, const double* eint, const double* bx, const double*
       dev[q] = d;
     }
   }
-  const Geom& g = S->g;
-  if (S->precision)
-    k_load_full<float><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, S->b32.s, dev[0], dev[1], dev[2], dev[3]);
-  else
-    k_load_full<double><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, S->b64.s, dev[0], dev[1], dev[2], dev[3]);
-  CK(cudaGetLastError());
+  CK(S->precision ? load_full(S, S->b32, dev) : load_full(S, S->b64, dev));
   int rc = refresh_cfl(S);
   if (rc != MHD_OK) return rc;
   CK(cudaStreamSynchronize(S->stream));
@@ -670,16 +533,16 @@ int mhd_stage(mhd_sim* S, int which, double tau) {
   int rc;
   if ((rc = set_params(S, 1.0, 0.0, 1, tau)) != MHD_OK) return rc;
   S->params_dirty = true;
-  k_begin_step<<<1, 32, 0, S->stream>>>(S->ph, S->sc);
-  const Geom& g = S->g;
   if (S->precision) {
-    if (which == 1) launch_euler_stage(S, S->b32);
-    if (which == 2) launch_lag_stage(S, S->b32);
-    if (which >= 3) k_post<float><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, S->ph, S->sc, S->b32.s, which == 3, which == 4);
+    launch_small(S->x32, S->stream, 0);
+    if (which == 1) launch_euler_stage(S->x32, S->stream);
+    if (which == 2) launch_lag_stage(S->x32, S->stream);
+    if (which >= 3) launch_post(S->x32, S->stream, which == 3, which == 4, 1);
   } else {
-    if (which == 1) launch_euler_stage(S, S->b64);
-    if (which == 2) launch_lag_stage(S, S->b64);
-    if (which >= 3) k_post<double><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, S->ph, S->sc, S->b64.s, which == 3, which == 4);
+    launch_small(S->x64, S->stream, 0);
+    if (which == 1) launch_euler_stage(S->x64, S->stream);
+    if (which == 2) launch_lag_stage(S->x64, S->stream);
+    if (which >= 3) launch_post(S->x64, S->stream, which == 3, which == 4, 1);
   }
   CK(cudaGetLastError());
   if ((rc = refresh_cfl(S)) != MHD_OK) return rc;
@@ -689,8 +552,9 @@ int mhd_stage(mhd_sim* S, int which, double tau) {
 
 int mhd_launches_per_step(mhd_sim* S) {
   if (!valid(S)) return fail(MHD_EINVAL, "mhd_launches_per_step: null sim");
-  // begin + 3 x (primitives, 3 faces, edges, update) + 3 x (3 faces, update) + post + end
-  return 1 + 3 * 6 + 3 * 4 + 1 + 1;
+  // begin + Q^n + 3 x (primitives, 3 faces, edges, update) + Q^n + 3 x (3 faces, update) + post
+  // + end
+  return 1 + 1 + 3 * 6 + 1 + 3 * 4 + 1 + 1;
 }
 
 int mhd_profile(mhd_sim* S, double cfl, int steps, double* out_ms, int64_t* out_launches) {
@@ -701,39 +565,30 @@ int mhd_profile(mhd_sim* S, double cfl, int steps, double* out_ms, int64_t* out_
   S->last_cfl = cfl;
   S->last_tend = 0.0;
   S->params_dirty = false;
-  S->profiling = true;
-  for (int k = 0; k < steps; ++k) {
-    if (S->precision)
-      launch_step(S, S->b32);
-    else
-      launch_step(S, S->b64);
-  }
-  S->profiling = false;
+  S->prof.on = true;
+  for (int k = 0; k < steps; ++k) launch_sim_step(S);
+  S->prof.on = false;
   cudaError_t e = cudaStreamSynchronize(S->stream);
   for (int c = 0; c < MHD_K_NCLASSES; ++c) {
     out_ms[c] = 0.0;
     out_launches[c] = 0;
   }
-  for (size_t q = 0; q < S->prof_cls.size(); ++q) {
+  for (size_t q = 0; q < S->prof.cls.size(); ++q) {
     float ms = 0.f;
-    if (e == cudaSuccess) cudaEventElapsedTime(&ms, S->prof_ev[2 * q], S->prof_ev[2 * q + 1]);
-    out_ms[S->prof_cls[q]] += ms;
-    out_launches[S->prof_cls[q]] += 1;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, S->prof.ev[2 * q], S->prof.ev[2 * q + 1]);
+    out_ms[report_class(S->prof.cls[q])] += ms;
+    out_launches[report_class(S->prof.cls[q])] += 1;
   }
-  for (cudaEvent_t ev : S->prof_ev) cudaEventDestroy(ev);
-  S->prof_ev.clear();
-  S->prof_cls.clear();
+  for (cudaEvent_t ev : S->prof.ev) cudaEventDestroy(ev);
+  S->prof.ev.clear();
+  S->prof.cls.clear();
   if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("mhd_profile: ") + cudaGetErrorString(e));
   return mhd_sync(S);
 }
 
 int mhd_diagnostics(mhd_sim* S, mhd_diag* out) {
   if (!valid(S) || !out) return fail(MHD_EINVAL, "mhd_diagnostics: null argument");
-  const Geom& g = S->g;
-  if (S->precision)
-    k_diag_partial<float><<<S->diag_blocks, DIAG_THREADS, 0, S->stream>>>(g, S->b32.s, S->diag_part);
-  else
-    k_diag_partial<double><<<S->diag_blocks, DIAG_THREADS, 0, S->stream>>>(g, S->b64.s, S->diag_part);
+  CK(S->precision ? diag_partial(S, S->b32) : diag_partial(S, S->b64));
   k_diag_final<<<1, DIAG_THREADS, 0, S->stream>>>(S->diag_part, S->diag_blocks, S->diag_out);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(S->diag_host, S->diag_out, 9 * sizeof(double), cudaMemcpyDeviceToHost, S->stream));
@@ -754,6 +609,322 @@ int mhd_diagnostics(mhd_sim* S, mhd_diag* out) {
   out->vel_branch = (int64_t)S->sc_host->vel_branch;
   out->error_flags = S->sc_host->flags;
   return MHD_OK;
+}
+
+}  // extern "C"
+
+// ================================================================================================
+// Batches: many boxes, one launch per kernel class
+struct mhd_batch {
+  std::vector<mhd_sim*> sims;
+  int precision = 0;
+  cudaStream_t stream = nullptr;
+  Exec<double> x64;
+  Exec<float> x32;
+  Profiler prof;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_valid = false;
+  double last_cfl = -1.0;
+};
+
+namespace {
+
+void batch_drop_graph(mhd_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  b->graph_valid = false;
+}
+
+template <typename T>
+Exec<T>& bexec(mhd_batch* b);
+template <>
+Exec<double>& bexec<double>(mhd_batch* b) { return b->x64; }
+template <>
+Exec<float>& bexec<float>(mhd_batch* b) { return b->x32; }
+
+template <typename T>
+const Box<T>& sim_box(mhd_sim* S);
+template <>
+const Box<double>& sim_box<double>(mhd_sim* S) { return S->b64; }
+template <>
+const Box<float>& sim_box<float>(mhd_sim* S) { return S->b32; }
+
+template <typename T>
+int batch_init(mhd_batch* b) {
+  std::vector<Box<T>> boxes;
+  for (mhd_sim* S : b->sims) boxes.push_back(sim_box<T>(S));
+  Exec<T>& X = bexec<T>(b);
+  X.prof = &b->prof;
+  cudaError_t e = exec_init(X, boxes);
+  if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+  return MHD_OK;
+}
+
+template <typename T>
+void batch_launch_step(mhd_batch* b) {
+  launch_step(bexec<T>(b), b->stream);
+}
+
+int batch_enqueue(mhd_batch* b) {
+  if (!b->graph_valid) {
+    batch_drop_graph(b);
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    if (b->precision)
+      batch_launch_step<float>(b);
+    else
+      batch_launch_step<double>(b);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    b->graph_valid = true;
+  }
+  CK(cudaGraphLaunch(b->gexec, b->stream));
+  return MHD_OK;
+}
+
+int batch_set_params(mhd_batch* b, double cfl) {
+  if (cfl != b->last_cfl) {
+    CK(b->precision ? launch_set_params(b->x32, b->stream, cfl, 0.0, 0, 0.0)
+                    : launch_set_params(b->x64, b->stream, cfl, 0.0, 0, 0.0));
+    b->last_cfl = cfl;
+  }
+  for (mhd_sim* S : b->sims) S->params_dirty = true;  // members' cached parameters are stale
+  return MHD_OK;
+}
+
+// state snapshot of every member (10 state arrays into its staging buffer, scalars on the host)
+template <typename T>
+int batch_snapshot(mhd_batch* b, std::vector<Scalars>& sc, bool restore) {
+  sc.resize(b->sims.size());
+  for (size_t i = 0; i < b->sims.size(); ++i) {
+    mhd_sim* S = b->sims[i];
+    const Box<T>& B = sim_box<T>(S);
+    T* arrs[10] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2, B.s.b[0], B.s.b[1], B.s.b[2]};
+    const size_t bytes = (size_t)S->g.N * sizeof(T);
+    for (int q = 0; q < 10; ++q) {
+      char* snap = S->staging + (size_t)q * S->g.N * 8;
+      if (restore)
+        CK(cudaMemcpyAsync(arrs[q], snap, bytes, cudaMemcpyDeviceToDevice, b->stream));
+      else
+        CK(cudaMemcpyAsync(snap, arrs[q], bytes, cudaMemcpyDeviceToDevice, b->stream));
+    }
+    if (restore)
+      CK(cudaMemcpyAsync(S->sc, &sc[i], sizeof(Scalars), cudaMemcpyHostToDevice, b->stream));
+    else
+      CK(cudaMemcpyAsync(&sc[i], S->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+  }
+  return MHD_OK;
+}
+
+// run `steps` launched steps with event pairs; per-tag milliseconds
+template <typename T>
+int batch_timed(mhd_batch* b, int steps, std::vector<double>& ms_per_tag, std::vector<long long>& n_per_tag) {
+  Exec<T>& X = bexec<T>(b);
+  b->prof.on = true;
+  for (int k = 0; k < steps; ++k) launch_step(X, b->stream);
+  b->prof.on = false;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  ms_per_tag.assign(PROF_KC_BASE + NKC, 0.0);
+  n_per_tag.assign(PROF_KC_BASE + NKC, 0);
+  for (size_t q = 0; q < b->prof.cls.size(); ++q) {
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, b->prof.ev[2 * q], b->prof.ev[2 * q + 1]);
+    ms_per_tag[b->prof.cls[q]] += ms;
+    n_per_tag[b->prof.cls[q]] += 1;
+  }
+  for (cudaEvent_t ev : b->prof.ev) cudaEventDestroy(ev);
+  b->prof.ev.clear();
+  b->prof.cls.clear();
+  if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("batch timing: ") + cudaGetErrorString(e));
+  return MHD_OK;
+}
+
+bool is_face_class(int kc) { return kc == KC_EFACE || kc == KC_LFACE; }
+
+template <typename T>
+int batch_tune(mhd_batch* b, double cfl, int reps, double* best_ms) {
+  Exec<T>& X = bexec<T>(b);
+  std::vector<Scalars> snap;
+  int rc = batch_snapshot<T>(b, snap, false);
+  if (rc != MHD_OK) return rc;
+  const int face_blocks[3] = {64, 128, 256}, cell_blocks[3] = {128, 256, 512}, mults[3] = {0, 4, 16};
+  double best[NKC];
+  LaunchCfg bestc[NKC];
+  for (int kc = 0; kc < NKC; ++kc) {
+    best[kc] = 1e300;
+    bestc[kc] = X.cfg[kc];
+  }
+  std::vector<double> ms;
+  std::vector<long long> nl;
+  for (int bi = 0; bi < 3; ++bi)
+    for (int mi = 0; mi < 3; ++mi) {
+      for (int kc = 0; kc < NKC; ++kc) X.cfg[kc] = LaunchCfg{is_face_class(kc) ? face_blocks[bi] : cell_blocks[bi], mults[mi]};
+      cudaError_t e = ensure_tables(X);
+      if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("tile tables: ") + cudaGetErrorString(e));
+      if ((rc = batch_snapshot<T>(b, snap, true)) != MHD_OK) return rc;
+      CK(launch_set_params(X, b->stream, cfl, 0.0, 0, 0.0));
+      if ((rc = batch_timed<T>(b, reps, ms, nl)) != MHD_OK) return rc;
+      for (int kc = 0; kc < NKC; ++kc)
+        if (ms[PROF_KC_BASE + kc] < best[kc]) {
+          best[kc] = ms[PROF_KC_BASE + kc];
+          bestc[kc] = X.cfg[kc];
+        }
+    }
+  for (int kc = 0; kc < NKC; ++kc) X.cfg[kc] = bestc[kc];
+  cudaError_t e = ensure_tables(X);
+  if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("tile tables: ") + cudaGetErrorString(e));
+  if (best_ms) {
+    double tot = 0.0;
+    for (int kc = 0; kc < NKC; ++kc) tot += best[kc];
+    *best_ms = tot / reps;
+  }
+  if ((rc = batch_snapshot<T>(b, snap, true)) != MHD_OK) return rc;
+  b->last_cfl = -1.0;
+  batch_drop_graph(b);
+  return MHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mhd_batch* mhd_batch_create(mhd_sim* const* sims, int n) {
+  if (!sims || n < 1) {
+    fail(MHD_EINVAL, "mhd_batch_create: need at least one sim");
+    return nullptr;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!valid(sims[i]) || !sims[i]->has_state) {
+      fail(MHD_EINVAL, "mhd_batch_create: every sim needs a loaded state");
+      return nullptr;
+    }
+    if (sims[i]->precision != sims[0]->precision || sims[i]->device != sims[0]->device) {
+      fail(MHD_EINVAL, "mhd_batch_create: sims differ in precision or device");
+      return nullptr;
+    }
+  }
+  mhd_batch* b = new (std::nothrow) mhd_batch();
+  if (!b) {
+    fail(MHD_ENOMEM, "mhd_batch_create: host allocation failed");
+    return nullptr;
+  }
+  b->precision = sims[0]->precision;
+  for (int i = 0; i < n; ++i) {
+    if (ensure_exec(sims[i]) != MHD_OK || cudaStreamSynchronize(sims[i]->stream) != cudaSuccess) {
+      fail(MHD_ECUDA, "mhd_batch_create: member not ready");
+      delete b;
+      return nullptr;
+    }
+    b->sims.push_back(sims[i]);
+  }
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    fail(MHD_ECUDA, "mhd_batch_create: stream");
+    delete b;
+    return nullptr;
+  }
+  int rc = b->precision ? batch_init<float>(b) : batch_init<double>(b);
+  if (rc != MHD_OK) {
+    mhd_batch_destroy(b);
+    return nullptr;
+  }
+  for (mhd_sim* S : b->sims) S->batched += 1;
+  return b;
+}
+
+void mhd_batch_destroy(mhd_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  exec_free(b->x64);
+  exec_free(b->x32);
+  for (mhd_sim* S : b->sims) S->batched -= 1;
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+int mhd_batch_step(mhd_batch* b, double cfl) {
+  if (!b) return fail(MHD_EINVAL, "mhd_batch_step: null batch");
+  if (!(cfl > 0.0)) return fail(MHD_EINVAL, "mhd_batch_step: cfl must be > 0");
+  int rc = batch_set_params(b, cfl);
+  if (rc != MHD_OK) return rc;
+  return batch_enqueue(b);
+}
+
+int mhd_batch_sync(mhd_batch* b) {
+  if (!b) return fail(MHD_EINVAL, "mhd_batch_sync: null batch");
+  CK(cudaStreamSynchronize(b->stream));
+  int bad = 0;
+  for (mhd_sim* S : b->sims) {
+    CK(cudaMemcpy(S->sc_host, S->sc, sizeof(Scalars), cudaMemcpyDeviceToHost));
+    if (S->sc_host->flags & 1) bad = 1;
+  }
+  if (bad) return fail(MHD_ENONPHYS, "non-physical state in a batch member");
+  return MHD_OK;
+}
+
+int mhd_batch_tune(mhd_batch* b, double cfl, int reps, double* best_ms) {
+  if (!b || reps < 1 || !(cfl > 0.0)) return fail(MHD_EINVAL, "mhd_batch_tune: bad argument");
+  CK(cudaStreamSynchronize(b->stream));
+  return b->precision ? batch_tune<float>(b, cfl, reps, best_ms) : batch_tune<double>(b, cfl, reps, best_ms);
+}
+
+static int kc_of_profile_class(int cls) {
+  for (int kc = 0; kc < NKC; ++kc)
+    if (profile_class(kc) == cls) return kc;
+  return -1;
+}
+
+int mhd_batch_get_shape(mhd_batch* b, int cls, int* block, int* grid_mult) {
+  int kc = kc_of_profile_class(cls);
+  if (!b || kc < 0 || !block || !grid_mult) return fail(MHD_EINVAL, "mhd_batch_get_shape: bad argument");
+  const LaunchCfg& c = b->precision ? b->x32.cfg[kc] : b->x64.cfg[kc];
+  *block = c.block;
+  *grid_mult = c.grid_mult;
+  return MHD_OK;
+}
+
+int mhd_batch_set_shape(mhd_batch* b, int cls, int block, int grid_mult) {
+  int kc = kc_of_profile_class(cls);
+  if (!b || kc < 0) return fail(MHD_EINVAL, "mhd_batch_set_shape: bad kernel class");
+  if ((block != 64 && block != 128 && block != 256 && block != 512) || grid_mult < 0)
+    return fail(MHD_EINVAL, "mhd_batch_set_shape: block in {64, 128, 256, 512}, grid_mult >= 0");
+  if (is_face_class(kc) && block > 256) return fail(MHD_EINVAL, "face kernels take at most 256 threads");
+  CK(cudaStreamSynchronize(b->stream));
+  cudaError_t e;
+  if (b->precision) {
+    b->x32.cfg[kc] = LaunchCfg{block, grid_mult};
+    e = ensure_tables(b->x32);
+  } else {
+    b->x64.cfg[kc] = LaunchCfg{block, grid_mult};
+    e = ensure_tables(b->x64);
+  }
+  if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("tile tables: ") + cudaGetErrorString(e));
+  batch_drop_graph(b);
+  return MHD_OK;
+}
+
+int mhd_batch_profile(mhd_batch* b, double cfl, int steps, double* out_ms, int64_t* out_launches) {
+  if (!b || steps < 1 || !out_ms || !out_launches) return fail(MHD_EINVAL, "mhd_batch_profile: bad argument");
+  int rc = batch_set_params(b, cfl);
+  if (rc != MHD_OK) return rc;
+  std::vector<double> ms;
+  std::vector<long long> nl;
+  rc = b->precision ? batch_timed<float>(b, steps, ms, nl) : batch_timed<double>(b, steps, ms, nl);
+  if (rc != MHD_OK) return rc;
+  for (int c = 0; c < MHD_K_NCLASSES; ++c) {
+    out_ms[c] = 0.0;
+    out_launches[c] = 0;
+  }
+  for (int tag = 0; tag < (int)ms.size(); ++tag) {
+    if (nl[tag] == 0) continue;
+    out_ms[report_class(tag)] += ms[tag];
+    out_launches[report_class(tag)] += nl[tag];
+  }
+  return mhd_batch_sync(b);
 }
 
 }  // extern "C"

@@ -6,6 +6,11 @@
 
 namespace mhd {
 
+// SSP-RK3 (Sec. 2.2): Q = a Q^n + b Q + g tau R for the substages r = 0, 1, 2
+__host__ __device__ __forceinline__ double RK3_A(int r) { return r == 0 ? 0.0 : (r == 1 ? 0.75 : 1.0 / 3.0); }
+__host__ __device__ __forceinline__ double RK3_B(int r) { return r == 0 ? 1.0 : (r == 1 ? 0.25 : 2.0 / 3.0); }
+__host__ __device__ __forceinline__ double RK3_G(int r) { return r == 0 ? 1.0 : (r == 1 ? 0.25 : 2.0 / 3.0); }
+
 // primitives W of every cell: v (3), cell-centred B (3), p, gamma, sqrt(rho)   [Sec. 2 closure,
 // Sec. 2.5 centring of B, Sec. 4.3 gamma_eff]
 template <typename T>
@@ -24,54 +29,90 @@ struct FaceOut {
 };
 
 // ------------------------------------------------------------------------------------------------
+// Batched execution.  Every step kernel walks a table of tiles; a tile is blockDim.x consecutive
+// elements (cells, faces of one direction, or lattice points) of one box, so a warp never spans
+// two boxes.  Grid-stride over tiles: a grid smaller than the tile count makes the launch
+// persistent.  A single simulation is a table of one box.
 template <typename T>
-__global__ void __launch_bounds__(256) k_prim(Geom g, Phys ph, State<T> s, Prim<T> w) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= g.N) return;
-  int i = (int)(c % g.n[0]);
-  long long r = c / g.n[0];
-  int j = (int)(r % g.n[1]);
-  int k = (int)(r / g.n[1]);
-  T rho = s.rho[c];
-  long long up[3] = {cmap(g, i + 1, j, k), cmap(g, i, j + 1, k), cmap(g, i, j, k + 1)};
+struct Box {
+  Geom g;
+  Phys ph;
+  Scalars* sc;
+  State<T> s, s0;
+  Prim<T> w;
+  FaceOut<T> fo[3];  // Eulerian face outputs; the Lagrangian fluxes reuse fo[d].f[0..6]
+  T* e[3];
+  int nv;            // advected fields of the Lagrangian stage (6, or 7 with rho_H2)
+};
+
+struct Tiles {
+  const int* box;    // box of tile t
+  const int* start;  // first element of tile t inside its box
+  int n;             // number of tiles
+};
+
+// domains of the tile tables
+enum { DOM_CELLS = 0, DOM_FACE_X = 1, DOM_FACE_Y = 2, DOM_FACE_Z = 3, DOM_LATTICE = 4, NDOM = 5 };
+
+// decode a cell index / a face index of direction D / a lattice index
+__device__ __forceinline__ void decode(long long t, int e0, int e1, int c[3]) {
+  c[0] = (int)(t % e0);
+  long long r = t / e0;
+  c[1] = (int)(r % e1);
+  c[2] = (int)(r / e1);
+}
+
+#define MHD_TILE_LOOP(tl) for (int t_ = blockIdx.x; t_ < (tl).n; t_ += gridDim.x)
+
+// ------------------------------------------------------------------------------------------------
+// primitives of one cell
+template <typename T>
+__device__ __forceinline__ void prim_cell(const Box<T>& B, long long c) {
+  const Geom& g = B.g;
+  int q[3];
+  decode(c, g.n[0], g.n[1], q);
+  T rho = B.s.rho[c];
+  long long up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
 #pragma unroll
-  for (int d = 0; d < 3; ++d) w.B[d][c] = T(0.5) * (s.b[d][c] + s.b[d][up[d]]);
-  double gm = ph.chem ? gamma_eff((double)rho, (double)s.rh2[c]) : ph.gamma;
+  for (int d = 0; d < 3; ++d) B.w.B[d][c] = T(0.5) * (B.s.b[d][c] + B.s.b[d][up[d]]);
+  double gm = B.ph.chem ? gamma_eff((double)rho, (double)B.s.rh2[c]) : B.ph.gamma;
   T gmt = (T)gm;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) w.v[d][c] = s.m[d][c] / rho;
-  w.p[c] = (gmt - T(1)) * s.eint[c];
-  w.g[c] = gmt;
-  w.sr[c] = sqrt(rho);
+  for (int d = 0; d < 3; ++d) B.w.v[d][c] = B.s.m[d][c] / rho;
+  B.w.p[c] = (gmt - T(1)) * B.s.eint[c];
+  B.w.g[c] = gmt;
+  B.w.sr[c] = sqrt(rho);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) kb_prim(const Box<T>* __restrict__ boxes, Tiles tl) {
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    long long c = (long long)tl.start[t_] + threadIdx.x;
+    if (c < B.g.N) prim_cell(B, c);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
-// Eulerian face kernel for direction D: the face i_D - 1/2 between cells i_D - 1 and i_D, for
-// i_D in [0, n_D] and the other two indices in [0, n).
+// Eulerian face of direction D: the face i_D - 1/2 between cells i_D - 1 and i_D, for i_D in
+// [0, n_D] and the other two indices in [0, n).
 template <typename T, int D>
-__global__ void __launch_bounds__(128) k_euler_face(Geom g, Scalars* sc, State<T> s, Prim<T> w,
-                                                   FaceOut<T> fo) {
+__device__ __forceinline__ void euler_face(const Box<T>& B, long long t) {
   constexpr int D1 = (D + 1) % 3, D2 = (D + 2) % 3;
+  const Geom& g = B.g;
   int ext[3] = {g.n[0], g.n[1], g.n[2]};
   ext[D] += 1;
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long total = (long long)ext[0] * ext[1] * ext[2];
-  if (t >= total) return;
   int c[3];
-  c[0] = (int)(t % ext[0]);
-  long long r = t / ext[0];
-  c[1] = (int)(r % ext[1]);
-  c[2] = (int)(r / ext[1]);
-  const T tau_h = (T)sc->tau_h;
-  // stencil cells i_D - 3 .. i_D + 2 along D
-  long long cell[6];
+  decode(t, ext[0], ext[1], c);
+  const T tau_h = (T)B.sc->tau_h;
+  long long cell[6];  // stencil cells i_D - 3 .. i_D + 2 along D
 #pragma unroll
   for (int o = 0; o < 6; ++o) {
     int cc[3] = {c[0], c[1], c[2]};
     cc[D] += o - 3;
     cell[o] = cmap(g, cc[0], cc[1], cc[2]);
   }
-  const T* qv[6] = {w.v[D], w.v[D1], w.v[D2], w.B[D1], w.B[D2], w.p};
+  const T* qv[6] = {B.w.v[D], B.w.v[D1], B.w.v[D2], B.w.B[D1], B.w.B[D2], B.w.p};
   Para<T> pl[6], pr[6];
 #pragma unroll
   for (int v = 0; v < 6; ++v) {
@@ -81,15 +122,16 @@ __global__ void __launch_bounds__(128) k_euler_face(Geom g, Scalars* sc, State<T
     pr[v] = ppm(q1, q2, q3, q4, q5);
   }
   long long cl = cell[2], cr = cell[3];
-  T wl[6] = {s.rho[cl], w.p[cl], w.g[cl], w.B[D1][cl], w.B[D2][cl], w.sr[cl]};
-  T wr[6] = {s.rho[cr], w.p[cr], w.g[cr], w.B[D1][cr], w.B[D2][cr], w.sr[cr]};
-  T Bn = s.b[D][cr];  // face i_D - 1/2 is stored with cell i_D (mapped: the nearest stored face)
+  T wl[6] = {B.s.rho[cl], B.w.p[cl], B.w.g[cl], B.w.B[D1][cl], B.w.B[D2][cl], B.w.sr[cl]};
+  T wr[6] = {B.s.rho[cr], B.w.p[cr], B.w.g[cr], B.w.B[D1][cr], B.w.B[D2][cr], B.w.sr[cr]};
+  T Bn = B.s.b[D][cr];  // face i_D - 1/2 is stored with cell i_D (mapped: the nearest stored face)
   T qs[6];
   riemann(wl, wr, Bn, pl, pr, tau_h, qs);
   // A12: non-advective fluxes from the face solution (V_n, V_t1, V_t2, B_t1, B_t2, P)
   T Vn = qs[0], Vt1 = qs[1], Vt2 = qs[2], Bt1 = qs[3], Bt2 = qs[4], P = qs[5];
   T pstar = P + T(0.5) * (Bn * Bn + Bt1 * Bt1 + Bt2 * Bt2);
   long long f = fidx(g, c[0], c[1], c[2]);
+  const FaceOut<T>& fo = B.fo[D];
   fo.f[0][f] = pstar - Bn * Bn;
   fo.f[1][f] = -(Bn * Bt1);
   fo.f[2][f] = -(Bn * Bt2);
@@ -99,63 +141,68 @@ __global__ void __launch_bounds__(128) k_euler_face(Geom g, Scalars* sc, State<T
   fo.f[6][f] = Bt2 * Vn - Bn * Vt2;  // E along t1
 }
 
+template <typename T, int D>
+__global__ void __launch_bounds__(256) kb_euler_face(const Box<T>* __restrict__ boxes, Tiles tl) {
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    long long t = (long long)tl.start[t_] + threadIdx.x;
+    long long total = (long long)(B.g.n[0] + (D == 0)) * (B.g.n[1] + (D == 1)) * (B.g.n[2] + (D == 2));
+    if (t < total) euler_face<T, D>(B, t);
+  }
+}
+
 // App. C: edge EMFs.  E_d at the corner (i_{d+1} - 1/2, i_{d+2} - 1/2) of lattice point c, for
 // c_d in [0, n_d) and c_{d+1}, c_{d+2} in [0, n]: the mean of the two faces of direction d+1 and
 // the two of direction d+2 that share the edge.
 template <typename T>
-__global__ void __launch_bounds__(256) k_edges(Geom g, FaceOut<T> fx, FaceOut<T> fy, FaceOut<T> fz,
-                                              T* ex, T* ey, T* ez) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= g.NF) return;
+__device__ __forceinline__ void edges_point(const Box<T>& B, long long t) {
+  const Geom& g = B.g;
   int c[3];
-  c[0] = (int)(t % (g.n[0] + 1));
-  long long r = t / (g.n[0] + 1);
-  c[1] = (int)(r % (g.n[1] + 1));
-  c[2] = (int)(r / (g.n[1] + 1));
-  const FaceOut<T>* F[3] = {&fx, &fy, &fz};
-  T* E[3] = {ex, ey, ez};
+  decode(t, g.n[0] + 1, g.n[1] + 1, c);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
     if (c[d] >= g.n[d]) continue;
-    // faces of direction d1: normal index c[d1] (stored 0..n), transverse indices mapped
     int a[3] = {c[0], c[1], c[2]};
     a[d2] = wrap(c[d2], g.n[d2], g.bc[d2]);
     int alo[3] = {c[0], c[1], c[2]};
     alo[d2] = wrap(c[d2] - 1, g.n[d2], g.bc[d2]);
-    T f1 = F[d1]->f[5][fidx(g, alo[0], alo[1], alo[2])] + F[d1]->f[5][fidx(g, a[0], a[1], a[2])];
+    T f1 = B.fo[d1].f[5][fidx(g, alo[0], alo[1], alo[2])] + B.fo[d1].f[5][fidx(g, a[0], a[1], a[2])];
     int b[3] = {c[0], c[1], c[2]};
     b[d1] = wrap(c[d1], g.n[d1], g.bc[d1]);
     int blo[3] = {c[0], c[1], c[2]};
     blo[d1] = wrap(c[d1] - 1, g.n[d1], g.bc[d1]);
-    T f2 = F[d2]->f[6][fidx(g, blo[0], blo[1], blo[2])] + F[d2]->f[6][fidx(g, b[0], b[1], b[2])];
-    E[d][t] = T(0.25) * (f1 + f2);
+    T f2 = B.fo[d2].f[6][fidx(g, blo[0], blo[1], blo[2])] + B.fo[d2].f[6][fidx(g, b[0], b[1], b[2])];
+    B.e[d][t] = T(0.25) * (f1 + f2);
   }
 }
 
-// Eulerian update of every cell: finite-volume R of m, rho E, rho eps (Sec. 2.4 + A12), Flux-CT of
-// the cell's three faces (Sec. 2.5), SSP-RK3 combination (Sec. 2.2).
 template <typename T>
-__global__ void __launch_bounds__(256) k_euler_update(Geom g, Phys ph, Scalars* sc, State<T> s,
-                                                      State<T> s0, Prim<T> w, FaceOut<T> fx,
-                                                      FaceOut<T> fy, FaceOut<T> fz, const T* ex,
-                                                      const T* ey, const T* ez, T a, T bb, T gg) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= g.N) return;
-  int i = (int)(c % g.n[0]);
-  long long r = c / g.n[0];
-  int j = (int)(r % g.n[1]);
-  int k = (int)(r / g.n[1]);
-  const T tau = (T)sc->tau;
-  const T ih = (T)ph.ih;
-  const FaceOut<T>* F[3] = {&fx, &fy, &fz};
-  long long f0 = fidx(g, i, j, k);
-  long long fup[3] = {fidx(g, i + 1, j, k), fidx(g, i, j + 1, k), fidx(g, i, j, k + 1)};
+__global__ void __launch_bounds__(512) kb_edges(const Box<T>* __restrict__ boxes, Tiles tl) {
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    long long t = (long long)tl.start[t_] + threadIdx.x;
+    if (t < B.g.NF) edges_point(B, t);
+  }
+}
+
+// Eulerian update of one cell: finite-volume R of m, rho E, rho eps (Sec. 2.4 + A12), Flux-CT of
+// the cell's three faces (Sec. 2.5), SSP-RK3 combination (Sec. 2.2) with stage r.
+template <typename T>
+__device__ __forceinline__ void euler_update_cell(const Box<T>& B, long long c, int r) {
+  const Geom& g = B.g;
+  int q[3];
+  decode(c, g.n[0], g.n[1], q);
+  const T a = (T)RK3_A(r), bb = (T)RK3_B(r), gg = (T)RK3_G(r);
+  const T tau = (T)B.sc->tau;
+  const T ih = (T)B.ph.ih;
+  long long f0 = fidx(g, q[0], q[1], q[2]);
+  long long fup[3] = {fidx(g, q[0] + 1, q[1], q[2]), fidx(g, q[0], q[1] + 1, q[2]), fidx(g, q[0], q[1], q[2] + 1)};
   T acc[5] = {T(0), T(0), T(0), T(0), T(0)};  // m_x, m_y, m_z, rho E, -h div V
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-    const FaceOut<T>& o = *F[d];
+    const FaceOut<T>& o = B.fo[d];
     acc[d] = acc[d] + (o.f[0][f0] - o.f[0][fup[d]]);
     acc[d1] = acc[d1] + (o.f[1][f0] - o.f[1][fup[d]]);
     acc[d2] = acc[d2] + (o.f[2][f0] - o.f[2][fup[d]]);
@@ -165,44 +212,41 @@ __global__ void __launch_bounds__(256) k_euler_update(Geom g, Phys ph, Scalars* 
   T Rv[5];
 #pragma unroll
   for (int v = 0; v < 4; ++v) Rv[v] = acc[v] * ih;
-  Rv[4] = ((w.g[c] - T(1)) * s.eint[c]) * (acc[4] * ih);  // -(gamma - 1) rho eps div V
-  T* q[5] = {s.m[0], s.m[1], s.m[2], s.E, s.eint};
-  T* q0[5] = {s0.m[0], s0.m[1], s0.m[2], s0.E, s0.eint};
+  Rv[4] = ((B.w.g[c] - T(1)) * B.s.eint[c]) * (acc[4] * ih);  // -(gamma - 1) rho eps div V
+  T* qq[5] = {B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint};
+  T* q0[5] = {B.s0.m[0], B.s0.m[1], B.s0.m[2], B.s0.E, B.s0.eint};
 #pragma unroll
-  for (int v = 0; v < 5; ++v) q[v][c] = (a * q0[v][c] + bb * q[v][c]) + gg * (tau * Rv[v]);
+  for (int v = 0; v < 5; ++v) qq[v][c] = (a * q0[v][c] + bb * qq[v][c]) + gg * (tau * Rv[v]);
   // Flux-CT: d b_d / dt = -(curl E)_d on the face i_d - 1/2 of this cell
-  const T* E[3] = {ex, ey, ez};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-    T curl = (E[d1][fup[d2]] - E[d1][f0]) - (E[d2][fup[d1]] - E[d2][f0]);
+    T curl = (B.e[d1][fup[d2]] - B.e[d1][f0]) - (B.e[d2][fup[d1]] - B.e[d2][f0]);
     T Rb = curl * ih;
-    s.b[d][c] = (a * s0.b[d][c] + bb * s.b[d][c]) + gg * (tau * Rb);
+    B.s.b[d][c] = (a * B.s0.b[d][c] + bb * B.s.b[d][c]) + gg * (tau * Rb);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) kb_euler_update(const Box<T>* __restrict__ boxes, Tiles tl, int r) {
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    long long c = (long long)tl.start[t_] + threadIdx.x;
+    if (c < B.g.N) euler_update_cell(B, c, r);
   }
 }
 
 // ------------------------------------------------------------------------------------------------
 // Sec. 2.6 Lagrangian face flux for direction D: F = v_n q(-|v_n| tau) (v_n >= 0, left cell) or
 // v_n q(|v_n| tau) (right cell) with v_n the sqrt(rho)-weighted mean of the cell velocities.
-template <typename T>
-struct LagFlux {
-  T* f[7];
-};
-
 template <typename T, int D>
-__global__ void __launch_bounds__(128) k_lag_face(Geom g, Scalars* sc, State<T> s, int nv,
-                                                 LagFlux<T> fl) {
+__device__ __forceinline__ void lag_face(const Box<T>& B, long long t) {
+  const Geom& g = B.g;
   int ext[3] = {g.n[0], g.n[1], g.n[2]};
   ext[D] += 1;
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long total = (long long)ext[0] * ext[1] * ext[2];
-  if (t >= total) return;
   int c[3];
-  c[0] = (int)(t % ext[0]);
-  long long r = t / ext[0];
-  c[1] = (int)(r % ext[1]);
-  c[2] = (int)(r / ext[1]);
-  const T tau_h = (T)sc->tau_h;
+  decode(t, ext[0], ext[1], c);
+  const T tau_h = (T)B.sc->tau_h;
   long long cell[6];
 #pragma unroll
   for (int o = 0; o < 6; ++o) {
@@ -211,45 +255,83 @@ __global__ void __launch_bounds__(128) k_lag_face(Geom g, Scalars* sc, State<T> 
     cell[o] = cmap(g, cc[0], cc[1], cc[2]);
   }
   long long cl = cell[2], cr = cell[3];
-  T rl = s.rho[cl], rr = s.rho[cr];
-  T vl = s.m[D][cl] / rl, vr = s.m[D][cr] / rr;
+  T rl = B.s.rho[cl], rr = B.s.rho[cr];
+  T vl = B.s.m[D][cl] / rl, vr = B.s.m[D][cr] / rr;
   T sl = sqrt(rl), sr = sqrt(rr);
   T vn = (vl * sl + vr * sr) / (sl + sr);
   T y = fabs(vn) * tau_h;
-  const T* q[7] = {s.rho, s.m[0], s.m[1], s.m[2], s.E, s.eint, s.rh2};
+  const T* q[7] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2};
   long long f = fidx(g, c[0], c[1], c[2]);
   const int o0 = vn >= T(0) ? 0 : 1;  // upwind cell: stencil cells o0 .. o0 + 4
+  const int nv = B.nv;
   for (int v = 0; v < nv; ++v) {
     const T* a = q[v];
     Para<T> P = ppm(a[cell[o0]], a[cell[o0 + 1]], a[cell[o0 + 2]], a[cell[o0 + 3]], a[cell[o0 + 4]]);
     T qb = o0 == 0 ? avg_right_end(P, y) : avg_left_end(P, y);
-    fl.f[v][f] = vn * qb;
+    B.fo[D].f[v][f] = vn * qb;
+  }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) kb_lag_face(const Box<T>* __restrict__ boxes, Tiles tl) {
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    long long t = (long long)tl.start[t_] + threadIdx.x;
+    long long total = (long long)(B.g.n[0] + (D == 0)) * (B.g.n[1] + (D == 1)) * (B.g.n[2] + (D == 2));
+    if (t < total) lag_face<T, D>(B, t);
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_lag_update(Geom g, Phys ph, Scalars* sc, State<T> s,
-                                                    State<T> s0, int nv, LagFlux<T> fx,
-                                                    LagFlux<T> fy, LagFlux<T> fz, T a, T bb, T gg) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= g.N) return;
-  int i = (int)(c % g.n[0]);
-  long long r = c / g.n[0];
-  int j = (int)(r % g.n[1]);
-  int k = (int)(r / g.n[1]);
-  const T tau = (T)sc->tau;
-  const T ih = (T)ph.ih;
-  long long f0 = fidx(g, i, j, k);
-  long long fup[3] = {fidx(g, i + 1, j, k), fidx(g, i, j + 1, k), fidx(g, i, j, k + 1)};
-  T* q[7] = {s.rho, s.m[0], s.m[1], s.m[2], s.E, s.eint, s.rh2};
-  T* q0[7] = {s0.rho, s0.m[0], s0.m[1], s0.m[2], s0.E, s0.eint, s0.rh2};
-  const LagFlux<T>* F[3] = {&fx, &fy, &fz};
+__device__ __forceinline__ void lag_update_cell(const Box<T>& B, long long c, int r) {
+  const Geom& g = B.g;
+  int q[3];
+  decode(c, g.n[0], g.n[1], q);
+  const T a = (T)RK3_A(r), bb = (T)RK3_B(r), gg = (T)RK3_G(r);
+  const T tau = (T)B.sc->tau;
+  const T ih = (T)B.ph.ih;
+  long long f0 = fidx(g, q[0], q[1], q[2]);
+  long long fup[3] = {fidx(g, q[0] + 1, q[1], q[2]), fidx(g, q[0], q[1] + 1, q[2]), fidx(g, q[0], q[1], q[2] + 1)};
+  T* qq[7] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2};
+  T* q0[7] = {B.s0.rho, B.s0.m[0], B.s0.m[1], B.s0.m[2], B.s0.E, B.s0.eint, B.s0.rh2};
+  const int nv = B.nv;
   for (int v = 0; v < nv; ++v) {
     T acc = T(0);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) acc = acc + (F[d]->f[v][f0] - F[d]->f[v][fup[d]]);
+    for (int d = 0; d < 3; ++d) acc = acc + (B.fo[d].f[v][f0] - B.fo[d].f[v][fup[d]]);
     T R = acc * ih;
-    q[v][c] = (a * q0[v][c] + bb * q[v][c]) + gg * (tau * R);
+    qq[v][c] = (a * q0[v][c] + bb * qq[v][c]) + gg * (tau * R);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) kb_lag_update(const Box<T>* __restrict__ boxes, Tiles tl, int r) {
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    long long c = (long long)tl.start[t_] + threadIdx.x;
+    if (c < B.g.N) lag_update_cell(B, c, r);
+  }
+}
+
+// RK register Q^n of a stage: Eulerian (m, rho E, rho eps, b) or Lagrangian (rho, m, rho E,
+// rho eps, rho_H2)
+template <typename T>
+__global__ void __launch_bounds__(512) kb_save_qn(const Box<T>* __restrict__ boxes, Tiles tl, int lagrangian) {
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    long long c = (long long)tl.start[t_] + threadIdx.x;
+    if (c >= B.g.N) continue;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) B.s0.m[d][c] = B.s.m[d][c];
+    B.s0.E[c] = B.s.E[c];
+    B.s0.eint[c] = B.s.eint[c];
+    if (lagrangian) {
+      B.s0.rho[c] = B.s.rho[c];
+      if (B.nv == 7) B.s0.rh2[c] = B.s.rh2[c];
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) B.s0.b[d][c] = B.s.b[d][c];
+    }
   }
 }
 
@@ -263,133 +345,132 @@ __device__ __forceinline__ double warp_max(double v) {
 
 // Per cell, after the Lagrangian stage: chemistry (Sec. 2.7, FP64), regularisation (Sec. 2.9),
 // the non-physical check, and the CFL denominator of the new state for the next tau (Sec. 2.3).
-// do_chem / do_reg select the stages (the full step runs both).
+// do_chem / do_reg select the stages (the full step runs both); do_chem = do_reg = 0 computes
+// only the CFL denominator.  Returns the flags via the warp-aggregated atomics of the caller.
 template <typename T>
-__global__ void __launch_bounds__(256) k_post(Geom g, Phys ph, Scalars* sc, State<T> s,
-                                              int do_chem, int do_reg) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double D = 0.0;
-  int bad = 0;
-  unsigned vb = 0;
-  if (c < g.N) {
-    int i = (int)(c % g.n[0]);
-    long long r = c / g.n[0];
-    int j = (int)(r % g.n[1]);
-    int k = (int)(r / g.n[1]);
-    const double tau = sc->tau;
-    if (do_chem && ph.chem)
-      s.rh2[c] = (T)chem_cell(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c], tau);
-    long long up[3] = {cmap(g, i + 1, j, k), cmap(g, i, j + 1, k), cmap(g, i, j, k + 1)};
-    T B[3];
+__device__ __forceinline__ void post_cell(const Box<T>& B, long long c, int do_chem, int do_reg,
+                                          double& D, int& bad, unsigned& vb) {
+  const Geom& g = B.g;
+  const Phys& ph = B.ph;
+  const State<T>& s = B.s;
+  int q[3];
+  decode(c, g.n[0], g.n[1], q);
+  const double tau = B.sc->tau;
+  if (do_chem && ph.chem)
+    s.rh2[c] = (T)chem_cell(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c], tau);
+  long long up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
+  T Bc[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) B[d] = T(0.5) * (s.b[d][c] + s.b[d][up[d]]);
-    T rho = s.rho[c];
-    T m[3] = {s.m[0][c], s.m[1][c], s.m[2][c]};
-    T E = s.E[c], eint = s.eint[c];
-    if (do_reg) {
-      T m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
-      T kin = T(0.5) * m2 / rho;
-      T mag = T(0.5) * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
-      T e = E - kin - mag;
-      T f = e / E;
-      bool entropy_branch = f >= T(1e-3);
-      if (ph.regul_mode == 2) entropy_branch = !entropy_branch;
-      if (entropy_branch) {
-        if (ph.regul_mode != 0 || e > eint) eint = e;
-      } else {
-        T v2 = T(2) * (E - eint - mag) / rho;
-        if (v2 < T(0)) v2 = T(0);
-        T vnew = sqrt(v2);
-        T vold = sqrt(m2) / rho;
-        if (vold > T(0)) {
-          T scl = vnew / vold;
+  for (int d = 0; d < 3; ++d) Bc[d] = T(0.5) * (s.b[d][c] + s.b[d][up[d]]);
+  T rho = s.rho[c];
+  T m[3] = {s.m[0][c], s.m[1][c], s.m[2][c]};
+  T E = s.E[c], eint = s.eint[c];
+  if (do_reg) {
+    T m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
+    T kin = T(0.5) * m2 / rho;
+    T mag = T(0.5) * (Bc[0] * Bc[0] + Bc[1] * Bc[1] + Bc[2] * Bc[2]);
+    T e = E - kin - mag;
+    T f = e / E;
+    bool entropy_branch = f >= T(1e-3);
+    if (ph.regul_mode == 2) entropy_branch = !entropy_branch;
+    if (entropy_branch) {
+      if (ph.regul_mode != 0 || e > eint) eint = e;
+    } else {
+      T v2 = T(2) * (E - eint - mag) / rho;
+      if (v2 < T(0)) v2 = T(0);
+      T vnew = sqrt(v2);
+      T vold = sqrt(m2) / rho;
+      if (vold > T(0)) {
+        T scl = vnew / vold;
 #pragma unroll
-          for (int d = 0; d < 3; ++d) m[d] = m[d] * scl;
-        }
-        vb = 1;
+        for (int d = 0; d < 3; ++d) m[d] = m[d] * scl;
       }
-      s.eint[c] = eint;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) s.m[d][c] = m[d];
+      vb = 1;
     }
-    T vals[10] = {rho, m[0], m[1], m[2], E, eint, ph.chem ? s.rh2[c] : T(0),
-                  s.b[0][c], s.b[1][c], s.b[2][c]};
+    s.eint[c] = eint;
 #pragma unroll
-    for (int q = 0; q < 10; ++q)
-      if (!isfinite(vals[q])) bad = 1;
-    if (!(rho > T(0)) || !(eint > T(0))) bad = 1;
-    double gm = ph.chem ? gamma_eff((double)rho, (double)s.rh2[c]) : ph.gamma;
-    if (!bad) {
-      double rr = (double)rho;
-      double pp = (gm - 1.0) * (double)eint;  // FP64 CFL of the new state (FP32 fields widened)
-      D = cfl_denominator(rr, (double)m[0] / rr, (double)m[1] / rr, (double)m[2] / rr, (double)B[0],
-                          (double)B[1], (double)B[2], pp, gm);
-    }
+    for (int d = 0; d < 3; ++d) s.m[d][c] = m[d];
   }
-  D = warp_max(D);
-  int anybad = __any_sync(0xffffffffu, bad);
-  unsigned nvb = __popc(__ballot_sync(0xffffffffu, vb));
-  if ((threadIdx.x & 31) == 0) {
-    if (D > 0.0) atomicMax(&sc->dmax, (unsigned long long)__double_as_longlong(D));
-    if (anybad) atomicOr(&sc->flags, 1);
-    if (nvb) atomicAdd(&sc->vel_branch, (unsigned long long)nvb);
+  T vals[10] = {rho, m[0], m[1], m[2], E, eint, ph.chem ? s.rh2[c] : T(0), s.b[0][c], s.b[1][c], s.b[2][c]};
+#pragma unroll
+  for (int k = 0; k < 10; ++k)
+    if (!isfinite(vals[k])) bad = 1;
+  if (!(rho > T(0)) || !(eint > T(0))) bad = 1;
+  double gm = ph.chem ? gamma_eff((double)rho, (double)s.rh2[c]) : ph.gamma;
+  if (!bad) {
+    double rr = (double)rho;
+    double pp = (gm - 1.0) * (double)eint;  // FP64 CFL of the new state (FP32 fields widened)
+    D = cfl_denominator(rr, (double)m[0] / rr, (double)m[1] / rr, (double)m[2] / rr, (double)Bc[0],
+                        (double)Bc[1], (double)Bc[2], pp, gm);
   }
 }
 
-// CFL denominator alone (after set_state): same arithmetic as the tail of k_post.
 template <typename T>
-__global__ void __launch_bounds__(256) k_cfl(Geom g, Phys ph, Scalars* sc, State<T> s) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double D = 0.0;
-  if (c < g.N) {
-    int i = (int)(c % g.n[0]);
-    long long r = c / g.n[0];
-    int j = (int)(r % g.n[1]);
-    int k = (int)(r / g.n[1]);
-    long long up[3] = {cmap(g, i + 1, j, k), cmap(g, i, j + 1, k), cmap(g, i, j, k + 1)};
-    T B[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) B[d] = T(0.5) * (s.b[d][c] + s.b[d][up[d]]);
-    T rho = s.rho[c];
-    double gm = ph.chem ? gamma_eff((double)rho, (double)s.rh2[c]) : ph.gamma;
-    double rr = (double)rho;
-    double pp = (gm - 1.0) * (double)s.eint[c];
-    if (rho > T(0))
-      D = cfl_denominator(rr, (double)s.m[0][c] / rr, (double)s.m[1][c] / rr, (double)s.m[2][c] / rr,
-                          (double)B[0], (double)B[1], (double)B[2], pp, gm);
+__global__ void __launch_bounds__(512) kb_post(const Box<T>* __restrict__ boxes, Tiles tl, int do_chem,
+                                               int do_reg, int check) {
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    long long c = (long long)tl.start[t_] + threadIdx.x;
+    double D = 0.0;
+    int bad = 0;
+    unsigned vb = 0;
+    if (c < B.g.N) post_cell(B, c, do_chem, do_reg, D, bad, vb);
+    if (!check) bad = 0;
+    D = warp_max(D);
+    int anybad = __any_sync(0xffffffffu, bad);
+    unsigned nvb = __popc(__ballot_sync(0xffffffffu, vb));
+    if ((threadIdx.x & 31) == 0) {
+      if (D > 0.0) atomicMax(&B.sc->dmax, (unsigned long long)__double_as_longlong(D));
+      if (anybad) atomicOr(&B.sc->flags, 1);
+      if (nvb) atomicAdd(&B.sc->vel_branch, (unsigned long long)nvb);
+    }
   }
-  D = warp_max(D);
-  if ((threadIdx.x & 31) == 0 && D > 0.0)
-    atomicMax(&sc->dmax, (unsigned long long)__double_as_longlong(D));
 }
 
 // tau of the step from the device-resident max denominator (Sec. 2.3; min over cells of
 // CFL h / D equals CFL h / max D since rounding is monotone), truncated at t_end (A18).
-__global__ void k_begin_step(Phys ph, Scalars* sc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+template <typename T>
+__global__ void kb_begin_step(const Box<T>* __restrict__ boxes, int nb) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  Scalars* sc = boxes[b].sc;
+  const double dx = boxes[b].ph.dx;
   if (!sc->fixed_tau) {
     double Dm = __longlong_as_double((long long)sc->dmax);
-    double tau = sc->cfl * ph.dx / Dm;
+    double tau = sc->cfl * dx / Dm;
     if (sc->t_end > 0.0 && tau > sc->t_end - sc->t) tau = sc->t_end - sc->t;
     sc->tau = tau;
   }
-  sc->tau_h = sc->tau / ph.dx;
+  sc->tau_h = sc->tau / dx;
   if (!(sc->tau > 0.0)) sc->flags |= 2;
   sc->dmax = 0ull;  // the post kernel of this step accumulates the next state's denominator
 }
 
-__global__ void k_end_step(Scalars* sc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+template <typename T>
+__global__ void kb_end_step(const Box<T>* __restrict__ boxes, int nb) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  Scalars* sc = boxes[b].sc;
   sc->t = sc->t + sc->tau;
   sc->steps += 1;
 }
 
-__global__ void k_set_params(Scalars* sc, double cfl, double t_end, int fixed_tau, double tau) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+template <typename T>
+__global__ void kb_set_params(const Box<T>* __restrict__ boxes, int nb, double cfl, double t_end,
+                              int fixed_tau, double tau) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  Scalars* sc = boxes[b].sc;
   sc->cfl = cfl;
   sc->t_end = t_end;
   sc->fixed_tau = fixed_tau;
   if (fixed_tau) sc->tau = tau;
+}
+
+template <typename T>
+__global__ void kb_zero_dmax(const Box<T>* __restrict__ boxes, int nb) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nb) boxes[b].sc->dmax = 0ull;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -534,7 +615,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Geom g, State<T> 
   if (threadIdx.x < 9) part[(long long)blockIdx.x * 9 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-__global__ void __launch_bounds__(DIAG_THREADS) k_diag_final(const double* part, int nblocks, double* out) {
+static __global__ void __launch_bounds__(DIAG_THREADS) k_diag_final(const double* part, int nblocks, double* out) {
   __shared__ double sh[9][DIAG_THREADS];
   double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int b = threadIdx.x; b < nblocks; b += DIAG_THREADS) {

@@ -1,0 +1,367 @@
+// mhd_runtime.cuh -- internal runtime of libmhd.so shared by its translation units: the simulation
+// object, the executor that steps a set of boxes with one launch per kernel class, and the
+// templated launchers.  The FP64 instances are compiled in mhd.cu (no contraction: every product
+// and sum rounded as written); the FP32-bulk instances in mhd_f32.cu (contraction allowed).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "mhd.h"
+#include "mhd_kernels.cuh"
+
+namespace mhd_rt {
+using namespace mhd;
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// kernel classes with their own launch shape
+enum KClass { KC_PRIM = 0, KC_EFACE, KC_EDGES, KC_EUPD, KC_LFACE, KC_LUPD, KC_POST, KC_QN, NKC };
+// profile class of each kernel class (include/mhd.h, enum mhd_kernel_class)
+inline int profile_class(int kc) {
+  const int m[NKC] = {MHD_K_PRIM, MHD_K_EULER_FACE, MHD_K_EDGES, MHD_K_EULER_UPDATE,
+                      MHD_K_LAG_FACE, MHD_K_LAG_UPDATE, MHD_K_POST, MHD_K_SMALL};
+  return m[kc];
+}
+// profiler tags: PROF_KC_BASE + kernel class for the tiled kernels, MHD_K_SMALL for the rest
+constexpr int PROF_KC_BASE = 100;
+inline int report_class(int tag) { return tag >= PROF_KC_BASE ? profile_class(tag - PROF_KC_BASE) : tag; }
+// domain of the tiles of each kernel class (face kernels: per direction, DOM_FACE_X + d)
+inline int class_domain(int kc) {
+  const int m[NKC] = {DOM_CELLS, DOM_FACE_X, DOM_LATTICE, DOM_CELLS, DOM_FACE_X, DOM_CELLS, DOM_CELLS, DOM_CELLS};
+  return m[kc];
+}
+
+// launch shape: threads per block (= tile size) and grid = min(tiles, grid_mult x SMs), or one
+// block per tile when grid_mult == 0
+struct LaunchCfg {
+  int block = 256;
+  int grid_mult = 0;
+};
+constexpr int NTILE_SIZES = 4;  // 64, 128, 256, 512
+inline int tile_slot(int block) { return block == 64 ? 0 : block == 128 ? 1 : block == 256 ? 2 : 3; }
+
+struct TileTable {
+  int* d = nullptr;  // [box..., start...] in one allocation
+  int n = 0;
+};
+
+// CUDA event pairs around launches while profiling
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> cls;
+};
+
+struct PScope {
+  Profiler* P;
+  cudaStream_t st;
+  PScope(Profiler* p, cudaStream_t s, int cls) : P(p), st(s) {
+    if (!P || !P->on) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    P->ev.push_back(e);
+    P->cls.push_back(cls);
+  }
+  ~PScope() {
+    if (!P || !P->on) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    P->ev.push_back(e);
+  }
+};
+
+// A set of boxes advanced together: one launch per kernel class covers every box.
+template <typename T>
+struct Exec {
+  std::vector<Box<T>> h;  // host copies of the descriptors
+  Box<T>* d = nullptr;    // device table
+  int nb = 0;
+  TileTable tab[NDOM][NTILE_SIZES];
+  LaunchCfg cfg[NKC];
+  int nsm = 152;
+  Profiler* prof = nullptr;
+};
+
+template <typename T>
+long long domain_size(const Box<T>& B, int dom) {
+  const Geom& g = B.g;
+  switch (dom) {
+    case DOM_CELLS: return g.N;
+    case DOM_FACE_X: return (long long)(g.n[0] + 1) * g.n[1] * g.n[2];
+    case DOM_FACE_Y: return (long long)g.n[0] * (g.n[1] + 1) * g.n[2];
+    case DOM_FACE_Z: return (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
+    default: return g.NF;
+  }
+}
+
+template <typename T>
+cudaError_t ensure_table(Exec<T>& X, int dom, int block) {
+  TileTable& t = X.tab[dom][tile_slot(block)];
+  if (t.d) return cudaSuccess;
+  std::vector<int> bx, st;
+  for (int b = 0; b < X.nb; ++b) {
+    long long n = domain_size(X.h[b], dom);
+    for (long long s = 0; s < n; s += block) {
+      bx.push_back(b);
+      st.push_back((int)s);
+    }
+  }
+  t.n = (int)bx.size();
+  if (t.n == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&t.d, sizeof(int) * 2 * (size_t)t.n);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(t.d, bx.data(), sizeof(int) * t.n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(t.d + t.n, st.data(), sizeof(int) * t.n, cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+cudaError_t ensure_tables(Exec<T>& X) {
+  for (int kc = 0; kc < NKC; ++kc) {
+    int dom = class_domain(kc);
+    int ndom = (dom == DOM_FACE_X) ? 3 : 1;
+    for (int q = 0; q < ndom; ++q) {
+      cudaError_t e = ensure_table(X, dom + q, X.cfg[kc].block);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+Tiles tiles_of(const Exec<T>& X, int dom, int block) {
+  const TileTable& t = X.tab[dom][tile_slot(block)];
+  Tiles r;
+  r.box = t.d;
+  r.start = t.d + t.n;
+  r.n = t.n;
+  return r;
+}
+
+inline unsigned grid_of(const Tiles& t, const LaunchCfg& c, int nsm) {
+  long long g = t.n;
+  if (c.grid_mult > 0 && (long long)c.grid_mult * nsm < g) g = (long long)c.grid_mult * nsm;
+  return (unsigned)(g > 0 ? g : 1);
+}
+
+// default launch shapes: FP64 face kernels are register heavy (128 threads), the rest 256
+template <typename T>
+void default_cfgs(Exec<T>& X) {
+  for (int kc = 0; kc < NKC; ++kc) X.cfg[kc] = LaunchCfg{256, 0};
+  if (sizeof(T) == 8) {
+    X.cfg[KC_EFACE].block = 128;
+    X.cfg[KC_LFACE].block = 128;
+  }
+}
+
+template <typename T>
+cudaError_t exec_init(Exec<T>& X, const std::vector<Box<T>>& boxes) {
+  X.h = boxes;
+  X.nb = (int)boxes.size();
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&X.nsm, cudaDevAttrMultiProcessorCount, dev);
+  default_cfgs(X);
+  cudaError_t e = cudaMalloc(&X.d, sizeof(Box<T>) * (size_t)X.nb);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(X.d, X.h.data(), sizeof(Box<T>) * (size_t)X.nb, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return ensure_tables(X);
+}
+
+template <typename T>
+void exec_free(Exec<T>& X) {
+  for (int d = 0; d < NDOM; ++d)
+    for (int q = 0; q < NTILE_SIZES; ++q) {
+      if (X.tab[d][q].d) cudaFree(X.tab[d][q].d);
+      X.tab[d][q].d = nullptr;
+      X.tab[d][q].n = 0;
+    }
+  if (X.d) cudaFree(X.d);
+  X.d = nullptr;
+  X.nb = 0;
+  X.h.clear();
+}
+
+// ------------------------------------------------------------------------------------------------
+// launchers
+template <typename T, typename K, typename... A>
+void launch_k(Exec<T>& X, cudaStream_t st, int kc, int dom, K kernel, A... args) {
+  const LaunchCfg& c = X.cfg[kc];
+  Tiles t = tiles_of(X, dom, c.block);
+  PScope p(X.prof, st, PROF_KC_BASE + kc);  // the profiler records the kernel class
+  kernel<<<grid_of(t, c, X.nsm), c.block, 0, st>>>(X.d, t, args...);
+}
+
+template <typename T>
+void launch_small(Exec<T>& X, cudaStream_t st, int which, double cfl = 0, double t_end = 0,
+                  int fixed = 0, double tau = 0) {
+  PScope p_(X.prof, st, MHD_K_SMALL);
+  unsigned g = nblk(X.nb, 128);
+  if (which == 0) kb_begin_step<T><<<g, 128, 0, st>>>(X.d, X.nb);
+  if (which == 1) kb_end_step<T><<<g, 128, 0, st>>>(X.d, X.nb);
+  if (which == 2) kb_set_params<T><<<g, 128, 0, st>>>(X.d, X.nb, cfl, t_end, fixed, tau);
+  if (which == 3) kb_zero_dmax<T><<<g, 128, 0, st>>>(X.d, X.nb);
+}
+
+template <typename T>
+void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
+  launch_k(X, st, KC_QN, DOM_CELLS, kb_save_qn<T>, 0);
+  for (int r = 0; r < 3; ++r) {
+    launch_k(X, st, KC_PRIM, DOM_CELLS, kb_prim<T>);
+    launch_k(X, st, KC_EFACE, DOM_FACE_X, kb_euler_face<T, 0>);
+    launch_k(X, st, KC_EFACE, DOM_FACE_Y, kb_euler_face<T, 1>);
+    launch_k(X, st, KC_EFACE, DOM_FACE_Z, kb_euler_face<T, 2>);
+    launch_k(X, st, KC_EDGES, DOM_LATTICE, kb_edges<T>);
+    launch_k(X, st, KC_EUPD, DOM_CELLS, kb_euler_update<T>, r);
+  }
+}
+
+template <typename T>
+void launch_lag_stage(Exec<T>& X, cudaStream_t st) {
+  launch_k(X, st, KC_QN, DOM_CELLS, kb_save_qn<T>, 1);
+  for (int r = 0; r < 3; ++r) {
+    launch_k(X, st, KC_LFACE, DOM_FACE_X, kb_lag_face<T, 0>);
+    launch_k(X, st, KC_LFACE, DOM_FACE_Y, kb_lag_face<T, 1>);
+    launch_k(X, st, KC_LFACE, DOM_FACE_Z, kb_lag_face<T, 2>);
+    launch_k(X, st, KC_LUPD, DOM_CELLS, kb_lag_update<T>, r);
+  }
+}
+
+// chemistry / regularisation / check / CFL of the new state (do_chem = do_reg = check = 0: only
+// the CFL denominator)
+template <typename T>
+void launch_post(Exec<T>& X, cudaStream_t st, int do_chem, int do_reg, int check) {
+  launch_k(X, st, KC_POST, DOM_CELLS, kb_post<T>, do_chem, do_reg, check);
+}
+
+template <typename T>
+void launch_step(Exec<T>& X, cudaStream_t st) {
+  launch_small(X, st, 0);
+  launch_euler_stage(X, st);
+  launch_lag_stage(X, st);
+  launch_post(X, st, 1, 1, 1);
+  launch_small(X, st, 1);
+}
+
+// the max CFL denominator of the current state of every box
+template <typename T>
+cudaError_t launch_cfl(Exec<T>& X, cudaStream_t st) {
+  launch_small(X, st, 3);
+  launch_post(X, st, 0, 0, 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_set_params(Exec<T>& X, cudaStream_t st, double cfl, double t_end, int fixed, double tau) {
+  launch_small(X, st, 2, cfl, t_end, fixed, tau);
+  return cudaGetLastError();
+}
+
+}  // namespace mhd_rt
+
+// ------------------------------------------------------------------------------------------------
+struct mhd_sim {
+  using Geom = mhd::Geom;
+  using Phys = mhd::Phys;
+  using Scalars = mhd::Scalars;
+  Geom g;
+  Phys ph;
+  int precision = 0;
+  int use_graph = 1;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char* pool = nullptr;
+  size_t pool_bytes = 0;
+  char* staging = nullptr;  // 10 * N * 8 bytes for host transfers / dtype conversion
+  Scalars* sc = nullptr;
+  Scalars* sc_host = nullptr;  // pinned mirror
+  double* diag_part = nullptr;
+  double* diag_out = nullptr;
+  double* diag_host = nullptr;  // pinned, 9 doubles
+  int diag_blocks = 0;
+  mhd::Box<double> b64;  // descriptors of this box (one of the two is used)
+  mhd::Box<float> b32;
+  mhd_rt::Exec<double> x64;  // executor of this box alone
+  mhd_rt::Exec<float> x32;
+  mhd_rt::Profiler prof;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_valid = false;
+  bool exec_valid = false;
+  bool params_dirty = true;
+  double last_cfl = -1.0, last_tend = -1.0;
+  bool has_state = false;
+  int batched = 0;  // number of batches that reference this sim
+};
+
+namespace mhd_rt {
+
+// ------------------------------------------------------------------------------------------------
+// per-sim (non-batched) helpers: state transfer and diagnostics
+template <typename T, typename In>
+cudaError_t load_state(mhd_sim* S, Box<T>& B, const In* const* p) {
+  const Geom& g = B.g;
+  k_load_cells<T, In><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s, p[0], p[1], p[2], p[3], p[4], p[8]);
+  k_faces_from_cells<T, In><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s, p[5], p[6], p[7]);
+  k_derive_eint<T><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s);
+  return cudaGetLastError();
+}
+
+template <typename T, typename Out>
+cudaError_t store_state(mhd_sim* S, Box<T>& B, Out* const* p) {
+  const Geom& g = B.g;
+  k_store_state<T, Out><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s, p[0], p[1], p[2], p[3], p[4], p[5],
+                                                                p[6], p[7], p[8]);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t set_faces(mhd_sim* S, Box<T>& B, const double* const* b) {
+  const Geom& g = B.g;
+  k_faces_copy<T><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s, b[0], b[1], b[2]);
+  k_derive_eint<T><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t store_full(mhd_sim* S, Box<T>& B, double* const* d) {
+  k_store_full<T><<<nblk(B.g.N, 256), 256, 0, S->stream>>>(B.g, B.s, d[0], d[1], d[2], d[3]);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t load_full(mhd_sim* S, Box<T>& B, const double* const* d) {
+  k_load_full<T><<<nblk(B.g.N, 256), 256, 0, S->stream>>>(B.g, B.s, d[0], d[1], d[2], d[3]);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t diag_partial(mhd_sim* S, Box<T>& B) {
+  k_diag_partial<T><<<S->diag_blocks, DIAG_THREADS, 0, S->stream>>>(B.g, B.s, S->diag_part);
+  return cudaGetLastError();
+}
+
+// The FP32 instances live in mhd_f32.cu.
+#ifndef MHD_RT_F32_TU
+extern template void launch_euler_stage<float>(Exec<float>&, cudaStream_t);
+extern template void launch_lag_stage<float>(Exec<float>&, cudaStream_t);
+extern template void launch_step<float>(Exec<float>&, cudaStream_t);
+extern template void launch_post<float>(Exec<float>&, cudaStream_t, int, int, int);
+extern template cudaError_t launch_cfl<float>(Exec<float>&, cudaStream_t);
+extern template cudaError_t launch_set_params<float>(Exec<float>&, cudaStream_t, double, double, int, double);
+extern template void launch_small<float>(Exec<float>&, cudaStream_t, int, double, double, int, double);
+extern template cudaError_t load_state<float, double>(mhd_sim*, Box<float>&, const double* const*);
+extern template cudaError_t load_state<float, float>(mhd_sim*, Box<float>&, const float* const*);
+extern template cudaError_t store_state<float, double>(mhd_sim*, Box<float>&, double* const*);
+extern template cudaError_t store_state<float, float>(mhd_sim*, Box<float>&, float* const*);
+extern template cudaError_t set_faces<float>(mhd_sim*, Box<float>&, const double* const*);
+extern template cudaError_t store_full<float>(mhd_sim*, Box<float>&, double* const*);
+extern template cudaError_t load_full<float>(mhd_sim*, Box<float>&, const double* const*);
+extern template cudaError_t diag_partial<float>(mhd_sim*, Box<float>&);
+#endif
+
+}  // namespace mhd_rt

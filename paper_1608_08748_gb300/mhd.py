@@ -70,6 +70,17 @@ def lib():
         L.mhd_diagnostics.argtypes = [vp, C.POINTER(Diag)]
         L.mhd_bytes_needed.restype = C.c_size_t
         L.mhd_bytes_needed.argtypes = [i, i, i, i, i]
+        L.mhd_profile.argtypes = [vp, d, i, C.POINTER(d), C.POINTER(C.c_int64)]
+        L.mhd_launches_per_step.argtypes = [vp]
+        L.mhd_batch_create.restype = vp
+        L.mhd_batch_create.argtypes = [C.POINTER(vp), i]
+        L.mhd_batch_destroy.argtypes = [vp]
+        L.mhd_batch_step.argtypes = [vp, d]
+        L.mhd_batch_sync.argtypes = [vp]
+        L.mhd_batch_tune.argtypes = [vp, d, i, C.POINTER(d)]
+        L.mhd_batch_get_shape.argtypes = [vp, i, C.POINTER(i), C.POINTER(i)]
+        L.mhd_batch_set_shape.argtypes = [vp, i, i, i]
+        L.mhd_batch_profile.argtypes = [vp, d, i, C.POINTER(d), C.POINTER(C.c_int64)]
         _lib = L
     return _lib
 
@@ -219,3 +230,64 @@ def from_ic(ic, **options):
     if "bface" in ic:
         s.set_face_B(*ic["bface"])
     return s
+
+
+KERNEL_CLASSES = ["prim", "euler_face", "edges", "euler_update", "lag_face", "lag_update", "post",
+                  "small"]
+
+
+def _profile_dict(ms, n):
+    return {k: {"ms_total": ms[c], "launches": int(n[c])} for c, k in enumerate(KERNEL_CLASSES)}
+
+
+def profile(sim, cfl, steps):
+    """Per kernel class CUDA-event time of `steps` launched steps of one sim (advances it)."""
+    ms = (C.c_double * 8)()
+    n = (C.c_int64 * 8)()
+    _check(sim.L.mhd_profile(sim.h, float(cfl), int(steps), ms, n))
+    return _profile_dict(ms, n)
+
+
+class Batch:
+    """Sims advanced together, one launch per kernel class over all their boxes."""
+
+    def __init__(self, sims):
+        self.L = lib()
+        self.sims = list(sims)  # keep the members alive
+        arr = (C.c_void_p * len(self.sims))(*[x.h for x in self.sims])
+        self.h = self.L.mhd_batch_create(arr, len(self.sims))
+        if not self.h:
+            raise MHDError(-1, self.L.mhd_last_error().decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mhd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self, cfl):
+        _check(self.L.mhd_batch_step(self.h, float(cfl)))
+
+    def sync(self):
+        _check(self.L.mhd_batch_sync(self.h))
+
+    def tune(self, cfl, reps=2):
+        best = C.c_double(0.0)
+        _check(self.L.mhd_batch_tune(self.h, float(cfl), int(reps), C.byref(best)))
+        return best.value
+
+    def shape(self, kernel_class):
+        b, g = C.c_int(0), C.c_int(0)
+        _check(self.L.mhd_batch_get_shape(self.h, KERNEL_CLASSES.index(kernel_class), C.byref(b), C.byref(g)))
+        return b.value, g.value
+
+    def set_shape(self, kernel_class, block, grid_mult):
+        _check(self.L.mhd_batch_set_shape(self.h, KERNEL_CLASSES.index(kernel_class), int(block), int(grid_mult)))
+
+    def profile(self, cfl, steps):
+        ms = (C.c_double * 8)()
+        n = (C.c_int64 * 8)()
+        _check(self.L.mhd_batch_profile(self.h, float(cfl), int(steps), ms, n))
+        return _profile_dict(ms, n)

@@ -119,3 +119,19 @@ def test_outflow_all_axes(M, oracle_mod):
     ic["options"] = {"bc_x": 1, "bc_y": 1, "bc_z": 1, "chem": 1}
     g, o = run_pair(M, oracle_mod, ic, steps=6)
     compare(g.get_state(), o.get_state())
+
+
+def test_turbulence_128_config2_full(M, oracle_mod):
+    """Config 2 at full size: 128^3 turbulence with chemistry (Mach 5, beta 1, seed 1), 50 steps in
+    the launch configuration bench.py times (one CUDA-graph replay per step), compared element by
+    element with the oracle."""
+    ic = I.turbulence(128, mach=5.0, beta=1.0, seed=1)
+    g = M.from_ic(ic)
+    for _ in range(50):
+        g.step(0.4, sync=False)
+    g.sync()
+    o = oracle_mod.run(ic, steps=50)
+    errs = compare(g.get_state(), o.get_state())
+    dg = g.diagnostics()
+    assert dg["steps"] == 50 and dg["t"] == pytest.approx(o.t, rel=1e-13)
+    print("config 2 rel L1:", {k: f"{v:.1e}" for k, v in errs.items()})
