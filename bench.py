@@ -33,14 +33,14 @@ WORKLOAD = "mhd_turbulence_h2chem_128^3_fp64"
 METRIC = "Mcell-updates/s"
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# algorithmic FP64 flops of one Eulerian face solve, counted from the kernel source: 12 PPM
-# parabolas (6 variables x 2 cells, ~70 each), Roe average and eigenvectors (~60), 36 parabola
-# averages with L q and R s (~400), fluxes (~25); add/sub/mul/div/sqrt one flop each, compares
-# not counted
-FLOPS_PER_EULER_FACE = 1350
-# DRAM bytes (read + write) of one k_euler_face launch at 128^3 from the ncu capture summarised in
-# profiles/k_euler_face_turbulence_128_fp64.md (set to None when the kernel changes)
-EULER_FACE_TRAFFIC_BYTES = 248.5e6
+# algorithmic FP64 flops of one Eulerian face, counted from the kernel source: 6 PPM parabola sets
+# (one per cell and variable, amortised over the cell's two faces, ~70 flops each) and the Riemann
+# solve (Roe average and eigenvectors ~60, 36 parabola averages with L q and R s ~400, fluxes ~25);
+# add/sub/mul/div/sqrt one flop each, compares not counted
+FLOPS_PER_EULER_FACE = 930
+# DRAM bytes (read + write) of one x-direction Eulerian face launch at 128^3 from the ncu capture
+# summarised in profiles/kb_euler_pencil_turbulence_128_fp64.md (None when the kernel changes)
+EULER_FACE_TRAFFIC_BYTES = 330.4e6
 
 
 def reduce_max(x, dist=None, device="cpu"):
@@ -154,6 +154,142 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def rel_l1_fields(a, b):
+    """Per-field relative L1 of state a against reference b (scales as in the parity tests)."""
+    rho = b["rho"]
+    vscale = np.sqrt(max(np.mean(2.0 * np.abs(b["E"]) / rho), 1e-300))
+    brms = np.sqrt(np.mean(b["B"] ** 2))
+    sc = {"rho": rho.mean(), "E": np.abs(b["E"]).mean(), "mom": rho.mean() * vscale,
+          "B": brms if brms > 0 else 1.0, "rho_h2": rho.mean()}
+    f = lambda x, y, s: float(np.abs(x - y).sum() / max(np.abs(y).sum(), y.size * s))
+    out = {k: f(a[k], b[k], sc[k]) for k in ["rho", "E", "rho_h2"]}
+    for c, ax in enumerate("xyz"):
+        out["m" + ax] = f(a["mom"][c], b["mom"][c], sc["mom"])
+        out["B" + ax] = f(a["B"][c], b["B"][c], sc["B"])
+    return out
+
+
+def timed_steps(torch, sim, steps, warm):
+    stream = torch.cuda.Stream()
+    sim.set_stream(stream.cuda_stream)
+    for _ in range(warm):
+        sim.step(CFL, sync=False)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        sim.step(CFL, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sim.sync()
+    return e0.elapsed_time(e1)
+
+
+def fp32_leg(M, I, torch, n=256, steps=10, warm=3, err_steps=5):
+    """Config 3: the same turbulence set-up at n^3 with the FP32-bulk path; per-field error against
+    the FP64 GPU path (which matches the FP64 oracle to 1e-15 at 128^3) after err_steps steps."""
+    ic = I.turbulence(n, mach=5.0, beta=1.0, seed=1)
+    s32 = M.from_ic(ic, precision=1)
+    ms = timed_steps(torch, s32, steps, warm)
+    del s32
+    a = M.from_ic(ic, precision=1)
+    b = M.from_ic(ic, precision=0)
+    for _ in range(err_steps):
+        a.step(CFL, sync=False)
+        b.step(CFL, sync=False)
+    a.sync()
+    b.sync()
+    err = rel_l1_fields(a.get_state(), b.get_state())
+    del a, b
+    return {"workload": f"mhd_turbulence_h2chem_{n}^3_fp32bulk", "value": n ** 3 * steps / (ms * 1e-3) / 1e6,
+            "unit": METRIC, "ms_per_step": ms / steps, "steps": steps, "warmup": warm,
+            "rel_l1_vs_fp64": err, "error_steps": err_steps}
+
+
+def batched_leg(M, I, torch, steps=20, warm=3):
+    """Config 4: 64 turbulence boxes, axes from {16..96}, FP32 bulk, one launch per kernel class
+    per step (CUDA graph), launch shapes autotuned first."""
+    sims = []
+    for b in I.ensemble_boxes():
+        ic = I.turbulence(8, mach=b["mach"], beta=b["beta"], seed=b["seed"], shape=b["shape"])
+        sims.append(M.from_ic(ic, precision=1))
+    cells = sum(int(np.prod(s.shape)) for s in sims)
+    batch = M.Batch(sims)
+    tuned = batch.tune(CFL, reps=1)
+    shapes = {k: batch.shape(k) for k in M.mhd.KERNEL_CLASSES[:7]}
+    for _ in range(warm):
+        batch.step(CFL)
+    batch.sync()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        batch.step(CFL)
+    batch.sync()
+    dt = time.perf_counter() - t0
+    prof = batch.profile(CFL, 2)
+    batch.close()
+    return {"workload": "ensemble_64_boxes_fp32bulk", "boxes": len(sims), "cells": cells,
+            "value": cells * steps / dt / 1e6, "unit": METRIC, "ms_per_step": dt / steps * 1e3,
+            "steps": steps, "tuned_ms_per_step": tuned, "tuned_shapes": shapes,
+            "kernels": {k: v["ms_total"] / 2 for k, v in prof.items()}}
+
+
+def serving_leg(M, I, torch, duration=10.0, big=False):
+    """Config 5: Poisson arrivals (20 requests/s, seed 5) of turbulence runs, cubic n in
+    {32..192} (and 512 with probability 0.005 when big), 20-200 steps, FP32 bulk, submitted in real
+    time to the continuous-batching server.  Velocity fields: one cached solenoidal field per size,
+    shifted periodically per request."""
+    arr = [r for r in I.serving_arrivals(big_prob=0.005 if big else 0.0) if r["t"] < duration]
+    base = {}
+    for n in sorted({r["n"] for r in arr}):
+        base[n] = I.solenoidal_field((n, n, n), seed=n)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.6)
+    srv = M.Server(budget, max_active=64)
+    rng = np.random.default_rng(5)
+    ids = []
+    t0 = time.perf_counter()
+    for r in arr:
+        ic = I.turbulence_from_field(base[r["n"]], mach=r["mach"], beta=r["beta"],
+                                     shift=rng.integers(0, r["n"], 3))
+        while time.perf_counter() - t0 < r["t"]:
+            time.sleep(0.001)
+        ids.append((srv.submit(ic, nsteps=r["steps"], precision=1), r))
+    srv.drain(1800)
+    wall = time.perf_counter() - t0
+    lat, work, first, last = [], 0, None, None
+    failed = {}
+    for rid, r in ids:
+        rc, res = srv.poll(rid)
+        if rc != 0:
+            key = f"status {rc} (n={r['n']}, mach={r['mach']:.1f}, beta={r['beta']:.2f})"
+            failed[key] = failed.get(key, 0) + 1
+            continue
+        lat.append(res["t_done"] - res["t_submit"])
+        work += res["cells"] * res["steps_done"]
+        first = res["t_submit"] if first is None else min(first, res["t_submit"])
+        last = res["t_done"] if last is None else max(last, res["t_done"])
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"workload": "serving_poisson_20rps_fp32bulk", "requests": len(ids), "completed": len(lat),
+            "stream_s": duration, "big_512": bool(big), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "value": work / (last - first) / 1e6,
+            "unit": METRIC, "wall_s": wall, "hbm_budget_bytes": budget, "peak_bytes": st["peak_bytes"],
+            "peak_active": st["peak_active"], "scheduler_iterations": st["iterations"], "failed": failed}
+
+
+def run_leg(args):
+    """One secondary leg alone (profiling): prints its JSON object."""
+    import torch
+    from paper_1608_08748_gb300 import build as B
+    B.build()
+    import paper_1608_08748_gb300 as M
+    from paper_1608_08748_gb300 import inputs as I
+    fn = {"fp32": fp32_leg, "batched": batched_leg, "serving": serving_leg}[args.leg]
+    print(json.dumps({args.leg: fn(M, I, torch)}), flush=True)
+
+
 def run_ours(args):
     import torch
     rank, world, local = rank_info()
@@ -243,18 +379,23 @@ def run_ours(args):
         faces_per_launch = (N_GRID + 1) * N_GRID * N_GRID
         avg_launch_s = kernels["euler_face"]["ms_total"] / kernels["euler_face"]["launches"] * 1e-3
         achieved = FLOPS_PER_EULER_FACE * faces_per_launch / avg_launch_s / 1e12
-        roofline = {"bound": "alu", "kernel": "k_euler_face (FP64)", "achieved": achieved,
+        roofline = {"bound": "alu", "kernel": "kb_euler_pencil (FP64)", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                     "traffic": EULER_FACE_TRAFFIC_BYTES, "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
 
     if rank != 0:
         return
+    del sim
+    extras = {}
+    if world == 1 and not args.no_extras:
+        extras["fp32_bulk"] = fp32_leg(M, I, torch)
+        extras["batched"] = batched_leg(M, I, torch)
+        extras["serving"] = serving_leg(M, I, torch, big=args.serving_big)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, secs = oracle_rate(48, 8)
         cpu = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle",
                "sample": f"48^3 box of the same turbulence set-up, 8 steps ({secs:.1f} s)"}
-    d = sim.diagnostics()
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -268,8 +409,8 @@ def run_ours(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "kernels": kernels,
-        "sim_time_after": d["t"],
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
 
 
@@ -280,11 +421,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP32-bulk (256^3), batched-ensemble and serving legs")
+    ap.add_argument("--leg", choices=["main", "fp32", "batched", "serving"], default="main",
+                    help="run one secondary leg alone (for profiling)")
+    ap.add_argument("--serving-big", action="store_true",
+                    help="include the 512^3 request class (probability 0.005) in the serving leg")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.leg != "main":
+        run_leg(args)
     else:
         run_ours(args)
 

@@ -181,6 +181,54 @@ int mhd_batch_set_shape(mhd_batch* b, int kernel_class, int block, int grid_mult
 /* Per-class CUDA-event timings of `steps` batch steps (as mhd_profile). */
 int mhd_batch_profile(mhd_batch* b, double cfl, int steps, double* out_ms, int64_t* out_launches);
 
+/* ---- Serving: continuous batching of simulation requests -------------------------------------
+   A server owns a scheduler thread.  Requests (a grid, an initial state and a number of steps)
+   wait in arrival order; a request is admitted when its device memory (mhd_bytes_needed) fits in
+   the remaining HBM budget and fewer than max_active are running.  Every scheduler iteration
+   advances all admitted requests of one precision by one step in one batched launch per kernel
+   class (their work overlaps on the device); a request that has taken its steps is copied back to
+   host memory and its device memory released, which admits waiting requests.  A request's result
+   is the same as running it alone (bit for bit).  mhd_submit, mhd_poll and mhd_fetch are
+   thread-safe. */
+typedef struct mhd_server mhd_server;
+
+typedef struct mhd_request {
+  int nx, ny, nz;
+  double gamma, dx;
+  int precision;       /* 0 FP64, 1 FP32 bulk */
+  int chem;            /* H/H2 network on */
+  int bc[3];           /* per axis: 0 periodic, 1 outflow */
+  double cfl;
+  int nsteps;          /* steps to take (> 0) */
+  mhd_fields state;    /* initial state, host pointers (copied by mhd_submit; not retained) */
+} mhd_request;
+
+typedef struct mhd_result {
+  int status;          /* MHD_PENDING while queued or running, then MHD_OK or an error */
+  int64_t steps_done;
+  double t;            /* simulated time reached */
+  double t_submit, t_admit, t_done;  /* seconds on the server's monotonic clock */
+  int64_t cells;
+} mhd_result;
+
+/* hbm_budget_bytes: device memory the admitted requests may use together; max_active >= 1. */
+mhd_server* mhd_server_create(size_t hbm_budget_bytes, int max_active);
+/* Stops the scheduler after the running step; unfinished requests are dropped. */
+void mhd_server_destroy(mhd_server* srv);
+/* >= 0: request id; < 0: MHD_EINVAL, or MHD_ECAPACITY if it can never fit the budget. */
+int64_t mhd_submit(mhd_server* srv, const mhd_request* req);
+/* Non-blocking: MHD_PENDING, MHD_OK (result ready), MHD_ENOTFOUND, or the request's error. */
+int mhd_poll(mhd_server* srv, int64_t id, mhd_result* out);
+/* Copy a finished request's state into `out` (host pointers; B cell-centred) and release it. */
+int mhd_fetch(mhd_server* srv, int64_t id, mhd_fields* out);
+/* Wait (up to timeout_s seconds) until every submitted request has finished: MHD_OK or
+   MHD_ETIMEOUT. */
+int mhd_server_drain(mhd_server* srv, double timeout_s);
+/* Server clock now (same clock as the result times). */
+double mhd_server_clock(mhd_server* srv);
+/* Scheduler statistics: iterations (batched steps), peak bytes admitted, peak active requests. */
+int mhd_server_stats(mhd_server* srv, int64_t* iterations, int64_t* peak_bytes, int* peak_active);
+
 /* FP64 diagnostics of caller-owned device arrays without any device allocation.  (The paper has
    no counterpart: this is a service of the library.)  It is for callers that cannot allocate
    device memory at the point of the call: code running while a stream is captured into a CUDA

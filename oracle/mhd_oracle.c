@@ -517,6 +517,21 @@ int osim_set_face_B(osim* s, const double* bx, const double* by, const double* b
   return O_OK;
 }
 
+/* set rho eps and the face fields directly (checkpoint / restart), float64 C order */
+int osim_set_full(osim* s, const double* eint, const double* bx, const double* by, const double* bz) {
+  const int nx = s->n[0], ny = s->n[1], nz = s->n[2];
+  const double* bf[3] = {bx, by, bz};
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t src = ((size_t)k * ny + j) * nx + i;
+        size_t c = IX(s, i + NG, j + NG, k + NG);
+        s->eint[c] = eint[src];
+        for (int d = 0; d < 3; ++d) s->b[d][c] = bf[d][src];
+      }
+  return O_OK;
+}
+
 int osim_get_state(osim* s, double* rho, double* mx, double* my, double* mz, double* E,
                    double* Bx, double* By, double* Bz, double* rh2) {
   const int nx = s->n[0], ny = s->n[1], nz = s->n[2];

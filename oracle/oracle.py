@@ -59,6 +59,7 @@ def lib():
         L.osim_set_face_B.argtypes = [vp, _dp, _dp, _dp]
         L.osim_get_state.argtypes = [vp] + [_dp] * 8 + [C.c_void_p]
         L.osim_get_full.argtypes = [vp, _dp, _dp, _dp, _dp]
+        L.osim_set_full.argtypes = [vp, _dp, _dp, _dp, _dp]
         L.osim_tau.restype = d
         L.osim_tau.argtypes = [vp, d]
         L.osim_step.argtypes = [vp, d, d, C.POINTER(d)]
@@ -133,6 +134,10 @@ class Sim:
         out = [np.empty(self.shape) for _ in range(4)]
         self.L.osim_get_full(self.h, *out)
         return {"eint": out[0], "bface": np.stack(out[1:])}
+
+    def set_full(self, eint, bface):
+        a = [_f64(x).reshape(self.shape) for x in (eint, bface[0], bface[1], bface[2])]
+        self.L.osim_set_full(self.h, *a)
 
     def tau(self, cfl):
         return self.L.osim_tau(self.h, float(cfl))

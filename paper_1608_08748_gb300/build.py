@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmhd.so")
-SOURCES = ["mhd.cu", "mhd_noalloc.cu"]
+SOURCES = ["mhd.cu", "mhd_noalloc.cu", "mhd_server.cu"]
 # FP32-bulk launchers: compiled separately with contraction on
 SOURCES_F32 = ["mhd_f32.cu"]
 HEADERS = ["mhd_device.cuh", "mhd_kernels.cuh", "mhd_runtime.cuh"]
@@ -45,7 +45,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     jobs, objs = [], []
     for f in SOURCES + SOURCES_F32:
         obj = os.path.join(OUT_DIR, f.replace(".cu", tag + ".o"))
-        extra = ["--fmad=true"] if f in SOURCES_F32 else ["--fmad=false"]
+        # FP32 bulk: contraction and the hardware-approximate float division / square root (a few
+        # ulp, far inside its 1e-4 target); its FP64 parts (chemistry, CFL) are unaffected.
+        extra = (["--fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+                 if f in SOURCES_F32 else ["--fmad=false"])
         p, cmd = _compile(nvcc, os.path.join(SRC, f), obj, extra)
         if verbose:
             print(" ".join(cmd))

@@ -238,6 +238,8 @@ mhd_sim* mhd_create(int nx, int ny, int nz, double gamma, double dx) {
   S->ph.lshield = 0.0;
   S->ph.bdop = 3.0;
   S->ph.xnorm = 5e14;
+  S->ph.ibdop = 1.0 / 3.0;
+  S->ph.ixnorm = 1.0 / 5e14;
   S->ph.taud = 1e-21;
   auto bail = [&](const char* what, cudaError_t e) {
     fail(e == cudaErrorMemoryAllocation ? MHD_ENOMEM : MHD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -317,10 +319,12 @@ int mhd_set_option(mhd_sim* S, int key, double v) {
     case MHD_OPT_CHEM_BDOP:
       if (!(v > 0.0)) return fail(MHD_EINVAL, "Doppler parameter must be > 0");
       S->ph.bdop = v;
+      S->ph.ibdop = 1.0 / v;
       break;
     case MHD_OPT_CHEM_XNORM:
       if (!(v > 0.0)) return fail(MHD_EINVAL, "x normaliser must be > 0");
       S->ph.xnorm = v;
+      S->ph.ixnorm = 1.0 / v;
       break;
     case MHD_OPT_CHEM_TAUD:
       if (v < 0.0) return fail(MHD_EINVAL, "dust opacity must be >= 0");

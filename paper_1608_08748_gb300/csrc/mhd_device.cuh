@@ -28,6 +28,7 @@ struct Phys {
   int regul_mode;    // Sec. 2.9 reading: 0 max form, 1 unconditional, 2 literal branch order
   double lshield;    // shielding length, code units
   double bdop, xnorm, taud;
+  double ibdop, ixnorm;  // 1 / bdop, 1 / xnorm
 };
 
 // Device-resident scalars of a simulation: tau never crosses to the host inside a step.
@@ -348,6 +349,21 @@ __device__ __forceinline__ double cfl_denominator(double rho, double vx, double 
   return Dmax;
 }
 
+// The same denominator for the FP32-bulk path, still in FP64 but with the identity
+// c_f + c_s = sqrt(c^2 + b^2 + 2 c c_a) (from c_f^2 + c_s^2 = c^2 + b^2 and c_f c_s = c c_a); the
+// denominator grows with |B_d|, so only the axis of the largest |B_d| is evaluated.
+__device__ __forceinline__ double cfl_denominator_fast(double rho, double vx, double vy, double vz,
+                                                       double Bx, double By, double Bz, double p,
+                                                       double gam) {
+  double irs = 1.0 / sqrt(rho);
+  double c = sqrt(gam * p / rho);
+  double b = sqrt(Bx * Bx + By * By + Bz * Bz) * irs;
+  double v = sqrt(vx * vx + vy * vy + vz * vz);
+  double Bm = fmax(fabs(Bx), fmax(fabs(By), fabs(Bz)));
+  double ca = Bm * irs;
+  return v + b + c + ca + sqrt(c * c + b * b + 2.0 * c * ca);
+}
+
 // Sec. 4.3 effective adiabatic index of the H/H2 mixture (no electrons)
 __device__ __forceinline__ double gamma_eff(double rho, double rh2) {
   double nH = rho - rh2, nH2 = 0.5 * rh2;
@@ -364,6 +380,9 @@ struct ChemConst {
   static constexpr double KMS = 1.0e5;               // cm / s
 };
 
+// `fast` (the FP32-bulk path): the same FP64 formulas with one reciprocal of T instead of the
+// divisions by T, so the rates differ from the plain form by a few ulp.
+template <bool fast = false>
 __device__ __forceinline__ double chem_cell(const Phys& ph, double rho, double eint, double rh2,
                                             double tau) {
   const double P0 = ChemConst::MH * ChemConst::KMS * ChemConst::KMS;  // code pressure, erg cm^-3
@@ -373,17 +392,27 @@ __device__ __forceinline__ double chem_cell(const Phys& ph, double rho, double e
   double p = (g - 1.0) * eint * P0;
   double T = p / ((nH + nH2) * ChemConst::KB);
   // App. D rates
-  double t2 = T / 100.0;
+  double t2, a2, a3;
+  if (fast) {
+    const double iT = 1.0 / T;
+    t2 = T * 0.01;
+    a2 = T > 7390.0 ? -2.93e4 * iT : -((6750.0 * iT) * (6750.0 * iT));
+    a3 = T > 7291.0 ? -3.22e4 * iT : -(4060.0 * iT) - (7500.0 * iT) * (7500.0 * iT);
+  } else {
+    t2 = T / 100.0;
+    a2 = T > 7390.0 ? -2.93e4 / T : -((6750.0 / T) * (6750.0 / T));
+    a3 = T > 7291.0 ? -3.22e4 / T : -(4060.0 / T) - (7500.0 / T) * (7500.0 / T);
+  }
   double s2 = sqrt(t2);
   double k1p = 3e-17 * s2 / (((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2));
-  double k2 = T > 7390.0 ? 6.11e-14 * exp(-2.93e4 / T) : 2.67e-15 * exp(-((6750.0 / T) * (6750.0 / T)));
-  double k3 = T > 7291.0 ? 5.22e-14 * exp(-3.22e4 / T)
-                         : 3.17e-15 * exp(-(4060.0 / T) - (7500.0 / T) * (7500.0 / T));
+  // exp of an argument below -746 is exactly 0 in double: skip the call in cold gas
+  double k2 = a2 < -746.0 ? 0.0 : (T > 7390.0 ? 6.11e-14 : 2.67e-15) * exp(a2);
+  double k3 = a3 < -746.0 ? 0.0 : (T > 7291.0 ? 5.22e-14 : 3.17e-15) * exp(a3);
   double Ls = (ph.lshield > 0.0 ? ph.lshield : ph.dx) * ChemConst::PC;
   double NH = nH * Ls, NH2 = nH2 * Ls;
   double fdust = exp(-(ph.taud * (NH + NH2)));
-  double x = NH2 / ph.xnorm;
-  double u = 1.0 + x / ph.bdop;
+  double x = fast ? NH2 * ph.ixnorm : NH2 / ph.xnorm;
+  double u = fast ? 1.0 + x * ph.ibdop : 1.0 + x / ph.bdop;
   double sx = sqrt(1.0 + x);
   double fsh = 0.965 / (u * u) + 0.035 / sx * exp(-8.5e-4 * sx);
   double k4 = (3.3 * 1.7e-11) * fsh * fdust;

@@ -52,7 +52,14 @@ struct Tiles {
 };
 
 // domains of the tile tables
-enum { DOM_CELLS = 0, DOM_FACE_X = 1, DOM_FACE_Y = 2, DOM_FACE_Z = 3, DOM_LATTICE = 4, NDOM = 5 };
+enum { DOM_CELLS = 0, DOM_FACE_X = 1, DOM_FACE_Y = 2, DOM_FACE_Z = 3, DOM_LATTICE = 4,
+       DOM_PENCIL_X = 5, DOM_PENCIL_Y = 6, DOM_PENCIL_Z = 7, NDOM = 8 };
+
+// Eulerian faces are solved in pencils of PENCIL consecutive faces along the sweep direction: the
+// thread carries the parabolas of the left cell from one face to the next, so every cell's
+// parabolas are built once per direction (plus one extra cell per pencil).
+constexpr int PENCIL = 8;
+__host__ __device__ __forceinline__ int pencil_segments(int n) { return (n + 1 + PENCIL - 1) / PENCIL; }
 
 // decode a cell index / a face index of direction D / a lattice index
 __device__ __forceinline__ void decode(long long t, int e0, int e1, int c[3]) {
@@ -148,6 +155,78 @@ __global__ void __launch_bounds__(256) kb_euler_face(const Box<T>* __restrict__ 
     long long t = (long long)tl.start[t_] + threadIdx.x;
     long long total = (long long)(B.g.n[0] + (D == 0)) * (B.g.n[1] + (D == 1)) * (B.g.n[2] + (D == 2));
     if (t < total) euler_face<T, D>(B, t);
+  }
+}
+
+// Eulerian faces i_D - 1/2 for i_D in [s PENCIL, min((s+1) PENCIL, n_D + 1)) of one pencil s; the
+// arithmetic per face is that of euler_face.
+template <typename T, int D>
+__device__ __forceinline__ void euler_pencil(const Box<T>& B, long long p) {
+  constexpr int D1 = (D + 1) % 3, D2 = (D + 2) % 3;
+  const Geom& g = B.g;
+  int ext[3] = {g.n[0], g.n[1], g.n[2]};
+  const int nf = g.n[D] + 1;
+  ext[D] = pencil_segments(g.n[D]);
+  int c[3];
+  decode(p, ext[0], ext[1], c);
+  const int f0 = c[D] * PENCIL;
+  const int f1 = f0 + PENCIL < nf ? f0 + PENCIL : nf;
+  const T tau_h = (T)B.sc->tau_h;
+  const T* qv[6] = {B.w.v[D], B.w.v[D1], B.w.v[D2], B.w.B[D1], B.w.B[D2], B.w.p};
+  auto cell_at = [&](int i) {
+    int cc[3] = {c[0], c[1], c[2]};
+    cc[D] = i;
+    return cmap(g, cc[0], cc[1], cc[2]);
+  };
+  Para<T> pl[6], pr[6];
+  {
+    long long cell[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o) cell[o] = cell_at(f0 - 3 + o);
+#pragma unroll
+    for (int v = 0; v < 6; ++v)
+      pl[v] = ppm(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
+  }
+  for (int i = f0; i < f1; ++i) {
+    long long cell[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o) cell[o] = cell_at(i - 2 + o);
+#pragma unroll
+    for (int v = 0; v < 6; ++v)
+      pr[v] = ppm(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
+    long long cl = cell[1], cr = cell[2];
+    T wl[6] = {B.s.rho[cl], B.w.p[cl], B.w.g[cl], B.w.B[D1][cl], B.w.B[D2][cl], B.w.sr[cl]};
+    T wr[6] = {B.s.rho[cr], B.w.p[cr], B.w.g[cr], B.w.B[D1][cr], B.w.B[D2][cr], B.w.sr[cr]};
+    T Bn = B.s.b[D][cr];
+    T qs[6];
+    riemann(wl, wr, Bn, pl, pr, tau_h, qs);
+    T Vn = qs[0], Vt1 = qs[1], Vt2 = qs[2], Bt1 = qs[3], Bt2 = qs[4], P = qs[5];
+    T pstar = P + T(0.5) * (Bn * Bn + Bt1 * Bt1 + Bt2 * Bt2);
+    int cf[3] = {c[0], c[1], c[2]};
+    cf[D] = i;
+    long long f = fidx(g, cf[0], cf[1], cf[2]);
+    const FaceOut<T>& fo = B.fo[D];
+    fo.f[0][f] = pstar - Bn * Bn;
+    fo.f[1][f] = -(Bn * Bt1);
+    fo.f[2][f] = -(Bn * Bt2);
+    fo.f[3][f] = pstar * Vn - Bn * (Bn * Vn + Bt1 * Vt1 + Bt2 * Vt2);
+    fo.f[4][f] = Vn;
+    fo.f[5][f] = Bn * Vt1 - Bt1 * Vn;
+    fo.f[6][f] = Bt2 * Vn - Bn * Vt2;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) pl[v] = pr[v];
+  }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) kb_euler_pencil(const Box<T>* __restrict__ boxes, Tiles tl) {
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    long long p = (long long)tl.start[t_] + threadIdx.x;
+    long long total = (long long)(D == 0 ? pencil_segments(B.g.n[0]) : B.g.n[0]) *
+                      (D == 1 ? pencil_segments(B.g.n[1]) : B.g.n[1]) *
+                      (D == 2 ? pencil_segments(B.g.n[2]) : B.g.n[2]);
+    if (p < total) euler_pencil<T, D>(B, p);
   }
 }
 
@@ -264,9 +343,14 @@ __device__ __forceinline__ void lag_face(const Box<T>& B, long long t) {
   long long f = fidx(g, c[0], c[1], c[2]);
   const int o0 = vn >= T(0) ? 0 : 1;  // upwind cell: stencil cells o0 .. o0 + 4
   const int nv = B.nv;
-  for (int v = 0; v < nv; ++v) {
+  long long st[5];
+#pragma unroll
+  for (int o = 0; o < 5; ++o) st[o] = o0 == 0 ? cell[o] : cell[o + 1];
+#pragma unroll
+  for (int v = 0; v < 7; ++v) {
+    if (v >= nv) break;
     const T* a = q[v];
-    Para<T> P = ppm(a[cell[o0]], a[cell[o0 + 1]], a[cell[o0 + 2]], a[cell[o0 + 3]], a[cell[o0 + 4]]);
+    Para<T> P = ppm(a[st[0]], a[st[1]], a[st[2]], a[st[3]], a[st[4]]);
     T qb = o0 == 0 ? avg_right_end(P, y) : avg_left_end(P, y);
     B.fo[D].f[v][f] = vn * qb;
   }
@@ -295,7 +379,9 @@ __device__ __forceinline__ void lag_update_cell(const Box<T>& B, long long c, in
   T* qq[7] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2};
   T* q0[7] = {B.s0.rho, B.s0.m[0], B.s0.m[1], B.s0.m[2], B.s0.E, B.s0.eint, B.s0.rh2};
   const int nv = B.nv;
-  for (int v = 0; v < nv; ++v) {
+#pragma unroll
+  for (int v = 0; v < 7; ++v) {
+    if (v >= nv) break;
     T acc = T(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) acc = acc + (B.fo[d].f[v][f0] - B.fo[d].f[v][fup[d]]);
@@ -357,7 +443,7 @@ __device__ __forceinline__ void post_cell(const Box<T>& B, long long c, int do_c
   decode(c, g.n[0], g.n[1], q);
   const double tau = B.sc->tau;
   if (do_chem && ph.chem)
-    s.rh2[c] = (T)chem_cell(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c], tau);
+    s.rh2[c] = (T)chem_cell<(sizeof(T) == 4)>(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c], tau);
   long long up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
   T Bc[3];
 #pragma unroll
@@ -400,8 +486,12 @@ __device__ __forceinline__ void post_cell(const Box<T>& B, long long c, int do_c
   if (!bad) {
     double rr = (double)rho;
     double pp = (gm - 1.0) * (double)eint;  // FP64 CFL of the new state (FP32 fields widened)
-    D = cfl_denominator(rr, (double)m[0] / rr, (double)m[1] / rr, (double)m[2] / rr, (double)Bc[0],
-                        (double)Bc[1], (double)Bc[2], pp, gm);
+    if (sizeof(T) == 8)
+      D = cfl_denominator(rr, (double)m[0] / rr, (double)m[1] / rr, (double)m[2] / rr, (double)Bc[0],
+                          (double)Bc[1], (double)Bc[2], pp, gm);
+    else
+      D = cfl_denominator_fast(rr, (double)m[0] / rr, (double)m[1] / rr, (double)m[2] / rr,
+                               (double)Bc[0], (double)Bc[1], (double)Bc[2], pp, gm);
   }
 }
 

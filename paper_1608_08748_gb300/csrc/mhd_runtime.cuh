@@ -26,9 +26,9 @@ inline int profile_class(int kc) {
 // profiler tags: PROF_KC_BASE + kernel class for the tiled kernels, MHD_K_SMALL for the rest
 constexpr int PROF_KC_BASE = 100;
 inline int report_class(int tag) { return tag >= PROF_KC_BASE ? profile_class(tag - PROF_KC_BASE) : tag; }
-// domain of the tiles of each kernel class (face kernels: per direction, DOM_FACE_X + d)
+// domain of the tiles of each kernel class (per-direction kernels: first of three domains)
 inline int class_domain(int kc) {
-  const int m[NKC] = {DOM_CELLS, DOM_FACE_X, DOM_LATTICE, DOM_CELLS, DOM_FACE_X, DOM_CELLS, DOM_CELLS, DOM_CELLS};
+  const int m[NKC] = {DOM_CELLS, DOM_PENCIL_X, DOM_LATTICE, DOM_CELLS, DOM_FACE_X, DOM_CELLS, DOM_CELLS, DOM_CELLS};
   return m[kc];
 }
 
@@ -93,6 +93,9 @@ long long domain_size(const Box<T>& B, int dom) {
     case DOM_FACE_X: return (long long)(g.n[0] + 1) * g.n[1] * g.n[2];
     case DOM_FACE_Y: return (long long)g.n[0] * (g.n[1] + 1) * g.n[2];
     case DOM_FACE_Z: return (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
+    case DOM_PENCIL_X: return (long long)pencil_segments(g.n[0]) * g.n[1] * g.n[2];
+    case DOM_PENCIL_Y: return (long long)g.n[0] * pencil_segments(g.n[1]) * g.n[2];
+    case DOM_PENCIL_Z: return (long long)g.n[0] * g.n[1] * pencil_segments(g.n[2]);
     default: return g.NF;
   }
 }
@@ -122,7 +125,7 @@ template <typename T>
 cudaError_t ensure_tables(Exec<T>& X) {
   for (int kc = 0; kc < NKC; ++kc) {
     int dom = class_domain(kc);
-    int ndom = (dom == DOM_FACE_X) ? 3 : 1;
+    int ndom = (dom == DOM_FACE_X || dom == DOM_PENCIL_X) ? 3 : 1;
     for (int q = 0; q < ndom; ++q) {
       cudaError_t e = ensure_table(X, dom + q, X.cfg[kc].block);
       if (e != cudaSuccess) return e;
@@ -212,9 +215,9 @@ void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
   launch_k(X, st, KC_QN, DOM_CELLS, kb_save_qn<T>, 0);
   for (int r = 0; r < 3; ++r) {
     launch_k(X, st, KC_PRIM, DOM_CELLS, kb_prim<T>);
-    launch_k(X, st, KC_EFACE, DOM_FACE_X, kb_euler_face<T, 0>);
-    launch_k(X, st, KC_EFACE, DOM_FACE_Y, kb_euler_face<T, 1>);
-    launch_k(X, st, KC_EFACE, DOM_FACE_Z, kb_euler_face<T, 2>);
+    launch_k(X, st, KC_EFACE, DOM_PENCIL_X, kb_euler_pencil<T, 0>);
+    launch_k(X, st, KC_EFACE, DOM_PENCIL_Y, kb_euler_pencil<T, 1>);
+    launch_k(X, st, KC_EFACE, DOM_PENCIL_Z, kb_euler_pencil<T, 2>);
     launch_k(X, st, KC_EDGES, DOM_LATTICE, kb_edges<T>);
     launch_k(X, st, KC_EUPD, DOM_CELLS, kb_euler_update<T>, r);
   }

@@ -168,6 +168,25 @@ def turbulence(n=128, mach=5.0, beta=1.0, seed=1, n_cm3=100.0, T_K=100.0, box_pc
     return ic
 
 
+def turbulence_from_field(v_unit, mach=5.0, beta=1.0, shift=(0, 0, 0), n_cm3=100.0, T_K=100.0,
+                          box_pc=256.0, chem=1):
+    """Turbulence initial state from a precomputed unit-rms solenoidal field (as made by
+    solenoidal_field), periodically shifted by `shift` cells (a cheap new realisation of the same
+    statistics), with the set-up of `turbulence`."""
+    gamma = 5.0 / 3.0
+    shape = v_unit.shape[1:]
+    rho = np.full(shape, float(n_cm3))
+    p0 = n_cm3 * KB_CGS * T_K / P_UNIT_CGS
+    cs = np.sqrt(gamma * p0 / n_cm3)
+    v = np.roll(v_unit, shift=tuple(int(x) for x in shift), axis=(1, 2, 3)) * (mach * cs)
+    Bz = np.sqrt(2.0 * p0 / beta)
+    B = np.stack([np.zeros(shape), np.zeros(shape), np.full(shape, Bz)])
+    ic = conserved(rho, v, np.full(shape, p0), B, gamma, np.zeros(shape))
+    ic.update(gamma=gamma, dx=box_pc / shape[2],
+              options={"bc_x": 0, "bc_y": 0, "bc_z": 0, "chem": chem})
+    return ic
+
+
 def ensemble_boxes(count=64, seed=4):
     """Box table of the batched ensemble: per box, each axis from {16, 24, ..., 96}, Mach from
     U[1, 10], beta log-uniform in [0.1, 10], turbulence seed = seed + box index."""

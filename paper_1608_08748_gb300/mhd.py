@@ -40,6 +40,18 @@ class Diag(C.Structure):
                 ("error_flags", C.c_int32)]
 
 
+class Request(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("gamma", C.c_double),
+                ("dx", C.c_double), ("precision", C.c_int), ("chem", C.c_int),
+                ("bc", C.c_int * 3), ("cfl", C.c_double), ("nsteps", C.c_int), ("state", Fields)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("steps_done", C.c_int64), ("t", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("cells", C.c_int64)]
+
+
 _lib = None
 
 
@@ -81,6 +93,17 @@ def lib():
         L.mhd_batch_get_shape.argtypes = [vp, i, C.POINTER(i), C.POINTER(i)]
         L.mhd_batch_set_shape.argtypes = [vp, i, i, i]
         L.mhd_batch_profile.argtypes = [vp, d, i, C.POINTER(d), C.POINTER(C.c_int64)]
+        L.mhd_server_create.restype = vp
+        L.mhd_server_create.argtypes = [C.c_size_t, i]
+        L.mhd_server_destroy.argtypes = [vp]
+        L.mhd_submit.restype = C.c_int64
+        L.mhd_submit.argtypes = [vp, C.POINTER(Request)]
+        L.mhd_poll.argtypes = [vp, C.c_int64, C.POINTER(Result)]
+        L.mhd_fetch.argtypes = [vp, C.c_int64, C.POINTER(Fields)]
+        L.mhd_server_drain.argtypes = [vp, d]
+        L.mhd_server_clock.restype = d
+        L.mhd_server_clock.argtypes = [vp]
+        L.mhd_server_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(i)]
         _lib = L
     return _lib
 
@@ -291,3 +314,81 @@ class Batch:
         n = (C.c_int64 * 8)()
         _check(self.L.mhd_batch_profile(self.h, float(cfl), int(steps), ms, n))
         return _profile_dict(ms, n)
+
+
+class Server:
+    """Continuous-batching request server of libmhd.so (scheduler thread in the library)."""
+
+    def __init__(self, hbm_budget_bytes, max_active=64):
+        self.L = lib()
+        self.h = self.L.mhd_server_create(int(hbm_budget_bytes), int(max_active))
+        if not self.h:
+            raise MHDError(-1, self.L.mhd_last_error().decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mhd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def submit(self, ic, nsteps, cfl=0.4, precision=1):
+        """Queue a request built from an initial-condition dict; returns its id."""
+        nz, ny, nx = ic["rho"].shape
+        opts = ic.get("options", {})
+        r = Request()
+        r.nx, r.ny, r.nz = nx, ny, nz
+        r.gamma, r.dx = float(ic["gamma"]), float(ic["dx"])
+        r.precision, r.chem = int(precision), int(opts.get("chem", 0))
+        r.bc[0], r.bc[1], r.bc[2] = int(opts.get("bc_x", 0)), int(opts.get("bc_y", 0)), int(opts.get("bc_z", 0))
+        r.cfl, r.nsteps = float(cfl), int(nsteps)
+        keep = []
+        f = Fields()
+        vals = []
+        for x in [ic["rho"], ic["mom"][0], ic["mom"][1], ic["mom"][2], ic["E"], ic["B"][0], ic["B"][1],
+                  ic["B"][2], ic.get("rho_h2")]:
+            if x is None:
+                vals.append(None)
+                continue
+            a = np.ascontiguousarray(x, dtype=np.float64)
+            keep.append(a)
+            vals.append(a.ctypes.data)
+        f.rho, f.E, f.rho_h2 = vals[0], vals[4], vals[8]
+        for q in range(3):
+            f.mom[q], f.B[q] = vals[1 + q], vals[5 + q]
+        f.dtype, f.on_device = F64, 0
+        r.state = f
+        rid = self.L.mhd_submit(self.h, C.byref(r))
+        if rid < 0:
+            raise MHDError(int(rid), self.L.mhd_last_error().decode())
+        return rid
+
+    def poll(self, rid):
+        res = Result()
+        rc = self.L.mhd_poll(self.h, int(rid), C.byref(res))
+        out = {k: getattr(res, k) for k, _ in Result._fields_}
+        return rc, out
+
+    def fetch(self, rid, shape):
+        out = {"rho": np.empty(shape), "mom": np.empty((3,) + tuple(shape)), "E": np.empty(shape),
+               "B": np.empty((3,) + tuple(shape)), "rho_h2": np.empty(shape)}
+        f = Fields()
+        f.rho, f.E, f.rho_h2 = out["rho"].ctypes.data, out["E"].ctypes.data, out["rho_h2"].ctypes.data
+        for q in range(3):
+            f.mom[q] = out["mom"][q].ctypes.data
+            f.B[q] = out["B"][q].ctypes.data
+        f.dtype, f.on_device = F64, 0
+        _check(self.L.mhd_fetch(self.h, int(rid), C.byref(f)))
+        return out
+
+    def drain(self, timeout_s=600.0):
+        _check(self.L.mhd_server_drain(self.h, float(timeout_s)))
+
+    def clock(self):
+        return self.L.mhd_server_clock(self.h)
+
+    def stats(self):
+        it, pb, pa = C.c_int64(0), C.c_int64(0), C.c_int(0)
+        _check(self.L.mhd_server_stats(self.h, C.byref(it), C.byref(pb), C.byref(pa)))
+        return {"iterations": it.value, "peak_bytes": pb.value, "peak_active": pa.value}

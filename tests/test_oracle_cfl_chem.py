@@ -64,7 +64,7 @@ def test_app_d_rates_golden(oracle_mod, row):
     name, T, nH, nH2, val, tol = row
     s = oracle_mod.Sim(4, 4, 4, 5 / 3, 1.0, chem=1)
     r = s.chem_rates(T, nH, nH2)
-    assert r[name] == pytest.approx(val, rel=tol)
+    assert r[name] == pytest.approx(val, rel=tol, abs=0)
 
 
 
@@ -90,10 +90,10 @@ def test_chemistry_update_limits_and_exact_solution(oracle_mod):
     for tau in [1e-6, 1e-7]:
         out = s.chem_cell(rho, eint, rh2, tau)
         dn = 0.5 * out["rho_h2"] - n0
-        assert dn == pytest.approx(tau * T0 * (C - D * n0), rel=1e-3 * (1 + 1e6 * tau))
+        assert dn == pytest.approx(tau * T0 * (C - D * n0), rel=1e-3 * (1 + 1e6 * tau), abs=0)
     # tau -> infinity: the fixed point C / D
     out = s.chem_cell(rho, eint, rh2, 1e12)
-    assert 0.5 * out["rho_h2"] == pytest.approx(min(C / D, 0.5 * rho), rel=1e-9)
+    assert 0.5 * out["rho_h2"] == pytest.approx(min(C / D, 0.5 * rho), rel=1e-9, abs=0)
     # frozen-rate exact solution n(t) = C/D + (n0 - C/D) exp(-D t); the local error of one
     # backward-Euler step is O(tau^2)
     errs = []

@@ -1,0 +1,115 @@
+"""The oracle's pins catch plausible mistakes: each case plants one mistake (a dropped term, a
+wrong sign, a transposed operand or index) in a copy of oracle/mhd_oracle.c, builds it, and
+checks that at least one pin fails against the mutant.  Everything runs on the CPU."""
+import importlib.util
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mhd_oracle.c")
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+import test_oracle_cfl_chem as T_cc  # noqa: E402
+import test_oracle_physics as T_ph  # noqa: E402
+import test_oracle_ppm as T_ppm  # noqa: E402
+import test_oracle_riemann as T_rs  # noqa: E402
+
+# (name, text in mhd_oracle.c, replacement)
+MUTATIONS = [
+    ("ppm_delta_sign", "P.d = qR - qL;", "P.d = qL - qR;"),
+    ("slope_factor_dropped", "b = 2.0 * fabs(dp)", "b = fabs(dp)"),
+    ("edge_value_sixth_sign", "qR = 0.5 * (q[2] + q[3]) - (dmp - dm0) * SIXTH;",
+     "qR = 0.5 * (q[2] + q[3]) + (dmp - dm0) * SIXTH;"),
+    ("dod_average_sign", "return P.R - 0.5 * y * (P.d - P.q6 * (1.0 - TWO_THIRDS * y));",
+     "return P.R - 0.5 * y * (P.d + P.q6 * (1.0 - TWO_THIRDS * y));"),
+    ("right_eigvec_slow_p_sign", "{as * cs, af * cf * by * sg, af * cf * bz * sg, -af * sc * by, -af * sc * bz, as * gp},",
+     "{as * cs, af * cf * by * sg, af * cf * bz * sg, -af * sc * by, -af * sc * bz, -as * gp},"),
+    ("left_alfven_sign_dropped", "{0.0, -bz * sg * INV_SQRT2, by * sg * INV_SQRT2, bz * isr2, -by * isr2, 0.0},",
+     "{0.0, -bz * INV_SQRT2, by * INV_SQRT2, bz * isr2, -by * isr2, 0.0},"),
+    ("upwind_sides_swapped", "double qb = (k % 2 == 0) ? avg_right_end(pl[m], y) : avg_left_end(pr[m], y);",
+     "double qb = (k % 2 == 1) ? avg_right_end(pl[m], y) : avg_left_end(pr[m], y);"),
+    ("energy_flux_term_dropped", "s->fo[3][cr] = pstar * Vn - Bn * (Bn * Vn + Bt1 * Vt1 + Bt2 * Vt2);",
+     "s->fo[3][cr] = pstar * Vn - Bn * (Bn * Vn + Bt1 * Vt1);"),
+    ("momentum_tension_dropped", "s->fo[0][cr] = pstar - Bn * Bn;", "s->fo[0][cr] = pstar;"),
+    ("ct_curl_sign", "double Rb = curl * ih;", "double Rb = -curl * ih;"),
+    ("emf_component_transposed", "s->eA[d][cr] = Bn * Vt1 - Bt1 * Vn;", "s->eA[d][cr] = Bn * Vt2 - Bt2 * Vn;"),
+    ("eint_source_sign", "R[4] = ((g_cell - 1.0) * s->eint[c]) * (s->acc[4][c] * ih);",
+     "R[4] = -((g_cell - 1.0) * s->eint[c]) * (s->acc[4][c] * ih);"),
+    ("lagrangian_upwind_reversed", "if (vn >= 0.0) {\n              for (int o = 0; o < 5; ++o) st[o] = q[v][cl + (o - 2) * sd];",
+     "if (vn < 0.0) {\n              for (int o = 0; o < 5; ++o) st[o] = q[v][cl + (o - 2) * sd];"),
+    ("rk_weights_transposed", "static const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};",
+     "static const double RK_A[3] = {0.0, 0.25, 1.0 / 3.0};"),
+    ("cfl_fast_speed_dropped", "double D = v + b + c + ca + cs + cf;", "double D = v + b + c + ca + cs;"),
+    ("chem_photodissociation_dropped", "r.D = (r.k2 * nH + r.k3 * nH2) + r.k4;", "r.D = (r.k2 * nH + r.k3 * nH2);"),
+    ("k1_temperature_power", "double s2 = sqrt(t2);", "double s2 = t2;"),
+    ("regularisation_half_dropped", "double kin = 0.5 * m2 / r;", "double kin = m2 / r;"),
+    ("gamma_eff_weights_swapped", "return (5.0 * nH + 7.0 * nH2) / (3.0 * nH + 5.0 * nH2);",
+     "return (7.0 * nH + 5.0 * nH2) / (5.0 * nH + 3.0 * nH2);"),
+    ("face_b_average_index", "s->b[d][c] = 0.5 * (Bc[d][srclo] + Bc[d][src]);", "s->b[d][c] = Bc[d][src];"),
+]
+
+
+def load_mutant(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"{name}: pattern must occur exactly once"
+    csrc = tmp_path / f"{name}.c"
+    csrc.write_text(src.replace(old, new))
+    lib = tmp_path / f"lib{name}.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", str(lib),
+                    str(csrc), "-lm"], check=True)
+    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{name}", os.path.join(ROOT, "oracle", "oracle.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod._LIB = str(lib)
+    mod.build = lambda force=False: str(lib)
+    return mod
+
+
+def pins(O):
+    """A fast selection of the pins, each run against module O."""
+    st = T_rs.random_states(5, 7)
+    yield "eigen", lambda: [T_rs.test_eigen_identities(O, s, 1e-11) for s in st]
+    yield "linear_riemann", lambda: [T_rs.test_flat_riemann_matches_numpy_linear_solution(O, k) for k in range(3)]
+    yield "acoustic", lambda: [T_rs.test_acoustic_limit(O, k) for k in range(2)]
+    yield "appB", lambda: [T_rs.test_appendix_B_expansion(O, k) for k in range(2)]
+    yield "ppm_linear", lambda: T_ppm.test_linear_data_exact_edges(O)
+    yield "ppm_average", lambda: T_ppm.test_cell_average_and_endpoints(O)
+    yield "ppm_dod", lambda: T_ppm.test_domain_of_dependence_averages_match_quadrature(O)
+    yield "cfl", lambda: [T_cc.test_cfl_denominator_closed_form(O, s) for s in
+                          [(1.0, [0, 0, 0], [0.75, 1.0, 0.0], 1.0, 2.0)]]
+    yield "gamma", lambda: T_cc.test_gamma_eff_limits(O)
+    yield "rates", lambda: [T_cc.test_app_d_rates_golden(O, r) for r in T_cc._golden()]
+    yield "chem_solver", lambda: T_cc.test_chemistry_update_limits_and_exact_solution(O)
+    yield "conservation", lambda: T_ph.test_periodic_conservation_and_div_b(O)
+    yield "uniform", lambda: T_ph.test_uniform_state_is_stationary(O)
+    yield "waves", lambda: [T_ph.test_linear_wave_first_order_convergence(O, k) for k in ["fast", "alfven", "slow", "entropy"]]
+    yield "sod", lambda: T_ph.test_sod_converges_to_exact_solution(O)
+    yield "ot_symmetry", lambda: T_ph.test_orszag_tang_point_symmetry(O)
+    yield "oblique_waves", lambda: [T_ph.test_oblique_linear_wave_converges(O, k) for k in ["fast", "alfven"]]
+    yield "regularisation", lambda: T_ph.test_regularisation_restores_the_energy_closure(O)
+    yield "faces_from_cells", lambda: T_ph.test_faces_from_linear_cell_field_are_midpoint_values(O)
+
+
+def first_failing_pin(O):
+    for name, fn in pins(O):
+        try:
+            fn()
+        except Exception:  # an assertion, or a non-physical state the oracle reports
+            return name
+    return None
+
+
+def test_unmutated_oracle_passes_the_selection(tmp_path):
+    O = load_mutant(tmp_path, "none", "#define NG 4", "#define NG 4")
+    assert first_failing_pin(O) is None
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_mutation_is_caught(tmp_path, name, old, new):
+    O = load_mutant(tmp_path, name, old, new)
+    caught = first_failing_pin(O)
+    assert caught is not None, f"mutation {name} survived every pin"

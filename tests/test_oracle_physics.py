@@ -255,3 +255,99 @@ def test_orszag_tang_point_symmetry(oracle_mod):
     s = oracle_mod.run(I.orszag_tang(n, nz=1), steps=25)
     rho = s.get_state()["rho"][0]
     assert np.abs(rho - rho[::-1, ::-1]).max() <= 1e-12 * rho.max()
+
+
+# ---------------------------------------------------------------------------- multi-D waves
+def oblique_wave_ic(n, kind, amp=1e-6, gamma=5 / 3, B0=(1.0, np.sqrt(2.0), 0.5)):
+    """Linear wave travelling along (1, 1, 0)/sqrt(2) in an n x n x 1 periodic box (wavelength
+    1/sqrt(2)), eigenvector from numpy for the wave-frame background B0 = (B_n, B_t1, B_t2)."""
+    rho0, p0 = 1.0, 1.0 / gamma
+    Bn, Bt1, Bt2 = B0
+    Bm = np.array([[0, 0, 0, Bt1 / rho0, Bt2 / rho0, 1 / rho0], [0, 0, 0, -Bn / rho0, 0, 0],
+                   [0, 0, 0, 0, -Bn / rho0, 0], [Bt1, -Bn, 0, 0, 0, 0], [Bt2, 0, -Bn, 0, 0, 0],
+                   [gamma * p0, 0, 0, 0, 0, 0]])
+    w, V = np.linalg.eig(Bm)
+    w, V = w.real, V.real
+    j = np.argsort(-w)[{"fast": 0, "alfven": 1}[kind]]
+    speed, r = w[j], V[:, j] / np.abs(V[:, j]).max()
+    kh = np.array([1.0, 1.0, 0.0]) / np.sqrt(2.0)
+    t1 = np.array([-1.0, 1.0, 0.0]) / np.sqrt(2.0)
+    t2 = np.array([0.0, 0.0, 1.0])
+    h = 1.0 / n
+    xc = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(xc, xc, indexing="xy")  # [j][i]
+    f = (np.cos(2 * np.pi * (X + Y)) * np.sinc(h) ** 2)[None]  # cell averages
+    shape = (1, n, n)
+    rho = rho0 + amp * rho0 * r[0] / speed * f
+    v = amp * f[None] * (r[0] * kh + r[1] * t1 + r[2] * t2)[:, None, None, None]
+    B = (Bn * kh + Bt1 * t1 + Bt2 * t2)[:, None, None, None] + amp * f[None] * (r[3] * t1 + r[4] * t2)[:, None, None, None]
+    B = np.broadcast_to(B, (3,) + shape).copy()
+    p = p0 + amp * r[5] * f
+    ic = I.conserved(rho, v, p, B, gamma)
+    ic.update(gamma=gamma, dx=h, options={"bc_x": 0, "bc_y": 0, "bc_z": 0, "chem": 0})
+    return ic, (1.0 / np.sqrt(2.0)) / speed  # one period: the wavelength along the diagonal / speed
+
+
+@pytest.mark.parametrize("kind", ["fast", "alfven"])
+def test_oblique_linear_wave_converges(oracle_mod, kind):
+    """The diagonal wave needs every multi-D term (B_n varies along n, CT uses both face families)."""
+    errs = []
+    for n in [16, 32]:
+        ic, period = oblique_wave_ic(n, kind)
+        s = oracle_mod.run(ic, t_end=period)
+        st = s.get_state()
+        errs.append(sum(np.abs(a - b).mean() for a, b in zip(fields(st).values(), fields(ic).values())) / 1e-6)
+    assert errs[0] < 0.8
+    assert errs[1] < 0.7 * errs[0], errs
+
+
+# ---------------------------------------------------------------------------- regularisation
+def test_regularisation_restores_the_energy_closure(oracle_mod):
+    """Sec. 2.9 on cells whose stored rho eps disagrees with rho E: where the thermal fraction is
+    >= 1e-3 and rho eps is too low, rho eps becomes rho E - rho v^2/2 - B^2/2; where the thermal
+    fraction is < 1e-3 the speed is rescaled (direction kept).  Either way the closure
+    rho E = rho eps + rho v^2/2 + B^2/2 of Sec. 2 holds afterwards."""
+    ic = I.turbulence(8, mach=2.0, seed=17, shape=(6, 7, 8))
+    s = oracle_mod.run(ic, chem=0)
+    full = s.get_full()
+    st = s.get_state()
+    kin = 0.5 * (st["mom"] ** 2).sum(0) / st["rho"]
+    mag = 0.5 * (st["B"] ** 2).sum(0)
+    e_true = st["E"] - kin - mag
+    eint = 0.5 * e_true  # too low everywhere: the entropy branch must raise it
+    fast = np.zeros(eint.shape, bool)
+    fast[0, :3, :4] = True  # here: kinetic-dominated cells (thermal fraction < 1e-3)
+    E = st["E"].copy()
+    E[fast] = kin[fast] + mag[fast] + 1e-6 * (kin[fast] + mag[fast])
+    eint[fast] = 0.4e-6 * (kin[fast] + mag[fast])
+    ic2 = dict(ic, E=E)
+    s2 = oracle_mod.run(ic2, chem=0)
+    s2.set_full(eint, full["bface"])
+    s2.stage(4, 1.0)
+    out, out_full = s2.get_state(), s2.get_full()
+    kin2 = 0.5 * (out["mom"] ** 2).sum(0) / out["rho"]
+    closure = out["E"] - out_full["eint"] - kin2 - 0.5 * (out["B"] ** 2).sum(0)
+    assert np.abs(closure).max() <= 1e-12 * np.abs(out["E"]).max()
+    assert np.allclose(out_full["eint"][~fast], (E - kin - mag)[~fast], rtol=1e-12, atol=0)
+    assert np.array_equal(out_full["eint"][fast], eint[fast])  # rho eps kept, speed rescaled
+    cosang = (out["mom"] * st["mom"]).sum(0) / np.sqrt((out["mom"] ** 2).sum(0) * (st["mom"] ** 2).sum(0))
+    assert np.allclose(cosang[fast], 1.0, atol=1e-12)
+    assert s2.diag()["vel_branch"] == fast.sum()
+
+
+def test_faces_from_linear_cell_field_are_midpoint_values(oracle_mod):
+    """A17: faces from a cell-centred field; for a field linear along its own axis the face value
+    is the field at the face, x_{i-1/2} (interior faces of an outflow axis)."""
+    n = 10
+    ic = I.uniform(n, n, n, rho=1.0, p=1.0, B=(0.0, 0.0, 0.0))
+    xc = (np.arange(n) + 0.5) / n
+    ic["B"][0] = (1.0 + 0.3 * xc)[None, None, :] * np.ones((n, n, n))
+    ic["B"][1] = (2.0 - 0.7 * xc)[None, :, None] * np.ones((n, n, n))
+    ic["B"][2] = (0.5 + 1.1 * xc)[:, None, None] * np.ones((n, n, n))
+    ic["options"] = {"bc_x": 1, "bc_y": 1, "bc_z": 1, "chem": 0}
+    s = oracle_mod.run(ic)
+    bf = s.get_full()["bface"]
+    xf = np.arange(1, n) / n  # interior face positions i - 1/2, i = 1..n-1
+    assert np.allclose(bf[0][:, :, 1:], (1.0 + 0.3 * xf)[None, None, :], rtol=0, atol=1e-14)
+    assert np.allclose(bf[1][:, 1:, :], (2.0 - 0.7 * xf)[None, :, None], rtol=0, atol=1e-14)
+    assert np.allclose(bf[2][1:, :, :], (0.5 + 1.1 * xf)[:, None, None], rtol=0, atol=1e-14)
