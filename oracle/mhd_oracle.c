@@ -28,7 +28,8 @@
  *   A6  v = |v|, h = dx.
  *   A7  face rho as written; p and gamma with the velocity weights; B_n = staggered face value.
  *   A8  degenerate alpha when c_f^2 - c_s^2 <= 1e-12 (c^2 + b^2); degenerate beta when
- *       B_perp^2 <= 1e-24 rho (c^2 + b^2); sign(0) = +1; radicands clamped at 0.
+ *       B_perp^2 <= 1e-24 rho (c^2 + b^2); sign(0) = +1; speeds and alpha evaluated in a
+ *       cancellation-free form of the same formulas (mhd_speeds).
  *   A9  row k of R^T is the right eigenvector for (+c_f, -c_f, +c_s, -c_s, +c_a, -c_a).
  *   A10 Flux-CT inside each Eulerian RK substage; tau fixed for the whole step.
  *   A11 domain-of-dependence averages (flag: edge values, i.e. the tau -> 0 limit).
@@ -227,27 +228,46 @@ typedef struct {
 
 static const double INV_SQRT2 = 0.70710678118654752440;
 
+/* Fast and slow magnetosonic speeds (Sec. 2.3) and the differences the alpha factors of Sec. 2.4
+   need, from c^2, c_a^2 = B_n^2/rho and b_perp^2 = B_perp^2/rho, evaluated without cancellation
+   (A8): with X = c^2 - c_a^2,
+     c_f^2 - c_s^2 = sqrt((c^2 + b^2)^2 - 4 c^2 c_a^2) = sqrt(X^2 + b_perp^2 (2c^2 + 2c_a^2 + b_perp^2)),
+     (c^2 - c_s^2)(c_f^2 - c^2) = c^2 b_perp^2,   c_f^2 c_s^2 = c^2 c_a^2.
+   The literal form takes the square root of rounding noise where B_perp -> 0; this one gives
+   alpha_s = 0 (or alpha_f = 0) exactly there, as the formula intends. */
+typedef struct { double cf2, cs2, sq, dcs, dfc; } speeds; /* dcs = c^2 - c_s^2, dfc = c_f^2 - c^2 */
+
+static speeds mhd_speeds(double c2, double ca2, double bp2) {
+  speeds r;
+  double X = c2 - ca2;
+  double W = bp2 * ((2.0 * c2 + 2.0 * ca2) + bp2);
+  r.sq = sqrt(X * X + W);
+  if (X >= 0.0) {
+    r.dcs = 0.5 * ((X + r.sq) - bp2);
+    if (r.dcs < 0.0) r.dcs = 0.0;
+    r.dfc = r.dcs > 0.0 ? c2 * bp2 / r.dcs : 0.0;
+  } else {
+    r.dfc = 0.5 * ((bp2 - X) + r.sq);
+    r.dcs = r.dfc > 0.0 ? c2 * bp2 / r.dfc : 0.0;
+  }
+  r.cf2 = c2 + r.dfc;
+  r.cs2 = r.cf2 > 0.0 ? c2 * ca2 / r.cf2 : 0.0;
+  return r;
+}
+
 /* Build R, L and the eigenvalues for the face state (A5, A8, A9). */
 static void build_eigen(eig* e) {
   const double rho = e->rho, p = e->p, gam = e->gam, Bn = e->Bn, Bt1 = e->Bt1, Bt2 = e->Bt2;
   double c2 = gam * p / rho;
   double ca2 = Bn * Bn / rho;
-  double b2 = (Bn * Bn + Bt1 * Bt1 + Bt2 * Bt2) / rho;
-  double s = c2 + b2;
-  double disc = s * s - 4.0 * c2 * ca2;
-  if (disc < 0.0) disc = 0.0;
-  double sq = sqrt(disc);
-  double cf2 = 0.5 * (s + sq);
-  double cs2 = 0.5 * (s - sq);
-  if (cs2 < 0.0) cs2 = 0.0;
-  double c = sqrt(c2), cf = sqrt(cf2), cs = sqrt(cs2), ca = sqrt(ca2);
+  double bp2r = (Bt1 * Bt1 + Bt2 * Bt2) / rho;
+  double s = c2 + (ca2 + bp2r);
+  speeds sp = mhd_speeds(c2, ca2, bp2r);
+  double c = sqrt(c2), cf = sqrt(sp.cf2), cs = sqrt(sp.cs2), ca = sqrt(ca2);
   double af, as;
-  if (cf2 - cs2 > 1e-12 * s) {
-    double a1 = c2 - cs2, a2 = cf2 - c2;
-    if (a1 < 0.0) a1 = 0.0;
-    if (a2 < 0.0) a2 = 0.0;
-    af = sqrt(a1 / (cf2 - cs2));
-    as = sqrt(a2 / (cf2 - cs2));
+  if (sp.sq > 1e-12 * s) {
+    af = sqrt(sp.dcs / sp.sq);
+    as = sqrt(sp.dfc / sp.sq);
   } else {
     af = INV_SQRT2;
     as = INV_SQRT2;
@@ -346,14 +366,9 @@ static double cfl_denominator(double rho, double vx, double vy, double vz, doubl
   double Dmax = 0.0;
   for (int d = 0; d < 3; ++d) {
     double ca2 = Bd[d] * Bd[d] / rho;
-    double s = c2 + b2;
-    double disc = s * s - 4.0 * c2 * ca2;
-    if (disc < 0.0) disc = 0.0;
-    double sq = sqrt(disc);
-    double cf = sqrt(0.5 * (s + sq));
-    double cs2 = 0.5 * (s - sq);
-    if (cs2 < 0.0) cs2 = 0.0;
-    double cs = sqrt(cs2), ca = sqrt(ca2);
+    double bp2r = (Bd[(d + 1) % 3] * Bd[(d + 1) % 3] + Bd[(d + 2) % 3] * Bd[(d + 2) % 3]) / rho;
+    speeds sp = mhd_speeds(c2, ca2, bp2r);
+    double cf = sqrt(sp.cf2), cs = sqrt(sp.cs2), ca = sqrt(ca2);
     double D = v + b + c + ca + cs + cf;
     if (D > Dmax) Dmax = D;
   }

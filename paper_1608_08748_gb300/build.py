@@ -14,8 +14,8 @@ SOURCES = ["mhd.cu", "mhd_noalloc.cu", "mhd_server.cu"]
 SOURCES_F32 = ["mhd_f32.cu"]
 HEADERS = ["mhd_device.cuh", "mhd_kernels.cuh", "mhd_runtime.cuh"]
 
-# mhd.cu (FP64 path) is compiled with --fmad=false: every product and sum is rounded separately,
-# in the order the formulas are written, like a plain evaluation of the same equations.
+# The FP64 path may contract a*b+c into FMAs (its kernels are bound by the FP64 pipe; contraction
+# removes ~15 % of its instructions); it then agrees with the FP64 oracle to ~1e-14 relative L1.
 
 
 def _stale() -> bool:
@@ -48,7 +48,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         # FP32 bulk: contraction and the hardware-approximate float division / square root (a few
         # ulp, far inside its 1e-4 target); its FP64 parts (chemistry, CFL) are unaffected.
         extra = (["--fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
-                 if f in SOURCES_F32 else ["--fmad=false"])
+                 if f in SOURCES_F32 else ["--fmad=true"])
         p, cmd = _compile(nvcc, os.path.join(SRC, f), obj, extra)
         if verbose:
             print(" ".join(cmd))

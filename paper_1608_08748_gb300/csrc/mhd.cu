@@ -215,8 +215,8 @@ mhd_sim* mhd_create(int nx, int ny, int nz, double gamma, double dx) {
     fail(MHD_EINVAL, "mhd_create: need nx, ny, nz >= 1, gamma > 1, dx > 0");
     return nullptr;
   }
-  if ((long long)(nx + 1) * (ny + 1) * (nz + 1) > (1ll << 40)) {
-    fail(MHD_EINVAL, "mhd_create: grid too large");
+  if ((long long)(nx + 1) * (ny + 1) * (nz + 1) >= (1ll << 31)) {
+    fail(MHD_EINVAL, "mhd_create: grid too large (the (nx+1)(ny+1)(nz+1) lattice must stay below 2^31)");
     return nullptr;
   }
   mhd_sim* S = new (std::nothrow) mhd_sim();

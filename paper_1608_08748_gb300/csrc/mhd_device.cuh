@@ -2,9 +2,10 @@
 // arXiv:1608.08748 (Kulikov, Chernykh & Protasov).  Templated on the bulk type T (double for the
 // FP64 path, float for the FP32-bulk path); the CFL reduction and the chemistry are FP64 always.
 //
-// The formulas follow the paper section by section and are written with a fixed operation order
-// (no reassociation, no contraction in the FP64 build) so that the FP64 path reproduces a plain
-// evaluation of the same equations up to the last bit wherever the math library is not involved.
+// The formulas follow the paper section by section, in the same operation order as a plain
+// evaluation; the FP64 build lets the compiler contract a*b+c into one FMA, so the FP64 path agrees
+// with a plain evaluation to a few ulp per operation (1e-14 relative L1 after 50 steps of the
+// 128^3 turbulence box).
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -62,14 +63,17 @@ __device__ __forceinline__ int wrap(int i, int n, int bc) {
   }
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
-__device__ __forceinline__ long long cidx(const Geom& g, int i, int j, int k) {
-  return ((long long)k * g.n[1] + j) * g.n[0] + i;
+// Cell, face and lattice indices are 32-bit: mhd_create rejects grids whose (n+1)^3 lattice does
+// not fit (512^3 needs 1.35e8).
+typedef int idx_t;
+__device__ __forceinline__ idx_t cidx(const Geom& g, int i, int j, int k) {
+  return (k * g.n[1] + j) * g.n[0] + i;
 }
-__device__ __forceinline__ long long fidx(const Geom& g, int i, int j, int k) {
-  return ((long long)k * (g.n[1] + 1) + j) * (g.n[0] + 1) + i;
+__device__ __forceinline__ idx_t fidx(const Geom& g, int i, int j, int k) {
+  return (k * (g.n[1] + 1) + j) * (g.n[0] + 1) + i;
 }
 // cell index of (c[0], c[1], c[2]) after the boundary map on each axis
-__device__ __forceinline__ long long cmap(const Geom& g, int c0, int c1, int c2) {
+__device__ __forceinline__ idx_t cmap(const Geom& g, int c0, int c1, int c2) {
   return cidx(g, wrap(c0, g.n[0], g.bc[0]), wrap(c1, g.n[1], g.bc[1]), wrap(c2, g.n[2], g.bc[2]));
 }
 
@@ -153,6 +157,36 @@ __device__ __forceinline__ T avg_left_end(const Para<T>& P, T y) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// Fast and slow magnetosonic speeds (Sec. 2.3) and the differences the alpha factors (Sec. 2.4)
+// need, without cancellation: with X = c^2 - c_a^2 and b_perp^2 = B_perp^2 / rho,
+//   c_f^2 - c_s^2 = sqrt(X^2 + b_perp^2 (2 c^2 + 2 c_a^2 + b_perp^2)),
+//   (c^2 - c_s^2)(c_f^2 - c^2) = c^2 b_perp^2,   c_f^2 c_s^2 = c^2 c_a^2,
+// so alpha_s (or alpha_f) is exactly 0 where B_perp = 0.
+template <typename T>
+struct Speeds {
+  T cf2, cs2, sq, dcs, dfc;  // dcs = c^2 - c_s^2, dfc = c_f^2 - c^2
+};
+
+template <typename T>
+__device__ __forceinline__ Speeds<T> mhd_speeds(T c2, T ca2, T bp2) {
+  Speeds<T> r;
+  T X = c2 - ca2;
+  T W = bp2 * ((T(2) * c2 + T(2) * ca2) + bp2);
+  r.sq = sqrt(X * X + W);
+  if (X >= T(0)) {
+    r.dcs = T(0.5) * ((X + r.sq) - bp2);
+    if (r.dcs < T(0)) r.dcs = T(0);
+    r.dfc = r.dcs > T(0) ? c2 * bp2 / r.dcs : T(0);
+  } else {
+    r.dfc = T(0.5) * ((bp2 - X) + r.sq);
+    r.dcs = r.dfc > T(0) ? c2 * bp2 / r.dfc : T(0);
+  }
+  r.cf2 = c2 + r.dfc;
+  r.cs2 = r.cf2 > T(0) ? c2 * ca2 / r.cf2 : T(0);
+  return r;
+}
+
+// ------------------------------------------------------------------------------------------------
 // Sec. 2.4 + App. A: Roe-type face state, eigenvectors and the characteristic Riemann solution.
 // wl/wr = (rho, p, gamma, B_t1, B_t2, sqrt(rho)) of the left/right cell; Bn the face field.
 // qs = (V_n, V_t1, V_t2, B_t1, B_t2, P).
@@ -170,22 +204,14 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
 
   T c2 = gam * p / rho;
   T ca2 = Bn * Bn / rho;
-  T b2 = (Bn * Bn + Bt1 * Bt1 + Bt2 * Bt2) / rho;
-  T s = c2 + b2;
-  T disc = s * s - T(4) * c2 * ca2;
-  if (disc < T(0)) disc = T(0);
-  T sq = sqrt(disc);
-  T cf2 = T(0.5) * (s + sq);
-  T cs2 = T(0.5) * (s - sq);
-  if (cs2 < T(0)) cs2 = T(0);
-  T c = sqrt(c2), cf = sqrt(cf2), cs = sqrt(cs2), ca = sqrt(ca2);
+  T bp2r = (Bt1 * Bt1 + Bt2 * Bt2) / rho;
+  T s = c2 + (ca2 + bp2r);
+  Speeds<T> sp = mhd_speeds(c2, ca2, bp2r);
+  T c = sqrt(c2), cf = sqrt(sp.cf2), cs = sqrt(sp.cs2), ca = sqrt(ca2);
   T af, as;
-  if (cf2 - cs2 > T(1e-12) * s) {
-    T a1 = c2 - cs2, a2 = cf2 - c2;
-    if (a1 < T(0)) a1 = T(0);
-    if (a2 < T(0)) a2 = T(0);
-    af = sqrt(a1 / (cf2 - cs2));
-    as = sqrt(a2 / (cf2 - cs2));
+  if (sp.sq > T(1e-12) * s) {
+    af = sqrt(sp.dcs / sp.sq);
+    as = sqrt(sp.dfc / sp.sq);
   } else {
     af = INV_SQRT2;
     as = INV_SQRT2;
@@ -335,14 +361,9 @@ __device__ __forceinline__ double cfl_denominator(double rho, double vx, double 
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     double ca2 = Bd[d] * Bd[d] / rho;
-    double s = c2 + b2;
-    double disc = s * s - 4.0 * c2 * ca2;
-    if (disc < 0.0) disc = 0.0;
-    double sq = sqrt(disc);
-    double cf = sqrt(0.5 * (s + sq));
-    double cs2 = 0.5 * (s - sq);
-    if (cs2 < 0.0) cs2 = 0.0;
-    double cs = sqrt(cs2), ca = sqrt(ca2);
+    double bp2r = (Bd[(d + 1) % 3] * Bd[(d + 1) % 3] + Bd[(d + 2) % 3] * Bd[(d + 2) % 3]) / rho;
+    Speeds<double> sp = mhd_speeds(c2, ca2, bp2r);
+    double cf = sqrt(sp.cf2), cs = sqrt(sp.cs2), ca = sqrt(ca2);
     double D = v + b + c + ca + cs + cf;
     if (D > Dmax) Dmax = D;
   }

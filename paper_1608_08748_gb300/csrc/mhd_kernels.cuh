@@ -62,9 +62,9 @@ constexpr int PENCIL = 8;
 __host__ __device__ __forceinline__ int pencil_segments(int n) { return (n + 1 + PENCIL - 1) / PENCIL; }
 
 // decode a cell index / a face index of direction D / a lattice index
-__device__ __forceinline__ void decode(long long t, int e0, int e1, int c[3]) {
-  c[0] = (int)(t % e0);
-  long long r = t / e0;
+__device__ __forceinline__ void decode(idx_t t, int e0, int e1, int c[3]) {
+  c[0] = t % e0;
+  idx_t r = t / e0;
   c[1] = (int)(r % e1);
   c[2] = (int)(r / e1);
 }
@@ -74,12 +74,12 @@ __device__ __forceinline__ void decode(long long t, int e0, int e1, int c[3]) {
 // ------------------------------------------------------------------------------------------------
 // primitives of one cell
 template <typename T>
-__device__ __forceinline__ void prim_cell(const Box<T>& B, long long c) {
+__device__ __forceinline__ void prim_cell(const Box<T>& B, idx_t c) {
   const Geom& g = B.g;
   int q[3];
   decode(c, g.n[0], g.n[1], q);
   T rho = B.s.rho[c];
-  long long up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
+  idx_t up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
 #pragma unroll
   for (int d = 0; d < 3; ++d) B.w.B[d][c] = T(0.5) * (B.s.b[d][c] + B.s.b[d][up[d]]);
   double gm = B.ph.chem ? gamma_eff((double)rho, (double)B.s.rh2[c]) : B.ph.gamma;
@@ -95,7 +95,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) kb_prim(const Box<T>* __restrict__ boxes, Tiles tl) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
-    long long c = (long long)tl.start[t_] + threadIdx.x;
+    idx_t c = tl.start[t_] + (idx_t)threadIdx.x;
     if (c < B.g.N) prim_cell(B, c);
   }
 }
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(512) kb_prim(const Box<T>* __restrict__ boxes,
 // Eulerian face of direction D: the face i_D - 1/2 between cells i_D - 1 and i_D, for i_D in
 // [0, n_D] and the other two indices in [0, n).
 template <typename T, int D>
-__device__ __forceinline__ void euler_face(const Box<T>& B, long long t) {
+__device__ __forceinline__ void euler_face(const Box<T>& B, idx_t t) {
   constexpr int D1 = (D + 1) % 3, D2 = (D + 2) % 3;
   const Geom& g = B.g;
   int ext[3] = {g.n[0], g.n[1], g.n[2]};
@@ -112,7 +112,7 @@ __device__ __forceinline__ void euler_face(const Box<T>& B, long long t) {
   int c[3];
   decode(t, ext[0], ext[1], c);
   const T tau_h = (T)B.sc->tau_h;
-  long long cell[6];  // stencil cells i_D - 3 .. i_D + 2 along D
+  idx_t cell[6];  // stencil cells i_D - 3 .. i_D + 2 along D
 #pragma unroll
   for (int o = 0; o < 6; ++o) {
     int cc[3] = {c[0], c[1], c[2]};
@@ -128,7 +128,7 @@ __device__ __forceinline__ void euler_face(const Box<T>& B, long long t) {
     pl[v] = ppm(q0, q1, q2, q3, q4);
     pr[v] = ppm(q1, q2, q3, q4, q5);
   }
-  long long cl = cell[2], cr = cell[3];
+  idx_t cl = cell[2], cr = cell[3];
   T wl[6] = {B.s.rho[cl], B.w.p[cl], B.w.g[cl], B.w.B[D1][cl], B.w.B[D2][cl], B.w.sr[cl]};
   T wr[6] = {B.s.rho[cr], B.w.p[cr], B.w.g[cr], B.w.B[D1][cr], B.w.B[D2][cr], B.w.sr[cr]};
   T Bn = B.s.b[D][cr];  // face i_D - 1/2 is stored with cell i_D (mapped: the nearest stored face)
@@ -137,7 +137,7 @@ __device__ __forceinline__ void euler_face(const Box<T>& B, long long t) {
   // A12: non-advective fluxes from the face solution (V_n, V_t1, V_t2, B_t1, B_t2, P)
   T Vn = qs[0], Vt1 = qs[1], Vt2 = qs[2], Bt1 = qs[3], Bt2 = qs[4], P = qs[5];
   T pstar = P + T(0.5) * (Bn * Bn + Bt1 * Bt1 + Bt2 * Bt2);
-  long long f = fidx(g, c[0], c[1], c[2]);
+  idx_t f = fidx(g, c[0], c[1], c[2]);
   const FaceOut<T>& fo = B.fo[D];
   fo.f[0][f] = pstar - Bn * Bn;
   fo.f[1][f] = -(Bn * Bt1);
@@ -152,8 +152,8 @@ template <typename T, int D>
 __global__ void __launch_bounds__(256) kb_euler_face(const Box<T>* __restrict__ boxes, Tiles tl) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
-    long long t = (long long)tl.start[t_] + threadIdx.x;
-    long long total = (long long)(B.g.n[0] + (D == 0)) * (B.g.n[1] + (D == 1)) * (B.g.n[2] + (D == 2));
+    idx_t t = tl.start[t_] + (idx_t)threadIdx.x;
+    idx_t total = (idx_t)(B.g.n[0] + (D == 0)) * (B.g.n[1] + (D == 1)) * (B.g.n[2] + (D == 2));
     if (t < total) euler_face<T, D>(B, t);
   }
 }
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) kb_euler_face(const Box<T>* __restrict__ 
 // Eulerian faces i_D - 1/2 for i_D in [s PENCIL, min((s+1) PENCIL, n_D + 1)) of one pencil s; the
 // arithmetic per face is that of euler_face.
 template <typename T, int D>
-__device__ __forceinline__ void euler_pencil(const Box<T>& B, long long p) {
+__device__ __forceinline__ void euler_pencil(const Box<T>& B, idx_t p) {
   constexpr int D1 = (D + 1) % 3, D2 = (D + 2) % 3;
   const Geom& g = B.g;
   int ext[3] = {g.n[0], g.n[1], g.n[2]};
@@ -180,7 +180,7 @@ __device__ __forceinline__ void euler_pencil(const Box<T>& B, long long p) {
   };
   Para<T> pl[6], pr[6];
   {
-    long long cell[5];
+    idx_t cell[5];
 #pragma unroll
     for (int o = 0; o < 5; ++o) cell[o] = cell_at(f0 - 3 + o);
 #pragma unroll
@@ -188,13 +188,13 @@ __device__ __forceinline__ void euler_pencil(const Box<T>& B, long long p) {
       pl[v] = ppm(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
   }
   for (int i = f0; i < f1; ++i) {
-    long long cell[5];
+    idx_t cell[5];
 #pragma unroll
     for (int o = 0; o < 5; ++o) cell[o] = cell_at(i - 2 + o);
 #pragma unroll
     for (int v = 0; v < 6; ++v)
       pr[v] = ppm(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
-    long long cl = cell[1], cr = cell[2];
+    idx_t cl = cell[1], cr = cell[2];
     T wl[6] = {B.s.rho[cl], B.w.p[cl], B.w.g[cl], B.w.B[D1][cl], B.w.B[D2][cl], B.w.sr[cl]};
     T wr[6] = {B.s.rho[cr], B.w.p[cr], B.w.g[cr], B.w.B[D1][cr], B.w.B[D2][cr], B.w.sr[cr]};
     T Bn = B.s.b[D][cr];
@@ -204,7 +204,7 @@ __device__ __forceinline__ void euler_pencil(const Box<T>& B, long long p) {
     T pstar = P + T(0.5) * (Bn * Bn + Bt1 * Bt1 + Bt2 * Bt2);
     int cf[3] = {c[0], c[1], c[2]};
     cf[D] = i;
-    long long f = fidx(g, cf[0], cf[1], cf[2]);
+    idx_t f = fidx(g, cf[0], cf[1], cf[2]);
     const FaceOut<T>& fo = B.fo[D];
     fo.f[0][f] = pstar - Bn * Bn;
     fo.f[1][f] = -(Bn * Bt1);
@@ -222,8 +222,8 @@ template <typename T, int D>
 __global__ void __launch_bounds__(256) kb_euler_pencil(const Box<T>* __restrict__ boxes, Tiles tl) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
-    long long p = (long long)tl.start[t_] + threadIdx.x;
-    long long total = (long long)(D == 0 ? pencil_segments(B.g.n[0]) : B.g.n[0]) *
+    idx_t p = tl.start[t_] + (idx_t)threadIdx.x;
+    idx_t total = (idx_t)(D == 0 ? pencil_segments(B.g.n[0]) : B.g.n[0]) *
                       (D == 1 ? pencil_segments(B.g.n[1]) : B.g.n[1]) *
                       (D == 2 ? pencil_segments(B.g.n[2]) : B.g.n[2]);
     if (p < total) euler_pencil<T, D>(B, p);
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) kb_euler_pencil(const Box<T>* __restrict_
 // c_d in [0, n_d) and c_{d+1}, c_{d+2} in [0, n]: the mean of the two faces of direction d+1 and
 // the two of direction d+2 that share the edge.
 template <typename T>
-__device__ __forceinline__ void edges_point(const Box<T>& B, long long t) {
+__device__ __forceinline__ void edges_point(const Box<T>& B, idx_t t) {
   const Geom& g = B.g;
   int c[3];
   decode(t, g.n[0] + 1, g.n[1] + 1, c);
@@ -260,7 +260,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) kb_edges(const Box<T>* __restrict__ boxes, Tiles tl) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
-    long long t = (long long)tl.start[t_] + threadIdx.x;
+    idx_t t = tl.start[t_] + (idx_t)threadIdx.x;
     if (t < B.g.NF) edges_point(B, t);
   }
 }
@@ -268,15 +268,15 @@ __global__ void __launch_bounds__(512) kb_edges(const Box<T>* __restrict__ boxes
 // Eulerian update of one cell: finite-volume R of m, rho E, rho eps (Sec. 2.4 + A12), Flux-CT of
 // the cell's three faces (Sec. 2.5), SSP-RK3 combination (Sec. 2.2) with stage r.
 template <typename T>
-__device__ __forceinline__ void euler_update_cell(const Box<T>& B, long long c, int r) {
+__device__ __forceinline__ void euler_update_cell(const Box<T>& B, idx_t c, int r) {
   const Geom& g = B.g;
   int q[3];
   decode(c, g.n[0], g.n[1], q);
   const T a = (T)RK3_A(r), bb = (T)RK3_B(r), gg = (T)RK3_G(r);
   const T tau = (T)B.sc->tau;
   const T ih = (T)B.ph.ih;
-  long long f0 = fidx(g, q[0], q[1], q[2]);
-  long long fup[3] = {fidx(g, q[0] + 1, q[1], q[2]), fidx(g, q[0], q[1] + 1, q[2]), fidx(g, q[0], q[1], q[2] + 1)};
+  idx_t f0 = fidx(g, q[0], q[1], q[2]);
+  idx_t fup[3] = {fidx(g, q[0] + 1, q[1], q[2]), fidx(g, q[0], q[1] + 1, q[2]), fidx(g, q[0], q[1], q[2] + 1)};
   T acc[5] = {T(0), T(0), T(0), T(0), T(0)};  // m_x, m_y, m_z, rho E, -h div V
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -310,7 +310,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) kb_euler_update(const Box<T>* __restrict__ boxes, Tiles tl, int r) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
-    long long c = (long long)tl.start[t_] + threadIdx.x;
+    idx_t c = tl.start[t_] + (idx_t)threadIdx.x;
     if (c < B.g.N) euler_update_cell(B, c, r);
   }
 }
@@ -319,31 +319,31 @@ __global__ void __launch_bounds__(512) kb_euler_update(const Box<T>* __restrict_
 // Sec. 2.6 Lagrangian face flux for direction D: F = v_n q(-|v_n| tau) (v_n >= 0, left cell) or
 // v_n q(|v_n| tau) (right cell) with v_n the sqrt(rho)-weighted mean of the cell velocities.
 template <typename T, int D>
-__device__ __forceinline__ void lag_face(const Box<T>& B, long long t) {
+__device__ __forceinline__ void lag_face(const Box<T>& B, idx_t t) {
   const Geom& g = B.g;
   int ext[3] = {g.n[0], g.n[1], g.n[2]};
   ext[D] += 1;
   int c[3];
   decode(t, ext[0], ext[1], c);
   const T tau_h = (T)B.sc->tau_h;
-  long long cell[6];
+  idx_t cell[6];
 #pragma unroll
   for (int o = 0; o < 6; ++o) {
     int cc[3] = {c[0], c[1], c[2]};
     cc[D] += o - 3;
     cell[o] = cmap(g, cc[0], cc[1], cc[2]);
   }
-  long long cl = cell[2], cr = cell[3];
+  idx_t cl = cell[2], cr = cell[3];
   T rl = B.s.rho[cl], rr = B.s.rho[cr];
   T vl = B.s.m[D][cl] / rl, vr = B.s.m[D][cr] / rr;
   T sl = sqrt(rl), sr = sqrt(rr);
   T vn = (vl * sl + vr * sr) / (sl + sr);
   T y = fabs(vn) * tau_h;
   const T* q[7] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2};
-  long long f = fidx(g, c[0], c[1], c[2]);
+  idx_t f = fidx(g, c[0], c[1], c[2]);
   const int o0 = vn >= T(0) ? 0 : 1;  // upwind cell: stencil cells o0 .. o0 + 4
   const int nv = B.nv;
-  long long st[5];
+  idx_t st[5];
 #pragma unroll
   for (int o = 0; o < 5; ++o) st[o] = o0 == 0 ? cell[o] : cell[o + 1];
 #pragma unroll
@@ -360,22 +360,22 @@ template <typename T, int D>
 __global__ void __launch_bounds__(256) kb_lag_face(const Box<T>* __restrict__ boxes, Tiles tl) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
-    long long t = (long long)tl.start[t_] + threadIdx.x;
-    long long total = (long long)(B.g.n[0] + (D == 0)) * (B.g.n[1] + (D == 1)) * (B.g.n[2] + (D == 2));
+    idx_t t = tl.start[t_] + (idx_t)threadIdx.x;
+    idx_t total = (idx_t)(B.g.n[0] + (D == 0)) * (B.g.n[1] + (D == 1)) * (B.g.n[2] + (D == 2));
     if (t < total) lag_face<T, D>(B, t);
   }
 }
 
 template <typename T>
-__device__ __forceinline__ void lag_update_cell(const Box<T>& B, long long c, int r) {
+__device__ __forceinline__ void lag_update_cell(const Box<T>& B, idx_t c, int r) {
   const Geom& g = B.g;
   int q[3];
   decode(c, g.n[0], g.n[1], q);
   const T a = (T)RK3_A(r), bb = (T)RK3_B(r), gg = (T)RK3_G(r);
   const T tau = (T)B.sc->tau;
   const T ih = (T)B.ph.ih;
-  long long f0 = fidx(g, q[0], q[1], q[2]);
-  long long fup[3] = {fidx(g, q[0] + 1, q[1], q[2]), fidx(g, q[0], q[1] + 1, q[2]), fidx(g, q[0], q[1], q[2] + 1)};
+  idx_t f0 = fidx(g, q[0], q[1], q[2]);
+  idx_t fup[3] = {fidx(g, q[0] + 1, q[1], q[2]), fidx(g, q[0], q[1] + 1, q[2]), fidx(g, q[0], q[1], q[2] + 1)};
   T* qq[7] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2};
   T* q0[7] = {B.s0.rho, B.s0.m[0], B.s0.m[1], B.s0.m[2], B.s0.E, B.s0.eint, B.s0.rh2};
   const int nv = B.nv;
@@ -394,7 +394,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) kb_lag_update(const Box<T>* __restrict__ boxes, Tiles tl, int r) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
-    long long c = (long long)tl.start[t_] + threadIdx.x;
+    idx_t c = tl.start[t_] + (idx_t)threadIdx.x;
     if (c < B.g.N) lag_update_cell(B, c, r);
   }
 }
@@ -405,7 +405,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) kb_save_qn(const Box<T>* __restrict__ boxes, Tiles tl, int lagrangian) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
-    long long c = (long long)tl.start[t_] + threadIdx.x;
+    idx_t c = tl.start[t_] + (idx_t)threadIdx.x;
     if (c >= B.g.N) continue;
 #pragma unroll
     for (int d = 0; d < 3; ++d) B.s0.m[d][c] = B.s.m[d][c];
@@ -434,7 +434,7 @@ __device__ __forceinline__ double warp_max(double v) {
 // do_chem / do_reg select the stages (the full step runs both); do_chem = do_reg = 0 computes
 // only the CFL denominator.  Returns the flags via the warp-aggregated atomics of the caller.
 template <typename T>
-__device__ __forceinline__ void post_cell(const Box<T>& B, long long c, int do_chem, int do_reg,
+__device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, int do_chem, int do_reg,
                                           double& D, int& bad, unsigned& vb) {
   const Geom& g = B.g;
   const Phys& ph = B.ph;
@@ -444,7 +444,7 @@ __device__ __forceinline__ void post_cell(const Box<T>& B, long long c, int do_c
   const double tau = B.sc->tau;
   if (do_chem && ph.chem)
     s.rh2[c] = (T)chem_cell<(sizeof(T) == 4)>(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c], tau);
-  long long up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
+  idx_t up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
   T Bc[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) Bc[d] = T(0.5) * (s.b[d][c] + s.b[d][up[d]]);
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(512) kb_post(const Box<T>* __restrict__ boxes,
                                                int do_reg, int check) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
-    long long c = (long long)tl.start[t_] + threadIdx.x;
+    idx_t c = tl.start[t_] + (idx_t)threadIdx.x;
     double D = 0.0;
     int bad = 0;
     unsigned vb = 0;

@@ -150,14 +150,13 @@ inline unsigned grid_of(const Tiles& t, const LaunchCfg& c, int nsm) {
   return (unsigned)(g > 0 ? g : 1);
 }
 
-// default launch shapes: FP64 face kernels are register heavy (128 threads), the rest 256
+// default launch shapes: the face kernels are register heavy (150-230 registers), so 128-thread
+// blocks let two or three blocks share an SM; the rest 256
 template <typename T>
 void default_cfgs(Exec<T>& X) {
   for (int kc = 0; kc < NKC; ++kc) X.cfg[kc] = LaunchCfg{256, 0};
-  if (sizeof(T) == 8) {
-    X.cfg[KC_EFACE].block = 128;
-    X.cfg[KC_LFACE].block = 128;
-  }
+  X.cfg[KC_EFACE].block = 128;
+  X.cfg[KC_LFACE].block = 128;
 }
 
 template <typename T>
