@@ -33,14 +33,15 @@ WORKLOAD = "mhd_turbulence_h2chem_128^3_fp64"
 METRIC = "Mcell-updates/s"
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# algorithmic FP64 flops of one Eulerian face, counted from the kernel source: 6 PPM parabola sets
-# (one per cell and variable, amortised over the cell's two faces, ~70 flops each) and the Riemann
-# solve (Roe average and eigenvectors ~60, 36 parabola averages with L q and R s ~400, fluxes ~25);
-# add/sub/mul/div/sqrt one flop each, compares not counted
-FLOPS_PER_EULER_FACE = 930
+# algorithmic FP64 flops of one Eulerian face, counted from the kernel source with an FMA as two
+# flops and a division, square root or reciprocal square root as one (compares not counted): the
+# parabolas of the six primitives of one new cell (6 x 36), the Riemann solve (Roe average, speeds
+# and eigenvector rows 116, the six waves' domain-of-dependence averages with L q and R s 286) and
+# the fluxes (25)
+FLOPS_PER_EULER_FACE = 643
 # DRAM bytes (read + write) of one x-direction Eulerian face launch at 128^3 from the ncu capture
 # summarised in profiles/kb_euler_pencil_turbulence_128_fp64.md (None when the kernel changes)
-EULER_FACE_TRAFFIC_BYTES = 330.4e6
+EULER_FACE_TRAFFIC_BYTES = None
 
 
 def reduce_max(x, dist=None, device="cpu"):
@@ -192,6 +193,7 @@ def fp32_leg(M, I, torch, n=256, steps=10, warm=3, err_steps=5):
     ic = I.turbulence(n, mach=5.0, beta=1.0, seed=1)
     s32 = M.from_ic(ic, precision=1)
     ms = timed_steps(torch, s32, steps, warm)
+    prof = M.profile(s32, CFL, 2)
     del s32
     a = M.from_ic(ic, precision=1)
     b = M.from_ic(ic, precision=0)
@@ -204,7 +206,8 @@ def fp32_leg(M, I, torch, n=256, steps=10, warm=3, err_steps=5):
     del a, b
     return {"workload": f"mhd_turbulence_h2chem_{n}^3_fp32bulk", "value": n ** 3 * steps / (ms * 1e-3) / 1e6,
             "unit": METRIC, "ms_per_step": ms / steps, "steps": steps, "warmup": warm,
-            "rel_l1_vs_fp64": err, "error_steps": err_steps}
+            "rel_l1_vs_fp64": err, "error_steps": err_steps,
+            "kernels": {k: v["ms_total"] / 2 for k, v in prof.items()}}
 
 
 def batched_leg(M, I, torch, steps=20, warm=3):

@@ -2,10 +2,11 @@
 // arXiv:1608.08748 (Kulikov, Chernykh & Protasov).  Templated on the bulk type T (double for the
 // FP64 path, float for the FP32-bulk path); the CFL reduction and the chemistry are FP64 always.
 //
-// The formulas follow the paper section by section, in the same operation order as a plain
-// evaluation; the FP64 build lets the compiler contract a*b+c into one FMA, so the FP64 path agrees
-// with a plain evaluation to a few ulp per operation (1e-14 relative L1 after 50 steps of the
-// 128^3 turbulence box).
+// The formulas follow the paper section by section.  The PPM limiter gives the plain evaluation's
+// values bit for bit (its tests run on the integer pipes); the Riemann solver forms its speeds and
+// eigenvector rows with fewer divisions and square roots, and the FP64 build lets the compiler
+// contract a*b+c into one FMA, so the FP64 path agrees with a plain evaluation to a few ulp per
+// operation (about 1e-15 relative L1 after 50 steps of the 128^3 turbulence box).
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -97,10 +98,10 @@ __device__ __forceinline__ T slope_m(T qm, T q0, T qp) {
   return T(0);
 }
 
-// Steps 1-5 from q_{i-2} .. q_{i+2}; Step 4 weights in the reading where hbar weighs the
-// flattened values q -+ delta_m q / 4 (the amendment acts in discontinuities).
+// Steps 1-5 from q_{i-2} .. q_{i+2} evaluated as written, for the FP32-bulk path (whose FP32 pipes
+// have room for the plain form); the FP64 path takes ppm below.
 template <typename T>
-__device__ __forceinline__ Para<T> ppm(T qm2, T qm1, T qc, T qp1, T qp2) {
+__device__ __forceinline__ Para<T> ppm_direct(T qm2, T qm1, T qc, T qp1, T qp2) {
   const T SIXTH = T(1.0 / 6.0);
   T dmm = slope_m(qm2, qm1, qc);
   T dm0 = slope_m(qm1, qc, qp1);
@@ -142,6 +143,215 @@ __device__ __forceinline__ Para<T> ppm(T qm2, T qm1, T qc, T qp1, T qp2) {
   P.d = qR - qL;
   P.q6 = T(6) * (qc - T(0.5) * (qL + qR));
   return P;
+}
+
+// Sign tests, absolute values, minima and comparisons of doubles on the integer pipes.  On sm_103
+// the FP64 pipe issues two instructions per clock per SM and the integer pipes 64, and the PPM
+// limiter is mostly such tests.  They work on the two 32-bit halves in inline PTX, so that the
+// compiler does not turn them back into floating-point negations, absolute values or compares.
+// For non-NaN operands they give the IEEE answer, with two exceptions that cannot change a
+// limited value: -0 and +0 are told apart, and a product of two differences that underflows to
+// zero is not formed (the test "a b > 0" is taken on the signs).  The float overloads are the plain
+// operations.
+__device__ __forceinline__ double abs_b(double x) {
+  double r;
+  asm("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tand.b32 hi, hi, 0x7fffffff;\n\t"
+      "mov.b64 %0, {lo, hi};\n\t}" : "=d"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ float abs_b(float x) { return fabsf(x); }
+__device__ __forceinline__ double neg_b(double x) {
+  double r;
+  asm("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\txor.b32 hi, hi, 0x80000000;\n\t"
+      "mov.b64 %0, {lo, hi};\n\t}" : "=d"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ float neg_b(float x) { return -x; }
+// m (>= 0) with the sign of s
+__device__ __forceinline__ double with_sign_b(double m, double s) {
+  double r;
+  asm("{\n\t.reg .b32 lo, hi, hs, ls;\n\tmov.b64 {lo, hi}, %1;\n\tmov.b64 {ls, hs}, %2;\n\t"
+      "and.b32 hs, hs, 0x80000000;\n\tor.b32 hi, hi, hs;\n\tmov.b64 %0, {lo, hi};\n\t}"
+      : "=d"(r) : "d"(m), "d"(s));
+  return r;
+}
+__device__ __forceinline__ float with_sign_b(float m, float s) { return copysignf(m, s); }
+// the smaller of a, b >= 0
+__device__ __forceinline__ double min_nn(double a, double b) {
+  double r;
+  asm("{\n\t.reg .s64 ia, ib;\n\t.reg .pred p;\n\tmov.b64 ia, %1;\n\tmov.b64 ib, %2;\n\t"
+      "setp.lt.s64 p, ia, ib;\n\tselp.b64 %0, %1, %2, p;\n\t}" : "=d"(r) : "d"(a), "d"(b));
+  return r;
+}
+__device__ __forceinline__ float min_nn(float a, float b) { return a < b ? a : b; }
+// a > b for b >= 0
+__device__ __forceinline__ bool gt_nn(double a, double b) {
+  unsigned r;
+  asm("{\n\t.reg .s64 ia, ib;\n\t.reg .pred p;\n\tmov.b64 ia, %1;\n\tmov.b64 ib, %2;\n\t"
+      "setp.gt.s64 p, ia, ib;\n\tselp.u32 %0, 1, 0, p;\n\t}" : "=r"(r) : "d"(a), "d"(b));
+  return r != 0;
+}
+__device__ __forceinline__ bool gt_nn(float a, float b) { return a > b; }
+// a b > 0: both nonzero, one sign
+__device__ __forceinline__ bool same_sign(double a, double b) {
+  unsigned r;
+  asm("{\n\t.reg .b32 la, ha, lb, hb, t;\n\t.reg .pred p;\n\t"
+      "mov.b64 {la, ha}, %1;\n\tmov.b64 {lb, hb}, %2;\n\t"
+      "and.b32 t, ha, 0x7fffffff;\n\tor.b32 t, t, la;\n\tsetp.ne.u32 p, t, 0;\n\t"
+      "and.b32 t, hb, 0x7fffffff;\n\tor.b32 t, t, lb;\n\tsetp.ne.and.u32 p, t, 0, p;\n\t"
+      "xor.b32 t, ha, hb;\n\tsetp.ge.and.s32 p, t, 0, p;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r) : "d"(a), "d"(b));
+  return r != 0;
+}
+__device__ __forceinline__ bool same_sign(float a, float b) { return a * b > 0.f; }
+// the sign bit
+__device__ __forceinline__ bool sign_bit_b(double x) {
+  unsigned r;
+  asm("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tshr.u32 %0, hi, 31;\n\t}" : "=r"(r) : "d"(x));
+  return r != 0;
+}
+__device__ __forceinline__ bool sign_bit_b(float x) { return signbit(x); }
+
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
+// Half the limited slope of Sec. 2.1 Step 1 for a cell with differences dn = q_0 - q_-1,
+// dp = q_1 - q_0 and s = q_1 - q_-1: the slope is min(|s|/2, 2|dp|, 2|dn|) with the sign of s where
+// dn and dp have one sign, else 0; halving it is exact, and saves the doublings.
+template <typename T>
+__device__ __forceinline__ T half_slope(T s, T dn, T dp) {
+  if (!same_sign(dn, dp)) return T(0);
+  T m = min_nn(min_nn(T(0.25) * abs_b(s), abs_b(dp)), abs_b(dn));
+  return with_sign_b(m, s);
+}
+
+// Sec. 2.1 Steps 1-5 for cell i from q_{i-2} .. q_{i+2}, with the Step 4 weights in the reading
+// where hbar weighs the flattened values q -+ delta_m q / 4 (the amendment acts in
+// discontinuities).  Written for few FP64 operations: the slopes are carried halved, the
+// differences q_{i+1} - q_{i-1} and the second differences are formed once, min(|q_{i+1}|,
+// |q_{i-1}|, |q_{i+1}| + |q_{i-1}|) is min(|q_{i+1}|, |q_{i-1}|), and eta = -(D+ - D-) / (3 dq) is
+// divided out only where it can exceed 1/20 (elsewhere hbar = 0 and Step 4 changes nothing;
+// hbar = 20 (eta - 1/20) is continuous there, so the test's rounding cannot move the result).
+template <typename T>
+__device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm, T s0, T qp1, T qm1) {
+  // Step 2: monotonicity
+  T dq = qR - qL;
+  T q6 = T(6) * (qc - T(0.5) * (qL + qR));
+  bool changed = false;
+  if (!same_sign(qL - qc, qc - qR)) {
+    qL = qc;
+    qR = qc;
+    changed = true;
+  } else {
+    const T a = dq * q6, b = dq * dq;
+    if (gt_nn(a, b)) {
+      qL = T(3) * qc - T(2) * qR;
+      changed = true;
+    } else if (gt_nn(neg_b(a), b)) {
+      qR = T(3) * qc - T(2) * qL;
+      changed = true;
+    }
+  }
+  // Step 4: discontinuity detector
+  const T mn = min_nn(abs_b(qp1), abs_b(qm1));
+  if (gt_nn(abs_b(s0), T(0.01) * mn) && !same_sign(Dp, Dm)) {
+    const T num = Dm - Dp, den = T(3) * s0;  // eta = num / den, den != 0 here
+    // num / den > 1/20  <=>  num sgn(den) > |den| / 20
+    const T num_s = sign_bit_b(den) ? neg_b(num) : num;
+    if (gt_nn(num_s, T(0.05) * abs_b(den))) {
+      const T eta = num / den;
+      T hb = T(20) * (eta - T(0.05));
+      hb = hb < T(1) ? hb : T(1);
+      if (hb > T(0)) {
+        const T qLp = qc - T(0.5) * h0, qRp = qc + T(0.5) * h0;
+        qL = hb * qLp + (T(1) - hb) * qL;
+        qR = hb * qRp + (T(1) - hb) * qR;
+        changed = true;
+      }
+    }
+  }
+  // Step 5
+  if (changed) {
+    dq = qR - qL;
+    q6 = T(6) * (qc - T(0.5) * (qL + qR));
+  }
+  Para<T> P;
+  P.L = qL;
+  P.R = qR;
+  P.d = dq;
+  P.q6 = q6;
+  return P;
+}
+
+template <typename T>
+__device__ __forceinline__ Para<T> ppm_fp64(T qm2, T qm1, T qc, T qp1, T qp2) {
+  const T THIRD = T(1.0 / 3.0);  // twice 1/6, exactly
+  const T d0 = qm1 - qm2, d1 = qc - qm1, d2 = qp1 - qc, d3 = qp2 - qp1;
+  const T sm = qc - qm2, s0 = qp1 - qm1, sp = qp2 - qc;
+  const T hm = half_slope(sm, d0, d1), h0 = half_slope(s0, d1, d2), hp = half_slope(sp, d2, d3);
+  // Step 1: edge values (dm0 - dmm) / 6 = (h0 - hm) / 3
+  const T qL = T(0.5) * (qm1 + qc) - (h0 - hm) * THIRD;
+  const T qR = T(0.5) * (qc + qp1) - (hp - h0) * THIRD;
+  // second differences D+ = q_{i+2} - 2 q_{i+1} + q_i, D- = q_i - 2 q_{i-1} + q_{i-2}
+  const T Dp = (qp2 - T(2) * qp1) + qc;
+  const T Dm = (qc - T(2) * qm1) + qm2;
+  return ppm_limit(qL, qR, qc, h0, Dp, Dm, s0, qp1, qm1);
+}
+
+// The parabolas of consecutive cells j, j+1, ... along a line, each from the quantities ppm_fp64
+// forms for it (so bit for bit the same), where the difference q_{j+1} - q_j, the halved slope, the
+// edge value between two cells and the second difference centred on a cell are formed once and
+// shared by the neighbours that use them.  Prime with q_{J-2} .. q_{J+1}; each next(q_{j+2}) then
+// returns the parabola of the next cell j = J, J+1, ...
+template <typename T>
+struct PPMStream {
+  T qm, q0, qp;  // q_{j-1}, q_j, q_{j+1}
+  T dp;          // q_{j+1} - q_j
+  T h0;          // halved slope of cell j
+  T eL;          // edge value between j-1 and j
+  T Cm, C0;      // second differences centred on j-1 and j
+  T s0;          // q_{j+1} - q_{j-1}
+
+  __device__ __forceinline__ void prime(T qa, T qb, T qc, T qd) {  // q_{J-2} .. q_{J+1}
+    const T THIRD = T(1.0 / 3.0);
+    const T d0 = qb - qa, d1 = qc - qb, d2 = qd - qc;
+    const T hm = half_slope(qc - qa, d0, d1);
+    s0 = qd - qb;
+    h0 = half_slope(s0, d1, d2);
+    eL = T(0.5) * (qb + qc) - (h0 - hm) * THIRD;
+    Cm = (qc - T(2) * qb) + qa;
+    C0 = (qd - T(2) * qc) + qb;
+    qm = qb;
+    q0 = qc;
+    qp = qd;
+    dp = d2;
+  }
+  __device__ __forceinline__ Para<T> next(T qn) {  // qn = q_{j+2}
+    const T THIRD = T(1.0 / 3.0);
+    const T d2 = qn - qp;
+    const T s1 = qn - q0;
+    const T h1 = half_slope(s1, dp, d2);
+    const T C1 = (qn - T(2) * qp) + q0;
+    const T eR = T(0.5) * (q0 + qp) - (h1 - h0) * THIRD;
+    Para<T> P = ppm_limit(eL, eR, q0, h0, C1, Cm, s0, qp, qm);
+    qm = q0;
+    q0 = qp;
+    qp = qn;
+    dp = d2;
+    h0 = h1;
+    eL = eR;
+    Cm = C0;
+    C0 = C1;
+    s0 = s1;
+    return P;
+  }
+};
+
+// Sec. 2.1 Steps 1-5 for cell i from q_{i-2} .. q_{i+2}
+template <typename T>
+__device__ __forceinline__ Para<T> ppm(T qm2, T qm1, T qc, T qp1, T qp2) {
+  if constexpr (sizeof(T) == 8) return ppm_fp64(qm2, qm1, qc, qp1, qp2);
+  else return ppm_direct(qm2, qm1, qc, qp1, qp2);
 }
 
 // Sec. 2.4: parabola averages over the domain of dependence of a wave of |speed| y h / tau
@@ -190,8 +400,137 @@ __device__ __forceinline__ Speeds<T> mhd_speeds(T c2, T ca2, T bp2) {
 // Sec. 2.4 + App. A: Roe-type face state, eigenvectors and the characteristic Riemann solution.
 // wl/wr = (rho, p, gamma, B_t1, B_t2, sqrt(rho)) of the left/right cell; Bn the face field.
 // qs = (V_n, V_t1, V_t2, B_t1, B_t2, P).
+//
+// The speeds, alpha factors and eigenvector entries are those of App. A with 10 divisions and
+// square roots instead of 29: one reciprocal of the weight sum, 1/sqrt(rho) (giving 1/rho,
+// sqrt(rho), c_a = |B_n| / sqrt(rho) and the 1/sqrt(2 rho) of the Alfven rows), 1/c (giving c and
+// the 1/(2c^2), 1/(2 sqrt(rho) c) factors of L), 1/c_f (giving c_f and c_s = c c_a / c_f, from
+// c_f^2 c_s^2 = c^2 c_a^2) and 1/|B_perp|.  The left and right waves of each pair share their
+// rows up to the sign of the velocity components, so the rows are formed once.
 template <typename T>
-__device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, const Para<T> pl[6],
+__device__ __forceinline__ void riemann_fp64(const T wl[6], const T wr[6], T Bn, const Para<T> pl[6],
+                                             const Para<T> pr[6], T tau_h, T qs[6]) {
+  const T INV_SQRT2 = T(0.70710678118654752440);
+  const T sl = wl[5], sr = wr[5];
+  const T iden = T(1) / (sl + sr);
+  const T rho = (sl * wl[0] + sr * wr[0]) * iden;
+  const T p = (sl * wl[1] + sr * wr[1]) * iden;
+  const T gam = (sl * wl[2] + sr * wr[2]) * iden;
+  const T Bt1 = (sl * wr[3] + sr * wl[3]) * iden;  // crossed weights for B
+  const T Bt2 = (sl * wr[4] + sr * wl[4]) * iden;
+
+  const T rs = rsqrt_t(rho);  // 1 / sqrt(rho)
+  const T irho = rs * rs;
+  const T gp = gam * p;
+  const T c2 = gp * irho;
+  const T ca2 = (Bn * Bn) * irho;
+  const T bp2 = Bt1 * Bt1 + Bt2 * Bt2;
+  const T bp2r = bp2 * irho;
+  const T s = c2 + (ca2 + bp2r);
+  // fast and slow speeds without cancellation (see mhd_speeds)
+  const T X = c2 - ca2;
+  const T sq = sqrt(X * X + bp2r * ((T(2) * c2 + T(2) * ca2) + bp2r));
+  T dcs, dfc;
+  if (X >= T(0)) {
+    dcs = T(0.5) * ((X + sq) - bp2r);
+    if (dcs < T(0)) dcs = T(0);
+    dfc = dcs > T(0) ? c2 * bp2r / dcs : T(0);
+  } else {
+    dfc = T(0.5) * ((bp2r - X) + sq);
+    dcs = dfc > T(0) ? c2 * bp2r / dfc : T(0);
+  }
+  const T cf2 = c2 + dfc;
+  const T rc = rsqrt_t(c2), rcf = rsqrt_t(cf2);
+  const T c = c2 * rc, cf = cf2 * rcf, ca = abs_b(Bn) * rs;
+  const T cs = (c * ca) * rcf;
+  T af, as;
+  if (sq > T(1e-12) * s) {
+    const T isq = T(1) / sq;
+    af = sqrt(dcs * isq);
+    as = sqrt(dfc * isq);
+  } else {
+    af = INV_SQRT2;
+    as = INV_SQRT2;
+  }
+  T by, bz;
+  if (bp2 > T(1e-24) * rho * s) {
+    const T ibp = rsqrt_t(bp2);
+    by = Bt1 * ibp;
+    bz = Bt2 * ibp;
+  } else {
+    by = INV_SQRT2;
+    bz = INV_SQRT2;
+  }
+  const T sg = Bn >= T(0) ? T(1) : T(-1);
+  const T sqr = rho * rs, sc = sqr * c, sr2 = sqr * INV_SQRT2;
+  const T i2c2 = T(0.5) * (rc * rc), i2sc = T(0.5) * (rs * rc), i2rc2 = i2c2 * irho;
+  const T isr2 = rs * INV_SQRT2;
+
+  // App. A rows of the +c_f and +c_s waves; the -c waves negate the v_n, v_t1, v_t2 entries
+  const T afcf = af * cf, ascs = as * cs, bys = by * sg, bzs = bz * sg;
+  const T Rf[6] = {afcf, -(ascs * bys), -(ascs * bzs), as * sc * by, as * sc * bz, af * gp};
+  const T Lf[6] = {afcf * i2c2, -(ascs * bys) * i2c2, -(ascs * bzs) * i2c2, as * by * i2sc,
+                   as * bz * i2sc, af * i2rc2};
+  const T Rs[6] = {ascs, afcf * bys, afcf * bzs, -(af * sc * by), -(af * sc * bz), as * gp};
+  const T Ls[6] = {ascs * i2c2, afcf * bys * i2c2, afcf * bzs * i2c2, -(af * by * i2sc),
+                   -(af * bz * i2sc), as * i2rc2};
+  // Alfven rows: v_t1, v_t2 entries shared, B_t1, B_t2 entries negated for the -c_a wave
+  const T Av[2] = {-(bzs * INV_SQRT2), bys * INV_SQRT2};
+  const T AL[2] = {bz * isr2, -(by * isr2)};
+  const T AR[2] = {sr2 * bz, -(sr2 * by)};
+
+#pragma unroll
+  for (int m = 0; m < 6; ++m) qs[m] = T(0);
+  const T TWO_THIRDS = T(2.0 / 3.0);
+  // one wave at a time, k ascending: s_k = L_k . qbar_k (qbar_k the domain-of-dependence average
+  // on the upwind side), q* += R_k s_k
+  auto magnetosonic = [&](const T L[6], const T R[6], const Para<T> P[6], T speed, bool right_moving) {
+    const T y = speed * tau_h;
+    const T hy = T(0.5) * y, w = T(1) - TWO_THIRDS * y;
+    T sa = T(0), sb = T(0);
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      // avg_right_end / avg_left_end of Sec. 2.4
+      const T qb = right_moving ? P[m].R - hy * (P[m].d - P[m].q6 * w)
+                                : P[m].L + hy * (P[m].d + P[m].q6 * w);
+      if (m < 3) sa = sa + L[m] * qb;
+      else sb = sb + L[m] * qb;
+    }
+    const T sk = right_moving ? sa + sb : sb - sa;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      const T Rm = (m < 3 && !right_moving) ? -R[m] : R[m];
+      qs[m] = qs[m] + Rm * sk;
+    }
+  };
+  auto alfven = [&](const Para<T> P[6], bool right_moving) {
+    const T y = ca * tau_h;
+    const T hy = T(0.5) * y, w = T(1) - TWO_THIRDS * y;
+    T qb[5];
+#pragma unroll
+    for (int m = 1; m < 5; ++m)
+      qb[m] = right_moving ? P[m].R - hy * (P[m].d - P[m].q6 * w) : P[m].L + hy * (P[m].d + P[m].q6 * w);
+    const T sa = Av[0] * qb[1] + Av[1] * qb[2];
+    const T sb = AL[0] * qb[3] + AL[1] * qb[4];
+    const T sk = right_moving ? sa + sb : sa - sb;
+    qs[1] = qs[1] + Av[0] * sk;
+    qs[2] = qs[2] + Av[1] * sk;
+    const T sgn = right_moving ? T(1) : T(-1);
+    qs[3] = qs[3] + (sgn * AR[0]) * sk;
+    qs[4] = qs[4] + (sgn * AR[1]) * sk;
+  };
+  magnetosonic(Lf, Rf, pl, cf, true);   // wave 1: +c_f, left cell
+  magnetosonic(Lf, Rf, pr, cf, false);  // wave 2: -c_f, right cell
+  magnetosonic(Ls, Rs, pl, cs, true);   // wave 3: +c_s
+  magnetosonic(Ls, Rs, pr, cs, false);  // wave 4: -c_s
+  alfven(pl, true);                     // wave 5: +c_a
+  alfven(pr, false);                    // wave 6: -c_a
+}
+
+// The same solution evaluated as written (one wave at a time, every entry formed in place), for
+// the FP32-bulk path.
+template <typename T>
+__device__ __forceinline__ void riemann_direct(const T wl[6], const T wr[6], T Bn, const Para<T> pl[6],
                                         const Para<T> pr[6], T tau_h, T qs[6]) {
   const T INV_SQRT2 = T(0.70710678118654752440);
   T sl = wl[5], sr = wr[5];
@@ -344,6 +683,13 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
     qs[3] = qs[3] + -sr2 * bz * sk;
     qs[4] = qs[4] + sr2 * by * sk;
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, const Para<T> pl[6],
+                                        const Para<T> pr[6], T tau_h, T qs[6]) {
+  if constexpr (sizeof(T) == 8) riemann_fp64(wl, wr, Bn, pl, pr, tau_h, qs);
+  else riemann_direct(wl, wr, Bn, pl, pr, tau_h, qs);
 }
 
 // ------------------------------------------------------------------------------------------------

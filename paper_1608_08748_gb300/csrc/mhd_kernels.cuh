@@ -334,10 +334,10 @@ __device__ __forceinline__ void lag_face(const Box<T>& B, idx_t t) {
     cell[o] = cmap(g, cc[0], cc[1], cc[2]);
   }
   idx_t cl = cell[2], cr = cell[3];
+  // v_l sqrt(rho_l) = m_l / sqrt(rho_l) and sqrt(rho) = rho / sqrt(rho): two 1/sqrt and a division
   T rl = B.s.rho[cl], rr = B.s.rho[cr];
-  T vl = B.s.m[D][cl] / rl, vr = B.s.m[D][cr] / rr;
-  T sl = sqrt(rl), sr = sqrt(rr);
-  T vn = (vl * sl + vr * sr) / (sl + sr);
+  T isl = rsqrt_t(rl), isr = rsqrt_t(rr);
+  T vn = (B.s.m[D][cl] * isl + B.s.m[D][cr] * isr) / (rl * isl + rr * isr);
   T y = fabs(vn) * tau_h;
   const T* q[7] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2};
   idx_t f = fidx(g, c[0], c[1], c[2]);
@@ -363,6 +363,85 @@ __global__ void __launch_bounds__(256) kb_lag_face(const Box<T>* __restrict__ bo
     idx_t t = tl.start[t_] + (idx_t)threadIdx.x;
     idx_t total = (idx_t)(B.g.n[0] + (D == 0)) * (B.g.n[1] + (D == 1)) * (B.g.n[2] + (D == 2));
     if (t < total) lag_face<T, D>(B, t);
+  }
+}
+
+// The same fluxes for the faces i_D - 1/2, i_D in [s PENCIL, min((s+1) PENCIL, n_D + 1)), of one
+// pencil s: the face velocities first, then field by field the parabolas of the pencil's cells in
+// one PPMStream along D, each face taking the average of its upwind cell.
+template <typename T, int D>
+__device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
+  const Geom& g = B.g;
+  int ext[3] = {g.n[0], g.n[1], g.n[2]};
+  const int nf = g.n[D] + 1;
+  ext[D] = pencil_segments(g.n[D]);
+  int c[3];
+  decode(p, ext[0], ext[1], c);
+  const int f0 = c[D] * PENCIL;
+  const int nfp = (f0 + PENCIL < nf ? f0 + PENCIL : nf) - f0;
+  const T tau_h = (T)B.sc->tau_h;
+  const T TWO_THIRDS = T(2.0 / 3.0);
+  auto cell_at = [&](int i) {
+    int cc[3] = {c[0], c[1], c[2]};
+    cc[D] = i;
+    return cmap(g, cc[0], cc[1], cc[2]);
+  };
+  int cf[3] = {c[0], c[1], c[2]};
+  cf[D] = f0;
+  const idx_t fbase = fidx(g, cf[0], cf[1], cf[2]);
+  const idx_t fstride = D == 0 ? 1 : (D == 1 ? (idx_t)(g.n[0] + 1) : (idx_t)(g.n[0] + 1) * (g.n[1] + 1));
+  // per face: v_n, and the average over the upwind fraction y = |v_n| tau / h written as
+  // E + shy (d + sgn q6 w) with E = q^R of the left cell (v_n >= 0, sgn = -1) or q^L of the right
+  // cell (sgn = +1), shy = sgn y / 2 and w = 1 - 2y/3 (the two forms of Sec. 2.4)
+  T vn[PENCIL], shy[PENCIL], w[PENCIL];
+#pragma unroll
+  for (int k = 0; k < PENCIL; ++k) {
+    vn[k] = T(0);
+    shy[k] = T(0);
+    w[k] = T(1);
+    if (k < nfp) {
+      const idx_t cl = cell_at(f0 + k - 1), cr = cell_at(f0 + k);
+      const T rl = B.s.rho[cl], rr = B.s.rho[cr];
+      const T isl = rsqrt_t(rl), isr = rsqrt_t(rr);
+      vn[k] = (B.s.m[D][cl] * isl + B.s.m[D][cr] * isr) / (rl * isl + rr * isr);
+      const T y = abs_b(vn[k]) * tau_h;
+      const T hy = T(0.5) * y;
+      shy[k] = vn[k] >= T(0) ? neg_b(hy) : hy;
+      w[k] = T(1) - TWO_THIRDS * y;
+    }
+  }
+  const int nv = B.nv;
+#pragma unroll 1
+  for (int v = 0; v < nv; ++v) {
+    const T* a = v == 0 ? B.s.rho : v < 4 ? B.s.m[v - 1] : v == 4 ? B.s.E : v == 5 ? B.s.eint : B.s.rh2;
+    T* out = B.fo[D].f[v] + fbase;
+    PPMStream<T> S;
+    S.prime(a[cell_at(f0 - 3)], a[cell_at(f0 - 2)], a[cell_at(f0 - 1)], a[cell_at(f0)]);
+    Para<T> Pl = S.next(a[cell_at(f0 + 1)]);  // cell f0 - 1
+#pragma unroll
+    for (int k = 0; k < PENCIL; ++k) {
+      if (k < nfp) {
+        const Para<T> Pr = S.next(a[cell_at(f0 + k + 2)]);  // cell f0 + k
+        const bool left = vn[k] >= T(0);
+        const T E = left ? Pl.R : Pr.L;
+        const T d = left ? Pl.d : Pr.d;
+        const T q6 = left ? neg_b(Pl.q6) : Pr.q6;
+        out[k * fstride] = vn[k] * (E + shy[k] * (d + q6 * w[k]));
+        Pl = Pr;
+      }
+    }
+  }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256, 1) kb_lag_pencil(const Box<T>* __restrict__ boxes, Tiles tl) {
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    idx_t p = tl.start[t_] + (idx_t)threadIdx.x;
+    idx_t total = (idx_t)(D == 0 ? pencil_segments(B.g.n[0]) : B.g.n[0]) *
+                      (D == 1 ? pencil_segments(B.g.n[1]) : B.g.n[1]) *
+                      (D == 2 ? pencil_segments(B.g.n[2]) : B.g.n[2]);
+    if (p < total) lag_pencil<T, D>(B, p);
   }
 }
 

@@ -27,8 +27,16 @@ inline int profile_class(int kc) {
 constexpr int PROF_KC_BASE = 100;
 inline int report_class(int tag) { return tag >= PROF_KC_BASE ? profile_class(tag - PROF_KC_BASE) : tag; }
 // domain of the tiles of each kernel class (per-direction kernels: first of three domains)
+// The Lagrangian faces run in pencils (kb_lag_pencil) where the parabolas are FP64: sharing the
+// differences, slopes and edge values of neighbouring cells saves FP64 instructions, the bound of
+// that path; the FP32 path keeps one thread per face (kb_lag_face).
+template <typename T>
+constexpr bool lag_in_pencils() { return sizeof(T) == 8; }
+
+template <typename T>
 inline int class_domain(int kc) {
-  const int m[NKC] = {DOM_CELLS, DOM_PENCIL_X, DOM_LATTICE, DOM_CELLS, DOM_FACE_X, DOM_CELLS, DOM_CELLS, DOM_CELLS};
+  const int lag = lag_in_pencils<T>() ? DOM_PENCIL_X : DOM_FACE_X;
+  const int m[NKC] = {DOM_CELLS, DOM_PENCIL_X, DOM_LATTICE, DOM_CELLS, lag, DOM_CELLS, DOM_CELLS, DOM_CELLS};
   return m[kc];
 }
 
@@ -124,7 +132,7 @@ cudaError_t ensure_table(Exec<T>& X, int dom, int block) {
 template <typename T>
 cudaError_t ensure_tables(Exec<T>& X) {
   for (int kc = 0; kc < NKC; ++kc) {
-    int dom = class_domain(kc);
+    int dom = class_domain<T>(kc);
     int ndom = (dom == DOM_FACE_X || dom == DOM_PENCIL_X) ? 3 : 1;
     for (int q = 0; q < ndom; ++q) {
       cudaError_t e = ensure_table(X, dom + q, X.cfg[kc].block);
@@ -226,9 +234,15 @@ template <typename T>
 void launch_lag_stage(Exec<T>& X, cudaStream_t st) {
   launch_k(X, st, KC_QN, DOM_CELLS, kb_save_qn<T>, 1);
   for (int r = 0; r < 3; ++r) {
-    launch_k(X, st, KC_LFACE, DOM_FACE_X, kb_lag_face<T, 0>);
-    launch_k(X, st, KC_LFACE, DOM_FACE_Y, kb_lag_face<T, 1>);
-    launch_k(X, st, KC_LFACE, DOM_FACE_Z, kb_lag_face<T, 2>);
+    if constexpr (lag_in_pencils<T>()) {
+      launch_k(X, st, KC_LFACE, DOM_PENCIL_X, kb_lag_pencil<T, 0>);
+      launch_k(X, st, KC_LFACE, DOM_PENCIL_Y, kb_lag_pencil<T, 1>);
+      launch_k(X, st, KC_LFACE, DOM_PENCIL_Z, kb_lag_pencil<T, 2>);
+    } else {
+      launch_k(X, st, KC_LFACE, DOM_FACE_X, kb_lag_face<T, 0>);
+      launch_k(X, st, KC_LFACE, DOM_FACE_Y, kb_lag_face<T, 1>);
+      launch_k(X, st, KC_LFACE, DOM_FACE_Z, kb_lag_face<T, 2>);
+    }
     launch_k(X, st, KC_LUPD, DOM_CELLS, kb_lag_update<T>, r);
   }
 }

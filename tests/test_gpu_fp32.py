@@ -57,11 +57,17 @@ def test_fp32_brio_wu_wave_positions(M, oracle_mod):
     g = run32(M, ic, t_end=0.1)
     o = oracle_mod.run(ic, t_end=0.1)
     rg, ro = g.get_state()["rho"][0, 0], o.get_state()["rho"][0, 0]
-    jump = lambda r: np.abs(np.diff(r))
+
+    def position(r, lo, hi):
+        # the |d rho| - weighted centroid of the interfaces lo .. hi - 1: the largest single jump is
+        # ill-posed at the slow shock, where the oracle's two largest jumps differ by 5 % and the
+        # post-shock state oscillates (beta = 0.13)
+        j = np.abs(np.diff(r))[lo:hi]
+        return lo + float(np.sum(np.arange(hi - lo) * j) / np.sum(j))
+
     for lo, hi in [(55, 66), (66, 76), (76, 92)]:  # compound wave, contact, slow shock at t = 0.1
-        pg = lo + int(np.argmax(jump(rg)[lo:hi]))
-        po = lo + int(np.argmax(jump(ro)[lo:hi]))
-        assert abs(pg - po) <= 1, (lo, hi, pg, po)
+        pg, po = position(rg, lo, hi), position(ro, lo, hi)
+        assert abs(pg - po) <= 1.0, (lo, hi, pg, po, np.round(rg[lo:hi + 1], 4), np.round(ro[lo:hi + 1], 4))
 
 
 def test_fp32_accepts_float32_inputs(M):
