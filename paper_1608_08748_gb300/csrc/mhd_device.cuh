@@ -694,41 +694,22 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
 
 // ------------------------------------------------------------------------------------------------
 // Sec. 2.3: CFL denominator |v| + b + c + c_a + c_s + c_f, the largest over the three choices of
-// the longitudinal axis (b^2 = B^2 / rho).  FP64.
-__device__ __forceinline__ double cfl_denominator(double rho, double vx, double vy, double vz,
-                                                  double Bx, double By, double Bz, double p,
-                                                  double gam) {
-  double c2 = gam * p / rho;
-  double b2 = (Bx * Bx + By * By + Bz * Bz) / rho;
-  double v = sqrt(vx * vx + vy * vy + vz * vz);
-  double b = sqrt(b2), c = sqrt(c2);
-  const double Bd[3] = {Bx, By, Bz};
-  double Dmax = 0.0;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    double ca2 = Bd[d] * Bd[d] / rho;
-    double bp2r = (Bd[(d + 1) % 3] * Bd[(d + 1) % 3] + Bd[(d + 2) % 3] * Bd[(d + 2) % 3]) / rho;
-    Speeds<double> sp = mhd_speeds(c2, ca2, bp2r);
-    double cf = sqrt(sp.cf2), cs = sqrt(sp.cs2), ca = sqrt(ca2);
-    double D = v + b + c + ca + cs + cf;
-    if (D > Dmax) Dmax = D;
-  }
-  return Dmax;
-}
-
-// The same denominator for the FP32-bulk path, still in FP64 but with the identity
-// c_f + c_s = sqrt(c^2 + b^2 + 2 c c_a) (from c_f^2 + c_s^2 = c^2 + b^2 and c_f c_s = c c_a); the
-// denominator grows with |B_d|, so only the axis of the largest |B_d| is evaluated.
-__device__ __forceinline__ double cfl_denominator_fast(double rho, double vx, double vy, double vz,
-                                                       double Bx, double By, double Bz, double p,
-                                                       double gam) {
-  double irs = 1.0 / sqrt(rho);
-  double c = sqrt(gam * p / rho);
-  double b = sqrt(Bx * Bx + By * By + Bz * Bz) * irs;
-  double v = sqrt(vx * vx + vy * vy + vz * vz);
-  double Bm = fmax(fabs(Bx), fmax(fabs(By), fabs(Bz)));
-  double ca = Bm * irs;
-  return v + b + c + ca + sqrt(c * c + b * b + 2.0 * c * ca);
+// the longitudinal axis (b^2 = B^2 / rho), in FP64.  With c_f^2 + c_s^2 = c^2 + b^2 and
+// c_f c_s = c c_a, c_f + c_s = sqrt(c^2 + b^2 + 2 c c_a); the denominator grows with c_a = |B_d| /
+// sqrt(rho), so the largest one is that of the axis of the largest |B_d|.  Takes the momenta and
+// gamma p; 1/sqrt(rho) is the one reciprocal: |v| = |m| / rho, b = |B| / sqrt(rho),
+// c = sqrt(gamma p) / sqrt(rho) and c_f + c_s = sqrt(gamma p + B^2 + 2 sqrt(gamma p) |B_d|) / sqrt(rho).
+__device__ __forceinline__ double cfl_denominator(double rho, double mx, double my, double mz,
+                                                  double Bx, double By, double Bz, double gp) {
+  const double irs = rsqrt(rho);
+  const double irho = irs * irs;
+  const double sgp = sqrt(gp);
+  const double B2 = Bx * Bx + By * By + Bz * Bz;
+  const double sB = sqrt(B2);
+  const double v = sqrt(mx * mx + my * my + mz * mz) * irho;
+  const double Bm = fmax(fabs(Bx), fmax(fabs(By), fabs(Bz)));
+  const double fs = sqrt((gp + B2) + 2.0 * sgp * Bm);
+  return v + ((sB + sgp + Bm) + fs) * irs;
 }
 
 // Sec. 4.3 effective adiabatic index of the H/H2 mixture (no electrons)
@@ -747,45 +728,41 @@ struct ChemConst {
   static constexpr double KMS = 1.0e5;               // cm / s
 };
 
-// `fast` (the FP32-bulk path): the same FP64 formulas with one reciprocal of T instead of the
-// divisions by T, so the rates differ from the plain form by a few ulp.
-template <bool fast = false>
+// The App. D formulas in FP64 with few divisions (the rates agree with a term-by-term evaluation to
+// about 1e-14 relative):
+//   T = (gamma - 1) rho eps P0 / ((n_H + n_H2) k_B) with gamma - 1 = 2 (n_H + n_H2) / (3 n_H + 5 n_H2)
+//     = 2 P0 rho eps / ((3 n_H + 5 n_H2) k_B), and T, 1/T from one reciprocal of the product;
+//   1/sqrt(1 + x) from one reciprocal square root; 1/x_norm and 1/b_doppler precomputed.
 __device__ __forceinline__ double chem_cell(const Phys& ph, double rho, double eint, double rh2,
                                             double tau) {
   const double P0 = ChemConst::MH * ChemConst::KMS * ChemConst::KMS;  // code pressure, erg cm^-3
   const double T0 = ChemConst::PC / ChemConst::KMS;                  // code time, s
-  double nH = rho - rh2, nH2 = 0.5 * rh2, n = rho;
-  double g = gamma_eff(rho, rh2);
-  double p = (g - 1.0) * eint * P0;
-  double T = p / ((nH + nH2) * ChemConst::KB);
+  const double nH = rho - rh2, nH2 = 0.5 * rh2, n = rho;
+  const double num = (2.0 * P0) * eint;
+  const double den = (3.0 * nH + 5.0 * nH2) * ChemConst::KB;
+  const double r = 1.0 / (num * den);
+  const double T = (num * num) * r, iT = (den * den) * r;
   // App. D rates
-  double t2, a2, a3;
-  if (fast) {
-    const double iT = 1.0 / T;
-    t2 = T * 0.01;
-    a2 = T > 7390.0 ? -2.93e4 * iT : -((6750.0 * iT) * (6750.0 * iT));
-    a3 = T > 7291.0 ? -3.22e4 * iT : -(4060.0 * iT) - (7500.0 * iT) * (7500.0 * iT);
-  } else {
-    t2 = T / 100.0;
-    a2 = T > 7390.0 ? -2.93e4 / T : -((6750.0 / T) * (6750.0 / T));
-    a3 = T > 7291.0 ? -3.22e4 / T : -(4060.0 / T) - (7500.0 / T) * (7500.0 / T);
-  }
-  double s2 = sqrt(t2);
-  double k1p = 3e-17 * s2 / (((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2));
+  const double t2 = T * 0.01;
+  const double a2 = T > 7390.0 ? -2.93e4 * iT : -((6750.0 * iT) * (6750.0 * iT));
+  const double a3 = T > 7291.0 ? -3.22e4 * iT : -(4060.0 * iT) - (7500.0 * iT) * (7500.0 * iT);
+  const double s2 = sqrt(t2);
+  const double k1p = 3e-17 * s2 / (((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2));
   // exp of an argument below -746 is exactly 0 in double: skip the call in cold gas
-  double k2 = a2 < -746.0 ? 0.0 : (T > 7390.0 ? 6.11e-14 : 2.67e-15) * exp(a2);
-  double k3 = a3 < -746.0 ? 0.0 : (T > 7291.0 ? 5.22e-14 : 3.17e-15) * exp(a3);
-  double Ls = (ph.lshield > 0.0 ? ph.lshield : ph.dx) * ChemConst::PC;
-  double NH = nH * Ls, NH2 = nH2 * Ls;
-  double fdust = exp(-(ph.taud * (NH + NH2)));
-  double x = fast ? NH2 * ph.ixnorm : NH2 / ph.xnorm;
-  double u = fast ? 1.0 + x * ph.ibdop : 1.0 + x / ph.bdop;
-  double sx = sqrt(1.0 + x);
-  double fsh = 0.965 / (u * u) + 0.035 / sx * exp(-8.5e-4 * sx);
-  double k4 = (3.3 * 1.7e-11) * fsh * fdust;
-  double C = k1p * n * nH;
-  double D = (k2 * nH + k3 * nH2) + k4;
-  double ts = tau * T0;
+  const double k2 = a2 < -746.0 ? 0.0 : (T > 7390.0 ? 6.11e-14 : 2.67e-15) * exp(a2);
+  const double k3 = a3 < -746.0 ? 0.0 : (T > 7291.0 ? 5.22e-14 : 3.17e-15) * exp(a3);
+  const double Ls = (ph.lshield > 0.0 ? ph.lshield : ph.dx) * ChemConst::PC;
+  const double NH = nH * Ls, NH2 = nH2 * Ls;
+  const double fdust = exp(-(ph.taud * (NH + NH2)));
+  const double x = NH2 * ph.ixnorm;
+  const double u = 1.0 + x * ph.ibdop;
+  const double isx = rsqrt(1.0 + x);
+  const double sx = (1.0 + x) * isx;
+  const double fsh = 0.965 / (u * u) + (0.035 * isx) * exp(-8.5e-4 * sx);
+  const double k4 = (3.3 * 1.7e-11) * fsh * fdust;
+  const double C = k1p * n * nH;
+  const double D = (k2 * nH + k3 * nH2) + k4;
+  const double ts = tau * T0;
   double nH2n = nH2 + ts * (C - D * nH2) / (1.0 + ts * D);
   if (nH2n < 0.0) nH2n = 0.0;
   if (nH2n > 0.5 * n) nH2n = 0.5 * n;

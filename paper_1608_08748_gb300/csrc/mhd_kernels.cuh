@@ -522,7 +522,7 @@ __device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, int do_chem,
   decode(c, g.n[0], g.n[1], q);
   const double tau = B.sc->tau;
   if (do_chem && ph.chem)
-    s.rh2[c] = (T)chem_cell<(sizeof(T) == 4)>(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c], tau);
+    s.rh2[c] = (T)chem_cell(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c], tau);
   idx_t up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
   T Bc[3];
 #pragma unroll
@@ -562,16 +562,9 @@ __device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, int do_chem,
     if (!isfinite(vals[k])) bad = 1;
   if (!(rho > T(0)) || !(eint > T(0))) bad = 1;
   double gm = ph.chem ? gamma_eff((double)rho, (double)s.rh2[c]) : ph.gamma;
-  if (!bad) {
-    double rr = (double)rho;
-    double pp = (gm - 1.0) * (double)eint;  // FP64 CFL of the new state (FP32 fields widened)
-    if (sizeof(T) == 8)
-      D = cfl_denominator(rr, (double)m[0] / rr, (double)m[1] / rr, (double)m[2] / rr, (double)Bc[0],
-                          (double)Bc[1], (double)Bc[2], pp, gm);
-    else
-      D = cfl_denominator_fast(rr, (double)m[0] / rr, (double)m[1] / rr, (double)m[2] / rr,
-                               (double)Bc[0], (double)Bc[1], (double)Bc[2], pp, gm);
-  }
+  if (!bad)  // FP64 CFL of the new state (FP32 fields widened)
+    D = cfl_denominator((double)rho, (double)m[0], (double)m[1], (double)m[2], (double)Bc[0],
+                        (double)Bc[1], (double)Bc[2], gm * ((gm - 1.0) * (double)eint));
 }
 
 template <typename T>
