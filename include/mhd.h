@@ -142,7 +142,7 @@ enum mhd_kernel_class {
   MHD_K_LAG_FACE = 4,    /* Lagrangian face fluxes, all three directions */
   MHD_K_LAG_UPDATE = 5,  /* Lagrangian update */
   MHD_K_POST = 6,        /* chemistry + regularisation + CFL of the new state */
-  MHD_K_SMALL = 7,       /* single-thread bookkeeping kernels and the RK register copies */
+  MHD_K_SMALL = 7,       /* single-thread bookkeeping kernels (step begin and end) */
   MHD_K_NCLASSES = 8
 };
 
@@ -174,8 +174,9 @@ int mhd_batch_sync(mhd_batch* b);
    timing `reps` full steps per candidate; the members' states are restored afterwards, so tuning
    changes no results.  best_ms (may be NULL) receives the tuned per-step time. */
 int mhd_batch_tune(mhd_batch* b, double cfl, int reps, double* best_ms);
-/* Launch shape of one kernel class (MHD_K_* of mhd_profile; MHD_K_SMALL = the RK register copy):
-   threads per tile (64, 128, 256 or 512) and grid = grid_mult x SMs (0: one block per tile). */
+/* Launch shape of one kernel class (MHD_K_PRIM .. MHD_K_POST of mhd_profile; MHD_K_SMALL has no
+   shape and gives MHD_EINVAL): threads per tile (64, 128, 256 or 512) and grid = grid_mult x SMs
+   (0: one block per tile). */
 int mhd_batch_get_shape(mhd_batch* b, int kernel_class, int* block, int* grid_mult);
 int mhd_batch_set_shape(mhd_batch* b, int kernel_class, int block, int grid_mult);
 /* Per-class CUDA-event timings of `steps` batch steps (as mhd_profile). */

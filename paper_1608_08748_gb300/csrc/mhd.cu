@@ -556,9 +556,9 @@ int mhd_stage(mhd_sim* S, int which, double tau) {
 
 int mhd_launches_per_step(mhd_sim* S) {
   if (!valid(S)) return fail(MHD_EINVAL, "mhd_launches_per_step: null sim");
-  // begin + Q^n + 3 x (primitives, 3 faces, edges, update) + Q^n + 3 x (3 faces, update) + post
-  // + end
-  return 1 + 1 + 3 * 6 + 1 + 3 * 4 + 1 + 1;
+  // begin + 3 x (primitives, 3 faces, edges, update) + 3 x (3 faces, update) + post + end (the
+  // first update of each stage stores its RK register Q^n)
+  return 1 + 3 * 6 + 3 * 4 + 1 + 1;
 }
 
 int mhd_profile(mhd_sim* S, double cfl, int steps, double* out_ms, int64_t* out_launches) {

@@ -58,11 +58,12 @@ struct State {
 // ------------------------------------------------------------------------------------------------
 // indexing: cells [k][j][i]; face / edge scratch arrays on the (n+1)^3 lattice
 __device__ __forceinline__ int wrap(int i, int n, int bc) {
+  if ((unsigned)i < (unsigned)n) return i;  // interior: no integer division
   if (bc == 0) {
     int r = i % n;
     return r < 0 ? r + n : r;
   }
-  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+  return i < 0 ? 0 : n - 1;
 }
 // Cell, face and lattice indices are 32-bit: mhd_create rejects grids whose (n+1)^3 lattice does
 // not fit (512^3 needs 1.35e8).
@@ -713,9 +714,10 @@ __device__ __forceinline__ double cfl_denominator(double rho, double mx, double 
 }
 
 // Sec. 4.3 effective adiabatic index of the H/H2 mixture (no electrons)
-__device__ __forceinline__ double gamma_eff(double rho, double rh2) {
-  double nH = rho - rh2, nH2 = 0.5 * rh2;
-  return (5.0 * nH + 7.0 * nH2) / (3.0 * nH + 5.0 * nH2);
+template <typename T>
+__device__ __forceinline__ T gamma_eff(T rho, T rh2) {
+  T nH = rho - rh2, nH2 = T(0.5) * rh2;
+  return (T(5) * nH + T(7) * nH2) / (T(3) * nH + T(5) * nH2);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -82,8 +82,8 @@ __device__ __forceinline__ void prim_cell(const Box<T>& B, idx_t c) {
   idx_t up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
 #pragma unroll
   for (int d = 0; d < 3; ++d) B.w.B[d][c] = T(0.5) * (B.s.b[d][c] + B.s.b[d][up[d]]);
-  double gm = B.ph.chem ? gamma_eff((double)rho, (double)B.s.rh2[c]) : B.ph.gamma;
-  T gmt = (T)gm;
+  // gamma_eff in the bulk type: the FP32-bulk path's fluxes are FP32
+  T gmt = B.ph.chem ? gamma_eff(rho, B.s.rh2[c]) : (T)B.ph.gamma;
 #pragma unroll
   for (int d = 0; d < 3; ++d) B.w.v[d][c] = B.s.m[d][c] / rho;
   B.w.p[c] = (gmt - T(1)) * B.s.eint[c];
@@ -265,6 +265,21 @@ __global__ void __launch_bounds__(512) kb_edges(const Box<T>* __restrict__ boxes
   }
 }
 
+// SSP-RK3 combination of Sec. 2.2 for one value: a Q^n + b Q + g tau R.  The first substage has
+// a = 0 and stores Q^n (the stage's start value, the Q it reads) in the RK register instead of
+// reading it; later substages read it.
+template <typename T>
+__device__ __forceinline__ T rk_combine(T* qn, T q, T a, T b, T g, T tauR, int r) {
+  T q0;
+  if (r == 0) {
+    *qn = q;
+    q0 = q;
+  } else {
+    q0 = *qn;
+  }
+  return (a * q0 + b * q) + g * tauR;
+}
+
 // Eulerian update of one cell: finite-volume R of m, rho E, rho eps (Sec. 2.4 + A12), Flux-CT of
 // the cell's three faces (Sec. 2.5), SSP-RK3 combination (Sec. 2.2) with stage r.
 template <typename T>
@@ -295,14 +310,14 @@ __device__ __forceinline__ void euler_update_cell(const Box<T>& B, idx_t c, int 
   T* qq[5] = {B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint};
   T* q0[5] = {B.s0.m[0], B.s0.m[1], B.s0.m[2], B.s0.E, B.s0.eint};
 #pragma unroll
-  for (int v = 0; v < 5; ++v) qq[v][c] = (a * q0[v][c] + bb * qq[v][c]) + gg * (tau * Rv[v]);
+  for (int v = 0; v < 5; ++v) qq[v][c] = rk_combine(q0[v] + c, qq[v][c], a, bb, gg, tau * Rv[v], r);
   // Flux-CT: d b_d / dt = -(curl E)_d on the face i_d - 1/2 of this cell
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
     T curl = (B.e[d1][fup[d2]] - B.e[d1][f0]) - (B.e[d2][fup[d1]] - B.e[d2][f0]);
     T Rb = curl * ih;
-    B.s.b[d][c] = (a * B.s0.b[d][c] + bb * B.s.b[d][c]) + gg * (tau * Rb);
+    B.s.b[d][c] = rk_combine(B.s0.b[d] + c, B.s.b[d][c], a, bb, gg, tau * Rb, r);
   }
 }
 
@@ -465,7 +480,7 @@ __device__ __forceinline__ void lag_update_cell(const Box<T>& B, idx_t c, int r)
 #pragma unroll
     for (int d = 0; d < 3; ++d) acc = acc + (B.fo[d].f[v][f0] - B.fo[d].f[v][fup[d]]);
     T R = acc * ih;
-    qq[v][c] = (a * q0[v][c] + bb * qq[v][c]) + gg * (tau * R);
+    qq[v][c] = rk_combine(q0[v] + c, qq[v][c], a, bb, gg, tau * R, r);
   }
 }
 
@@ -475,28 +490,6 @@ __global__ void __launch_bounds__(512) kb_lag_update(const Box<T>* __restrict__ 
     const Box<T>& B = boxes[tl.box[t_]];
     idx_t c = tl.start[t_] + (idx_t)threadIdx.x;
     if (c < B.g.N) lag_update_cell(B, c, r);
-  }
-}
-
-// RK register Q^n of a stage: Eulerian (m, rho E, rho eps, b) or Lagrangian (rho, m, rho E,
-// rho eps, rho_H2)
-template <typename T>
-__global__ void __launch_bounds__(512) kb_save_qn(const Box<T>* __restrict__ boxes, Tiles tl, int lagrangian) {
-  MHD_TILE_LOOP(tl) {
-    const Box<T>& B = boxes[tl.box[t_]];
-    idx_t c = tl.start[t_] + (idx_t)threadIdx.x;
-    if (c >= B.g.N) continue;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) B.s0.m[d][c] = B.s.m[d][c];
-    B.s0.E[c] = B.s.E[c];
-    B.s0.eint[c] = B.s.eint[c];
-    if (lagrangian) {
-      B.s0.rho[c] = B.s.rho[c];
-      if (B.nv == 7) B.s0.rh2[c] = B.s.rh2[c];
-    } else {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) B.s0.b[d][c] = B.s.b[d][c];
-    }
   }
 }
 

@@ -16,11 +16,11 @@ using namespace mhd;
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // kernel classes with their own launch shape
-enum KClass { KC_PRIM = 0, KC_EFACE, KC_EDGES, KC_EUPD, KC_LFACE, KC_LUPD, KC_POST, KC_QN, NKC };
+enum KClass { KC_PRIM = 0, KC_EFACE, KC_EDGES, KC_EUPD, KC_LFACE, KC_LUPD, KC_POST, NKC };
 // profile class of each kernel class (include/mhd.h, enum mhd_kernel_class)
 inline int profile_class(int kc) {
   const int m[NKC] = {MHD_K_PRIM, MHD_K_EULER_FACE, MHD_K_EDGES, MHD_K_EULER_UPDATE,
-                      MHD_K_LAG_FACE, MHD_K_LAG_UPDATE, MHD_K_POST, MHD_K_SMALL};
+                      MHD_K_LAG_FACE, MHD_K_LAG_UPDATE, MHD_K_POST};
   return m[kc];
 }
 // profiler tags: PROF_KC_BASE + kernel class for the tiled kernels, MHD_K_SMALL for the rest
@@ -36,7 +36,7 @@ constexpr bool lag_in_pencils() { return sizeof(T) == 8; }
 template <typename T>
 inline int class_domain(int kc) {
   const int lag = lag_in_pencils<T>() ? DOM_PENCIL_X : DOM_FACE_X;
-  const int m[NKC] = {DOM_CELLS, DOM_PENCIL_X, DOM_LATTICE, DOM_CELLS, lag, DOM_CELLS, DOM_CELLS, DOM_CELLS};
+  const int m[NKC] = {DOM_CELLS, DOM_PENCIL_X, DOM_LATTICE, DOM_CELLS, lag, DOM_CELLS, DOM_CELLS};
   return m[kc];
 }
 
@@ -219,7 +219,6 @@ void launch_small(Exec<T>& X, cudaStream_t st, int which, double cfl = 0, double
 
 template <typename T>
 void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
-  launch_k(X, st, KC_QN, DOM_CELLS, kb_save_qn<T>, 0);
   for (int r = 0; r < 3; ++r) {
     launch_k(X, st, KC_PRIM, DOM_CELLS, kb_prim<T>);
     launch_k(X, st, KC_EFACE, DOM_PENCIL_X, kb_euler_pencil<T, 0>);
@@ -232,7 +231,6 @@ void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
 
 template <typename T>
 void launch_lag_stage(Exec<T>& X, cudaStream_t st) {
-  launch_k(X, st, KC_QN, DOM_CELLS, kb_save_qn<T>, 1);
   for (int r = 0; r < 3; ++r) {
     if constexpr (lag_in_pencils<T>()) {
       launch_k(X, st, KC_LFACE, DOM_PENCIL_X, kb_lag_pencil<T, 0>);
