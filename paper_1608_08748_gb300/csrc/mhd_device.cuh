@@ -368,36 +368,6 @@ __device__ __forceinline__ T avg_left_end(const Para<T>& P, T y) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Fast and slow magnetosonic speeds (Sec. 2.3) and the differences the alpha factors (Sec. 2.4)
-// need, without cancellation: with X = c^2 - c_a^2 and b_perp^2 = B_perp^2 / rho,
-//   c_f^2 - c_s^2 = sqrt(X^2 + b_perp^2 (2 c^2 + 2 c_a^2 + b_perp^2)),
-//   (c^2 - c_s^2)(c_f^2 - c^2) = c^2 b_perp^2,   c_f^2 c_s^2 = c^2 c_a^2,
-// so alpha_s (or alpha_f) is exactly 0 where B_perp = 0.
-template <typename T>
-struct Speeds {
-  T cf2, cs2, sq, dcs, dfc;  // dcs = c^2 - c_s^2, dfc = c_f^2 - c^2
-};
-
-template <typename T>
-__device__ __forceinline__ Speeds<T> mhd_speeds(T c2, T ca2, T bp2) {
-  Speeds<T> r;
-  T X = c2 - ca2;
-  T W = bp2 * ((T(2) * c2 + T(2) * ca2) + bp2);
-  r.sq = sqrt(X * X + W);
-  if (X >= T(0)) {
-    r.dcs = T(0.5) * ((X + r.sq) - bp2);
-    if (r.dcs < T(0)) r.dcs = T(0);
-    r.dfc = r.dcs > T(0) ? c2 * bp2 / r.dcs : T(0);
-  } else {
-    r.dfc = T(0.5) * ((bp2 - X) + r.sq);
-    r.dcs = r.dfc > T(0) ? c2 * bp2 / r.dfc : T(0);
-  }
-  r.cf2 = c2 + r.dfc;
-  r.cs2 = r.cf2 > T(0) ? c2 * ca2 / r.cf2 : T(0);
-  return r;
-}
-
-// ------------------------------------------------------------------------------------------------
 // Sec. 2.4 + App. A: Roe-type face state, eigenvectors and the characteristic Riemann solution.
 // wl/wr = (rho, p, gamma, B_t1, B_t2, sqrt(rho)) of the left/right cell; Bn the face field.
 // qs = (V_n, V_t1, V_t2, B_t1, B_t2, P).
@@ -409,8 +379,8 @@ __device__ __forceinline__ Speeds<T> mhd_speeds(T c2, T ca2, T bp2) {
 // c_f^2 c_s^2 = c^2 c_a^2) and 1/|B_perp|.  The left and right waves of each pair share their
 // rows up to the sign of the velocity components, so the rows are formed once.
 template <typename T>
-__device__ __forceinline__ void riemann_fp64(const T wl[6], const T wr[6], T Bn, const Para<T> pl[6],
-                                             const Para<T> pr[6], T tau_h, T qs[6]) {
+__device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, const Para<T> pl[6],
+                                        const Para<T> pr[6], T tau_h, T qs[6]) {
   const T INV_SQRT2 = T(0.70710678118654752440);
   const T sl = wl[5], sr = wr[5];
   const T iden = T(1) / (sl + sr);
@@ -428,7 +398,10 @@ __device__ __forceinline__ void riemann_fp64(const T wl[6], const T wr[6], T Bn,
   const T bp2 = Bt1 * Bt1 + Bt2 * Bt2;
   const T bp2r = bp2 * irho;
   const T s = c2 + (ca2 + bp2r);
-  // fast and slow speeds without cancellation (see mhd_speeds)
+  // fast and slow speeds without cancellation: with X = c^2 - c_a^2 and b_perp^2 = B_perp^2 / rho,
+  //   c_f^2 - c_s^2 = sqrt(X^2 + b_perp^2 (2 c^2 + 2 c_a^2 + b_perp^2)),
+  //   (c^2 - c_s^2)(c_f^2 - c^2) = c^2 b_perp^2,
+  // so alpha_s (or alpha_f) is exactly 0 where B_perp = 0; dcs = c^2 - c_s^2, dfc = c_f^2 - c^2
   const T X = c2 - ca2;
   const T sq = sqrt(X * X + bp2r * ((T(2) * c2 + T(2) * ca2) + bp2r));
   T dcs, dfc;
@@ -526,171 +499,6 @@ __device__ __forceinline__ void riemann_fp64(const T wl[6], const T wr[6], T Bn,
   magnetosonic(Ls, Rs, pr, cs, false);  // wave 4: -c_s
   alfven(pl, true);                     // wave 5: +c_a
   alfven(pr, false);                    // wave 6: -c_a
-}
-
-// The same solution evaluated as written (one wave at a time, every entry formed in place), for
-// the FP32-bulk path.
-template <typename T>
-__device__ __forceinline__ void riemann_direct(const T wl[6], const T wr[6], T Bn, const Para<T> pl[6],
-                                        const Para<T> pr[6], T tau_h, T qs[6]) {
-  const T INV_SQRT2 = T(0.70710678118654752440);
-  T sl = wl[5], sr = wr[5];
-  T den = sl + sr;
-  T rho = (sl * wl[0] + sr * wr[0]) / den;
-  T p = (sl * wl[1] + sr * wr[1]) / den;
-  T gam = (sl * wl[2] + sr * wr[2]) / den;
-  T Bt1 = (sl * wr[3] + sr * wl[3]) / den;  // crossed weights for B
-  T Bt2 = (sl * wr[4] + sr * wl[4]) / den;
-
-  T c2 = gam * p / rho;
-  T ca2 = Bn * Bn / rho;
-  T bp2r = (Bt1 * Bt1 + Bt2 * Bt2) / rho;
-  T s = c2 + (ca2 + bp2r);
-  Speeds<T> sp = mhd_speeds(c2, ca2, bp2r);
-  T c = sqrt(c2), cf = sqrt(sp.cf2), cs = sqrt(sp.cs2), ca = sqrt(ca2);
-  T af, as;
-  if (sp.sq > T(1e-12) * s) {
-    af = sqrt(sp.dcs / sp.sq);
-    as = sqrt(sp.dfc / sp.sq);
-  } else {
-    af = INV_SQRT2;
-    as = INV_SQRT2;
-  }
-  T bp2 = Bt1 * Bt1 + Bt2 * Bt2;
-  T by, bz;
-  if (bp2 > T(1e-24) * rho * s) {
-    T bp = sqrt(bp2);
-    by = Bt1 / bp;
-    bz = Bt2 / bp;
-  } else {
-    by = INV_SQRT2;
-    bz = INV_SQRT2;
-  }
-  T sg = Bn >= T(0) ? T(1) : T(-1);
-  T sqr = sqrt(rho);
-  T gp = gam * p, sc = sqr * c, sr2 = sqrt(T(0.5) * rho);
-  T i2c2 = T(1) / (T(2) * c2), i2sc = T(1) / (T(2) * sc), i2rc2 = T(1) / (T(2) * rho * c2);
-  T isr2 = T(1) / sqrt(T(2) * rho);
-
-#pragma unroll
-  for (int m = 0; m < 6; ++m) qs[m] = T(0);
-
-  // one wave at a time: s_k = L_k . qbar_k, q* += R_{:,k} s_k (k ascending, as R s)
-  T qb[6];
-  T sk;
-  // wave 1: +c_f, left cell, right end
-  {
-    T y = cf * tau_h;
-#pragma unroll
-    for (int m = 0; m < 6; ++m) qb[m] = avg_right_end(pl[m], y);
-    sk = T(0);
-    sk = sk + af * cf * i2c2 * qb[0];
-    sk = sk + -as * cs * by * sg * i2c2 * qb[1];
-    sk = sk + -as * cs * bz * sg * i2c2 * qb[2];
-    sk = sk + as * by * i2sc * qb[3];
-    sk = sk + as * bz * i2sc * qb[4];
-    sk = sk + af * i2rc2 * qb[5];
-    qs[0] = qs[0] + af * cf * sk;
-    qs[1] = qs[1] + -as * cs * by * sg * sk;
-    qs[2] = qs[2] + -as * cs * bz * sg * sk;
-    qs[3] = qs[3] + as * sc * by * sk;
-    qs[4] = qs[4] + as * sc * bz * sk;
-    qs[5] = qs[5] + af * gp * sk;
-  }
-  // wave 2: -c_f, right cell, left end
-  {
-    T y = cf * tau_h;
-#pragma unroll
-    for (int m = 0; m < 6; ++m) qb[m] = avg_left_end(pr[m], y);
-    sk = T(0);
-    sk = sk + -af * cf * i2c2 * qb[0];
-    sk = sk + as * cs * by * sg * i2c2 * qb[1];
-    sk = sk + as * cs * bz * sg * i2c2 * qb[2];
-    sk = sk + as * by * i2sc * qb[3];
-    sk = sk + as * bz * i2sc * qb[4];
-    sk = sk + af * i2rc2 * qb[5];
-    qs[0] = qs[0] + -af * cf * sk;
-    qs[1] = qs[1] + as * cs * by * sg * sk;
-    qs[2] = qs[2] + as * cs * bz * sg * sk;
-    qs[3] = qs[3] + as * sc * by * sk;
-    qs[4] = qs[4] + as * sc * bz * sk;
-    qs[5] = qs[5] + af * gp * sk;
-  }
-  // wave 3: +c_s, left cell
-  {
-    T y = cs * tau_h;
-#pragma unroll
-    for (int m = 0; m < 6; ++m) qb[m] = avg_right_end(pl[m], y);
-    sk = T(0);
-    sk = sk + as * cs * i2c2 * qb[0];
-    sk = sk + af * cf * by * sg * i2c2 * qb[1];
-    sk = sk + af * cf * bz * sg * i2c2 * qb[2];
-    sk = sk + -af * by * i2sc * qb[3];
-    sk = sk + -af * bz * i2sc * qb[4];
-    sk = sk + as * i2rc2 * qb[5];
-    qs[0] = qs[0] + as * cs * sk;
-    qs[1] = qs[1] + af * cf * by * sg * sk;
-    qs[2] = qs[2] + af * cf * bz * sg * sk;
-    qs[3] = qs[3] + -af * sc * by * sk;
-    qs[4] = qs[4] + -af * sc * bz * sk;
-    qs[5] = qs[5] + as * gp * sk;
-  }
-  // wave 4: -c_s, right cell
-  {
-    T y = cs * tau_h;
-#pragma unroll
-    for (int m = 0; m < 6; ++m) qb[m] = avg_left_end(pr[m], y);
-    sk = T(0);
-    sk = sk + -as * cs * i2c2 * qb[0];
-    sk = sk + -af * cf * by * sg * i2c2 * qb[1];
-    sk = sk + -af * cf * bz * sg * i2c2 * qb[2];
-    sk = sk + -af * by * i2sc * qb[3];
-    sk = sk + -af * bz * i2sc * qb[4];
-    sk = sk + as * i2rc2 * qb[5];
-    qs[0] = qs[0] + -as * cs * sk;
-    qs[1] = qs[1] + -af * cf * by * sg * sk;
-    qs[2] = qs[2] + -af * cf * bz * sg * sk;
-    qs[3] = qs[3] + -af * sc * by * sk;
-    qs[4] = qs[4] + -af * sc * bz * sk;
-    qs[5] = qs[5] + as * gp * sk;
-  }
-  // wave 5: +c_a, left cell (no v_n, p components)
-  {
-    T y = ca * tau_h;
-#pragma unroll
-    for (int m = 1; m < 5; ++m) qb[m] = avg_right_end(pl[m], y);
-    sk = T(0);
-    sk = sk + -bz * sg * INV_SQRT2 * qb[1];
-    sk = sk + by * sg * INV_SQRT2 * qb[2];
-    sk = sk + bz * isr2 * qb[3];
-    sk = sk + -by * isr2 * qb[4];
-    qs[1] = qs[1] + -bz * INV_SQRT2 * sg * sk;
-    qs[2] = qs[2] + by * INV_SQRT2 * sg * sk;
-    qs[3] = qs[3] + sr2 * bz * sk;
-    qs[4] = qs[4] + -sr2 * by * sk;
-  }
-  // wave 6: -c_a, right cell
-  {
-    T y = ca * tau_h;
-#pragma unroll
-    for (int m = 1; m < 5; ++m) qb[m] = avg_left_end(pr[m], y);
-    sk = T(0);
-    sk = sk + -bz * sg * INV_SQRT2 * qb[1];
-    sk = sk + by * sg * INV_SQRT2 * qb[2];
-    sk = sk + -bz * isr2 * qb[3];
-    sk = sk + by * isr2 * qb[4];
-    qs[1] = qs[1] + -bz * INV_SQRT2 * sg * sk;
-    qs[2] = qs[2] + by * INV_SQRT2 * sg * sk;
-    qs[3] = qs[3] + -sr2 * bz * sk;
-    qs[4] = qs[4] + sr2 * by * sk;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, const Para<T> pl[6],
-                                        const Para<T> pr[6], T tau_h, T qs[6]) {
-  if constexpr (sizeof(T) == 8) riemann_fp64(wl, wr, Bn, pl, pr, tau_h, qs);
-  else riemann_direct(wl, wr, Bn, pl, pr, tau_h, qs);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -101,65 +101,11 @@ __global__ void __launch_bounds__(512) kb_prim(const Box<T>* __restrict__ boxes,
 }
 
 // ------------------------------------------------------------------------------------------------
-// Eulerian face of direction D: the face i_D - 1/2 between cells i_D - 1 and i_D, for i_D in
-// [0, n_D] and the other two indices in [0, n).
-template <typename T, int D>
-__device__ __forceinline__ void euler_face(const Box<T>& B, idx_t t) {
-  constexpr int D1 = (D + 1) % 3, D2 = (D + 2) % 3;
-  const Geom& g = B.g;
-  int ext[3] = {g.n[0], g.n[1], g.n[2]};
-  ext[D] += 1;
-  int c[3];
-  decode(t, ext[0], ext[1], c);
-  const T tau_h = (T)B.sc->tau_h;
-  idx_t cell[6];  // stencil cells i_D - 3 .. i_D + 2 along D
-#pragma unroll
-  for (int o = 0; o < 6; ++o) {
-    int cc[3] = {c[0], c[1], c[2]};
-    cc[D] += o - 3;
-    cell[o] = cmap(g, cc[0], cc[1], cc[2]);
-  }
-  const T* qv[6] = {B.w.v[D], B.w.v[D1], B.w.v[D2], B.w.B[D1], B.w.B[D2], B.w.p};
-  Para<T> pl[6], pr[6];
-#pragma unroll
-  for (int v = 0; v < 6; ++v) {
-    T q0 = qv[v][cell[0]], q1 = qv[v][cell[1]], q2 = qv[v][cell[2]], q3 = qv[v][cell[3]],
-      q4 = qv[v][cell[4]], q5 = qv[v][cell[5]];
-    pl[v] = ppm(q0, q1, q2, q3, q4);
-    pr[v] = ppm(q1, q2, q3, q4, q5);
-  }
-  idx_t cl = cell[2], cr = cell[3];
-  T wl[6] = {B.s.rho[cl], B.w.p[cl], B.w.g[cl], B.w.B[D1][cl], B.w.B[D2][cl], B.w.sr[cl]};
-  T wr[6] = {B.s.rho[cr], B.w.p[cr], B.w.g[cr], B.w.B[D1][cr], B.w.B[D2][cr], B.w.sr[cr]};
-  T Bn = B.s.b[D][cr];  // face i_D - 1/2 is stored with cell i_D (mapped: the nearest stored face)
-  T qs[6];
-  riemann(wl, wr, Bn, pl, pr, tau_h, qs);
-  // A12: non-advective fluxes from the face solution (V_n, V_t1, V_t2, B_t1, B_t2, P)
-  T Vn = qs[0], Vt1 = qs[1], Vt2 = qs[2], Bt1 = qs[3], Bt2 = qs[4], P = qs[5];
-  T pstar = P + T(0.5) * (Bn * Bn + Bt1 * Bt1 + Bt2 * Bt2);
-  idx_t f = fidx(g, c[0], c[1], c[2]);
-  const FaceOut<T>& fo = B.fo[D];
-  fo.f[0][f] = pstar - Bn * Bn;
-  fo.f[1][f] = -(Bn * Bt1);
-  fo.f[2][f] = -(Bn * Bt2);
-  fo.f[3][f] = pstar * Vn - Bn * (Bn * Vn + Bt1 * Vt1 + Bt2 * Vt2);
-  fo.f[4][f] = Vn;
-  fo.f[5][f] = Bn * Vt1 - Bt1 * Vn;  // E along t2 (Sec. 2.5: E = B x U)
-  fo.f[6][f] = Bt2 * Vn - Bn * Vt2;  // E along t1
-}
-
-template <typename T, int D>
-__global__ void __launch_bounds__(256) kb_euler_face(const Box<T>* __restrict__ boxes, Tiles tl) {
-  MHD_TILE_LOOP(tl) {
-    const Box<T>& B = boxes[tl.box[t_]];
-    idx_t t = tl.start[t_] + (idx_t)threadIdx.x;
-    idx_t total = (idx_t)(B.g.n[0] + (D == 0)) * (B.g.n[1] + (D == 1)) * (B.g.n[2] + (D == 2));
-    if (t < total) euler_face<T, D>(B, t);
-  }
-}
-
-// Eulerian faces i_D - 1/2 for i_D in [s PENCIL, min((s+1) PENCIL, n_D + 1)) of one pencil s; the
-// arithmetic per face is that of euler_face.
+// Eulerian faces of direction D (Sec. 2.4): the face i_D - 1/2 lies between cells i_D - 1 and i_D.
+// One thread takes the faces i_D in [s PENCIL, min((s+1) PENCIL, n_D + 1)) of one pencil s (the
+// other two indices in [0, n)); each cell's parabolas are built once and serve both its faces.
+// Per face: the PPM parabolas of (v_n, v_t1, v_t2, B_t1, B_t2, p) of the two cells, the Riemann
+// solve, and the non-advective fluxes with the two EMF contributions E = B x U (Sec. 2.5).
 template <typename T, int D>
 __device__ __forceinline__ void euler_pencil(const Box<T>& B, idx_t p) {
   constexpr int D1 = (D + 1) % 3, D2 = (D + 2) % 3;
@@ -219,7 +165,7 @@ __device__ __forceinline__ void euler_pencil(const Box<T>& B, idx_t p) {
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(256) kb_euler_pencil(const Box<T>* __restrict__ boxes, Tiles tl) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) kb_euler_pencil(const Box<T>* __restrict__ boxes, Tiles tl) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
     idx_t p = tl.start[t_] + (idx_t)threadIdx.x;
