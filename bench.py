@@ -39,9 +39,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # and eigenvector rows 116, the six waves' domain-of-dependence averages with L q and R s 286) and
 # the fluxes (25)
 FLOPS_PER_EULER_FACE = 643
-# DRAM bytes (read + write) of one x-direction Eulerian face launch at 128^3 from the ncu capture
-# summarised in profiles/kb_euler_pencil_turbulence_128_fp64.md (None when the kernel changes)
-EULER_FACE_TRAFFIC_BYTES = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one x-direction Eulerian face launch
+# at 128^3, from one ncu capture of this kernel (set to None whenever the kernel changes)
+EULER_FACE_TRAFFIC_BYTES = 328.4e6
 
 
 def reduce_max(x, dist=None, device="cpu"):
