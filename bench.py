@@ -34,14 +34,15 @@ METRIC = "Mcell-updates/s"
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # algorithmic FP64 flops of one Eulerian face, counted from the kernel source with an FMA as two
-# flops and a division, square root or reciprocal square root as one (compares not counted): the
-# parabolas of the six primitives of one new cell (6 x 36), the Riemann solve (Roe average, speeds
-# and eigenvector rows 116, the six waves' domain-of-dependence averages with L q and R s 286) and
-# the fluxes (25)
-FLOPS_PER_EULER_FACE = 643
+# flops and a division, square root or reciprocal square root as one (compares and selects not
+# counted): the parabolas of the six primitives of one new cell, streamed along the pencil (6 x 35:
+# differences, halved slope, edge value and second difference 11, Steps 2-5 21, the Step 4 test 3),
+# the Riemann solve (Roe average, speeds and eigenvector rows 116, the six waves'
+# domain-of-dependence averages with L q and R s 286) and the fluxes (25)
+FLOPS_PER_EULER_FACE = 637
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one x-direction Eulerian face launch
 # at 128^3, from one ncu capture of this kernel (set to None whenever the kernel changes)
-EULER_FACE_TRAFFIC_BYTES = 328.4e6
+EULER_FACE_TRAFFIC_BYTES = None
 
 
 def reduce_max(x, dist=None, device="cpu"):

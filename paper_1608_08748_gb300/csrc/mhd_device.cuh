@@ -226,38 +226,28 @@ __device__ __forceinline__ T half_slope(T s, T dn, T dp) {
   return with_sign_b(m, s);
 }
 
-// Sec. 2.1 Steps 1-5 for cell i from q_{i-2} .. q_{i+2}, with the Step 4 weights in the reading
-// where hbar weighs the flattened values q -+ delta_m q / 4 (the amendment acts in
-// discontinuities).  Written for few FP64 operations: the slopes are carried halved, the
-// differences q_{i+1} - q_{i-1} and the second differences are formed once, min(|q_{i+1}|,
-// |q_{i-1}|, |q_{i+1}| + |q_{i-1}|) is min(|q_{i+1}|, |q_{i-1}|), and eta = -(D+ - D-) / (3 dq) is
-// divided out only where it can exceed 1/20 (elsewhere hbar = 0 and Step 4 changes nothing;
-// hbar = 20 (eta - 1/20) is continuous there, so the test's rounding cannot move the result).
+// Steps 2-5 from the Step 1 edge values qL, qR of cell i (value qc, halved slope h0), the second
+// differences D+ and D-, s0 = q_{i+1} - q_{i-1} and q_{i+1}, q_{i-1}.  Steps 2 and 5 are taken by
+// selects, not branches: partly taken branches leave FP64 lanes idle, and the FP64 pipe is the
+// bound.
 template <typename T>
 __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm, T s0, T qp1, T qm1) {
   // Step 2: monotonicity
-  T dq = qR - qL;
-  T q6 = T(6) * (qc - T(0.5) * (qL + qR));
-  bool changed = false;
-  if (!same_sign(qL - qc, qc - qR)) {
-    qL = qc;
-    qR = qc;
-    changed = true;
-  } else {
+  {
+    const T dq = qR - qL;
+    const T q6 = T(6) * (qc - T(0.5) * (qL + qR));
+    const bool ext = !same_sign(qL - qc, qc - qR);
     const T a = dq * q6, b = dq * dq;
-    if (gt_nn(a, b)) {
-      qL = T(3) * qc - T(2) * qR;
-      changed = true;
-    } else if (gt_nn(neg_b(a), b)) {
-      qR = T(3) * qc - T(2) * qL;
-      changed = true;
-    }
+    const bool up = gt_nn(a, b), dn = !up && gt_nn(neg_b(a), b);
+    const T qLm = ext ? qc : (up ? T(3) * qc - T(2) * qR : qL);
+    const T qRm = ext ? qc : (dn ? T(3) * qc - T(2) * qL : qR);
+    qL = qLm;
+    qR = qRm;
   }
   // Step 4: discontinuity detector
   const T mn = min_nn(abs_b(qp1), abs_b(qm1));
   if (gt_nn(abs_b(s0), T(0.01) * mn) && !same_sign(Dp, Dm)) {
     const T num = Dm - Dp, den = T(3) * s0;  // eta = num / den, den != 0 here
-    // num / den > 1/20  <=>  num sgn(den) > |den| / 20
     const T num_s = sign_bit_b(den) ? neg_b(num) : num;
     if (gt_nn(num_s, T(0.05) * abs_b(den))) {
       const T eta = num / den;
@@ -267,23 +257,25 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
         const T qLp = qc - T(0.5) * h0, qRp = qc + T(0.5) * h0;
         qL = hb * qLp + (T(1) - hb) * qL;
         qR = hb * qRp + (T(1) - hb) * qR;
-        changed = true;
       }
     }
   }
   // Step 5
-  if (changed) {
-    dq = qR - qL;
-    q6 = T(6) * (qc - T(0.5) * (qL + qR));
-  }
   Para<T> P;
   P.L = qL;
   P.R = qR;
-  P.d = dq;
-  P.q6 = q6;
+  P.d = qR - qL;
+  P.q6 = T(6) * (qc - T(0.5) * (qL + qR));
   return P;
 }
 
+// Sec. 2.1 Steps 1-5 for cell i from q_{i-2} .. q_{i+2}, with the Step 4 weights in the reading
+// where hbar weighs the flattened values q -+ delta_m q / 4 (the amendment acts in
+// discontinuities).  Written for few FP64 operations: the slopes are carried halved, the
+// differences q_{i+1} - q_{i-1} and the second differences are formed once, min(|q_{i+1}|,
+// |q_{i-1}|, |q_{i+1}| + |q_{i-1}|) is min(|q_{i+1}|, |q_{i-1}|), and eta = -(D+ - D-) / (3 dq) is
+// divided out only where it can exceed 1/20 (elsewhere hbar = 0 and Step 4 changes nothing;
+// hbar = 20 (eta - 1/20) is continuous there, so the test's rounding cannot move the result).
 template <typename T>
 __device__ __forceinline__ Para<T> ppm_fp64(T qm2, T qm1, T qc, T qp1, T qp2) {
   const T THIRD = T(1.0 / 3.0);  // twice 1/6, exactly
@@ -404,14 +396,25 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
   // so alpha_s (or alpha_f) is exactly 0 where B_perp = 0; dcs = c^2 - c_s^2, dfc = c_f^2 - c^2
   const T X = c2 - ca2;
   const T sq = sqrt(X * X + bp2r * ((T(2) * c2 + T(2) * ca2) + bp2r));
+  // the larger of the two differences from the sum, the other from their product
   T dcs, dfc;
-  if (X >= T(0)) {
-    dcs = T(0.5) * ((X + sq) - bp2r);
-    if (dcs < T(0)) dcs = T(0);
-    dfc = dcs > T(0) ? c2 * bp2r / dcs : T(0);
+  if constexpr (sizeof(T) == 8) {
+    // one FP64 division for both signs of X, so a warp with both signs does not take two
+    const bool xpos = X >= T(0);
+    T big = xpos ? T(0.5) * ((X + sq) - bp2r) : T(0.5) * ((bp2r - X) + sq);
+    if (big < T(0)) big = T(0);
+    const T other = big > T(0) ? c2 * bp2r / big : T(0);
+    dcs = xpos ? big : other;
+    dfc = xpos ? other : big;
   } else {
-    dfc = T(0.5) * ((bp2r - X) + sq);
-    dcs = dfc > T(0) ? c2 * bp2r / dfc : T(0);
+    if (X >= T(0)) {
+      dcs = T(0.5) * ((X + sq) - bp2r);
+      if (dcs < T(0)) dcs = T(0);
+      dfc = dcs > T(0) ? c2 * bp2r / dcs : T(0);
+    } else {
+      dfc = T(0.5) * ((bp2r - X) + sq);
+      dcs = dfc > T(0) ? c2 * bp2r / dfc : T(0);
+    }
   }
   const T cf2 = c2 + dfc;
   const T rc = rsqrt_t(c2), rcf = rsqrt_t(cf2);

@@ -101,6 +101,38 @@ __global__ void __launch_bounds__(512) kb_prim(const Box<T>* __restrict__ boxes,
 }
 
 // ------------------------------------------------------------------------------------------------
+// The FP64 Eulerian pencils keep each primitive's PPMStream in this thread's slots of dynamic
+// shared memory between faces (9 values x 6 primitives; value k of primitive v at
+// [(9 v + k) blockDim.x + threadIdx.x], so a warp's accesses are consecutive).
+__device__ __forceinline__ double& stream_slot(int v, int k) {
+  extern __shared__ double stream_smem[];
+  return stream_smem[(9 * v + k) * blockDim.x + threadIdx.x];
+}
+__device__ __forceinline__ void stream_save(const PPMStream<double>& S, int v) {
+  stream_slot(v, 0) = S.qm;
+  stream_slot(v, 1) = S.q0;
+  stream_slot(v, 2) = S.qp;
+  stream_slot(v, 3) = S.dp;
+  stream_slot(v, 4) = S.h0;
+  stream_slot(v, 5) = S.eL;
+  stream_slot(v, 6) = S.Cm;
+  stream_slot(v, 7) = S.C0;
+  stream_slot(v, 8) = S.s0;
+}
+__device__ __forceinline__ PPMStream<double> stream_load(int v) {
+  PPMStream<double> S;
+  S.qm = stream_slot(v, 0);
+  S.q0 = stream_slot(v, 1);
+  S.qp = stream_slot(v, 2);
+  S.dp = stream_slot(v, 3);
+  S.h0 = stream_slot(v, 4);
+  S.eL = stream_slot(v, 5);
+  S.Cm = stream_slot(v, 6);
+  S.C0 = stream_slot(v, 7);
+  S.s0 = stream_slot(v, 8);
+  return S;
+}
+
 // Eulerian faces of direction D (Sec. 2.4): the face i_D - 1/2 lies between cells i_D - 1 and i_D.
 // One thread takes the faces i_D in [s PENCIL, min((s+1) PENCIL, n_D + 1)) of one pencil s (the
 // other two indices in [0, n)); each cell's parabolas are built once and serve both its faces.
@@ -129,17 +161,36 @@ __device__ __forceinline__ void euler_pencil(const Box<T>& B, idx_t p) {
     idx_t cell[5];
 #pragma unroll
     for (int o = 0; o < 5; ++o) cell[o] = cell_at(f0 - 3 + o);
+    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-    for (int v = 0; v < 6; ++v)
-      pl[v] = ppm(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
+      for (int v = 0; v < 6; ++v) {
+        PPMStream<double> S;
+        S.prime(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]]);
+        pl[v] = S.next(qv[v][cell[4]]);  // cell f0 - 1
+        stream_save(S, v);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 6; ++v)
+        pl[v] = ppm(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
+    }
   }
   for (int i = f0; i < f1; ++i) {
     idx_t cell[5];
 #pragma unroll
     for (int o = 0; o < 5; ++o) cell[o] = cell_at(i - 2 + o);
+    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-    for (int v = 0; v < 6; ++v)
-      pr[v] = ppm(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
+      for (int v = 0; v < 6; ++v) {
+        PPMStream<double> S = stream_load(v);
+        pr[v] = S.next(qv[v][cell[4]]);  // cell i
+        stream_save(S, v);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 6; ++v)
+        pr[v] = ppm(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
+    }
     idx_t cl = cell[1], cr = cell[2];
     T wl[6] = {B.s.rho[cl], B.w.p[cl], B.w.g[cl], B.w.B[D1][cl], B.w.B[D2][cl], B.w.sr[cl]};
     T wr[6] = {B.s.rho[cr], B.w.p[cr], B.w.g[cr], B.w.B[D1][cr], B.w.B[D2][cr], B.w.sr[cr]};

@@ -33,6 +33,10 @@ inline int report_class(int tag) { return tag >= PROF_KC_BASE ? profile_class(ta
 template <typename T>
 constexpr bool lag_in_pencils() { return sizeof(T) == 8; }
 
+// shared memory per thread of the Eulerian pencils: the FP64 path keeps six PPMStreams there
+template <typename T>
+constexpr size_t euler_pencil_smem() { return sizeof(T) == 8 ? 6 * 9 * sizeof(double) : 0; }
+
 template <typename T>
 inline int class_domain(int kc) {
   const int lag = lag_in_pencils<T>() ? DOM_PENCIL_X : DOM_FACE_X;
@@ -174,6 +178,12 @@ cudaError_t exec_init(Exec<T>& X, const std::vector<Box<T>>& boxes) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&X.nsm, cudaDevAttrMultiProcessorCount, dev);
+  if constexpr (euler_pencil_smem<T>() > 0) {  // up to 256 threads per block
+    const int bytes = (int)(256 * euler_pencil_smem<T>());
+    cudaFuncSetAttribute(kb_euler_pencil<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(kb_euler_pencil<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(kb_euler_pencil<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  }
   default_cfgs(X);
   cudaError_t e = cudaMalloc(&X.d, sizeof(Box<T>) * (size_t)X.nb);
   if (e != cudaSuccess) return e;
@@ -199,12 +209,17 @@ void exec_free(Exec<T>& X) {
 // ------------------------------------------------------------------------------------------------
 // launchers
 template <typename T, typename K, typename... A>
-void launch_k(Exec<T>& X, cudaStream_t st, int kc, int dom, K kernel, A... args) {
+void launch_ks(Exec<T>& X, cudaStream_t st, int kc, int dom, size_t smem_per_thread, K kernel, A... args) {
   const LaunchCfg& c = X.cfg[kc];
   Tiles t = tiles_of(X, dom, c.block);
   PScope p(X.prof, st, PROF_KC_BASE + kc);  // the profiler records the kernel class
-  kernel<<<grid_of(t, c, X.nsm), c.block, 0, st>>>(X.d, t, args...);
+  kernel<<<grid_of(t, c, X.nsm), c.block, smem_per_thread * c.block, st>>>(X.d, t, args...);
 }
+template <typename T, typename K, typename... A>
+void launch_k(Exec<T>& X, cudaStream_t st, int kc, int dom, K kernel, A... args) {
+  launch_ks(X, st, kc, dom, 0, kernel, args...);
+}
+
 
 template <typename T>
 void launch_small(Exec<T>& X, cudaStream_t st, int which, double cfl = 0, double t_end = 0,
@@ -221,9 +236,9 @@ template <typename T>
 void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
   for (int r = 0; r < 3; ++r) {
     launch_k(X, st, KC_PRIM, DOM_CELLS, kb_prim<T>);
-    launch_k(X, st, KC_EFACE, DOM_PENCIL_X, kb_euler_pencil<T, 0>);
-    launch_k(X, st, KC_EFACE, DOM_PENCIL_Y, kb_euler_pencil<T, 1>);
-    launch_k(X, st, KC_EFACE, DOM_PENCIL_Z, kb_euler_pencil<T, 2>);
+    launch_ks(X, st, KC_EFACE, DOM_PENCIL_X, euler_pencil_smem<T>(), kb_euler_pencil<T, 0>);
+    launch_ks(X, st, KC_EFACE, DOM_PENCIL_Y, euler_pencil_smem<T>(), kb_euler_pencil<T, 1>);
+    launch_ks(X, st, KC_EFACE, DOM_PENCIL_Z, euler_pencil_smem<T>(), kb_euler_pencil<T, 2>);
     launch_k(X, st, KC_EDGES, DOM_LATTICE, kb_edges<T>);
     launch_k(X, st, KC_EUPD, DOM_CELLS, kb_euler_update<T>, r);
   }
