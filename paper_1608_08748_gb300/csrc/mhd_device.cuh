@@ -99,8 +99,9 @@ __device__ __forceinline__ T slope_m(T qm, T q0, T qp) {
   return T(0);
 }
 
-// Steps 1-5 from q_{i-2} .. q_{i+2} evaluated as written, for the FP32-bulk path (whose FP32 pipes
-// have room for the plain form); the FP64 path takes ppm below.
+// Steps 1-5 from q_{i-2} .. q_{i+2} evaluated as written: the FP32 Eulerian pencils take this form
+// (their bound is instruction issue, and this one has the fewest branches there); ppm_lean below
+// serves the other parabolas.
 template <typename T>
 __device__ __forceinline__ Para<T> ppm_direct(T qm2, T qm1, T qc, T qp1, T qp2) {
   const T SIXTH = T(1.0 / 6.0);
@@ -277,7 +278,7 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
 // divided out only where it can exceed 1/20 (elsewhere hbar = 0 and Step 4 changes nothing;
 // hbar = 20 (eta - 1/20) is continuous there, so the test's rounding cannot move the result).
 template <typename T>
-__device__ __forceinline__ Para<T> ppm_fp64(T qm2, T qm1, T qc, T qp1, T qp2) {
+__device__ __forceinline__ Para<T> ppm_lean(T qm2, T qm1, T qc, T qp1, T qp2) {
   const T THIRD = T(1.0 / 3.0);  // twice 1/6, exactly
   const T d0 = qm1 - qm2, d1 = qc - qm1, d2 = qp1 - qc, d3 = qp2 - qp1;
   const T sm = qc - qm2, s0 = qp1 - qm1, sp = qp2 - qc;
@@ -291,7 +292,7 @@ __device__ __forceinline__ Para<T> ppm_fp64(T qm2, T qm1, T qc, T qp1, T qp2) {
   return ppm_limit(qL, qR, qc, h0, Dp, Dm, s0, qp1, qm1);
 }
 
-// The parabolas of consecutive cells j, j+1, ... along a line, each from the quantities ppm_fp64
+// The parabolas of consecutive cells j, j+1, ... along a line, each from the quantities ppm_lean
 // forms for it (so bit for bit the same), where the difference q_{j+1} - q_j, the halved slope, the
 // edge value between two cells and the second difference centred on a cell are formed once and
 // shared by the neighbours that use them.  Prime with q_{J-2} .. q_{J+1}; each next(q_{j+2}) then
@@ -339,13 +340,6 @@ struct PPMStream {
     return P;
   }
 };
-
-// Sec. 2.1 Steps 1-5 for cell i from q_{i-2} .. q_{i+2}
-template <typename T>
-__device__ __forceinline__ Para<T> ppm(T qm2, T qm1, T qc, T qp1, T qp2) {
-  if constexpr (sizeof(T) == 8) return ppm_fp64(qm2, qm1, qc, qp1, qp2);
-  else return ppm_direct(qm2, qm1, qc, qp1, qp2);
-}
 
 // Sec. 2.4: parabola averages over the domain of dependence of a wave of |speed| y h / tau
 template <typename T>

@@ -172,7 +172,7 @@ __device__ __forceinline__ void euler_pencil(const Box<T>& B, idx_t p) {
     } else {
 #pragma unroll
       for (int v = 0; v < 6; ++v)
-        pl[v] = ppm(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
+        pl[v] = ppm_direct(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
     }
   }
   for (int i = f0; i < f1; ++i) {
@@ -189,7 +189,7 @@ __device__ __forceinline__ void euler_pencil(const Box<T>& B, idx_t p) {
     } else {
 #pragma unroll
       for (int v = 0; v < 6; ++v)
-        pr[v] = ppm(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
+        pr[v] = ppm_direct(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]], qv[v][cell[4]]);
     }
     idx_t cl = cell[1], cr = cell[2];
     T wl[6] = {B.s.rho[cl], B.w.p[cl], B.w.g[cl], B.w.B[D1][cl], B.w.B[D2][cl], B.w.sr[cl]};
@@ -362,7 +362,7 @@ __device__ __forceinline__ void lag_face(const Box<T>& B, idx_t t) {
   for (int v = 0; v < 7; ++v) {
     if (v >= nv) break;
     const T* a = q[v];
-    Para<T> P = ppm(a[st[0]], a[st[1]], a[st[2]], a[st[3]], a[st[4]]);
+    Para<T> P = ppm_lean(a[st[0]], a[st[1]], a[st[2]], a[st[3]], a[st[4]]);
     T qb = o0 == 0 ? avg_right_end(P, y) : avg_left_end(P, y);
     B.fo[D].f[v][f] = vn * qb;
   }
