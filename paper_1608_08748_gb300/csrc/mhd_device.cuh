@@ -147,6 +147,7 @@ __device__ __forceinline__ Para<T> ppm_direct(T qm2, T qm1, T qc, T qp1, T qp2) 
   return P;
 }
 
+// ---- begin integer-pipe helpers ----
 // Sign tests, absolute values, minima and comparisons of doubles on the integer pipes.  On sm_103
 // the FP64 pipe issues two instructions per clock per SM and the integer pipes 64, and the PPM
 // limiter is mostly such tests.  They work on the two 32-bit halves in inline PTX, so that the
@@ -213,6 +214,8 @@ __device__ __forceinline__ bool sign_bit_b(double x) {
   return r != 0;
 }
 __device__ __forceinline__ bool sign_bit_b(float x) { return signbit(x); }
+
+// ---- end integer-pipe helpers ----
 
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }

@@ -1,0 +1,236 @@
+// The CUDA path's per-face and per-cell arithmetic (mhd_device.cuh) compiled for the host and
+// compared with the oracle's unit entry points on seeded random and adversarial inputs.  The test
+// that builds this file gives it a copy of the header in which the inline-PTX integer-pipe helpers
+// are replaced by portable C++ with the same definitions (MHD_DEVICE_HOST_COPY).  Prints one line
+// per check: "<name> <cases> <worst relative difference> <cases beyond the bound>".
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+
+static inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
+static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+#include MHD_DEVICE_HOST_COPY
+
+extern "C" {
+struct osim;
+osim* osim_create(int nx, int ny, int nz, double gamma, double dx);
+void osim_destroy(osim* s);
+void osim_chem_cell(const osim* s, double rho, double eint, double rh2, double tau, double out[8]);
+void o_ppm(const double q[5], int step4_as_written, double out[4]);
+void o_face_solve(const double wl[5], const double wr[5], double Bn, const double sl[30], const double sr[30],
+                  double tau_h, int edge, int step4_as_written, double out[6]);
+double o_cfl_denominator(const double w[9]);
+}
+
+using namespace mhd;
+
+static void report(const char* name, long n, double worst, long beyond) {
+  std::printf("%s %ld %.6e %ld\n", name, n, worst, beyond);
+}
+
+// stencils of five values: rough, smooth, jumps, oscillating, and on a coarse lattice (ties, zeros)
+static void stencil(std::mt19937_64& g, long it, double q[5]) {
+  std::uniform_real_distribution<double> U(-1, 1);
+  const int kind = (int)(it % 5);
+  for (int i = 0; i < 5; ++i) {
+    if (kind == 0) q[i] = U(g);
+    else if (kind == 1) q[i] = 1.0 + 0.01 * i + 1e-3 * U(g) * (i == 2);
+    else if (kind == 2) q[i] = (i < 2 + (it / 5) % 3) ? 1.0 : 0.125 + 1e-6 * U(g);
+    else if (kind == 3) q[i] = std::sin(0.3 * i + U(g)) * (1 + 0.1 * U(g));
+    else q[i] = std::round(4 * U(g)) / 4;
+  }
+}
+
+int main() {
+  std::mt19937_64 g(20160829);
+  std::uniform_real_distribution<double> U(-1, 1), U01(0, 1);
+
+  // 1. FP64 parabolas: the oracle's Steps 1-5 exactly (equal values)
+  {
+    const long n = 400000;
+    long bad = 0;
+    double worst = 0;
+    for (long it = 0; it < n; ++it) {
+      double q[5], o[4];
+      stencil(g, it, q);
+      o_ppm(q, 0, o);
+      const Para<double> P = ppm_lean(q[0], q[1], q[2], q[3], q[4]);
+      const double d[4] = {P.L, P.R, P.d, P.q6};
+      bool same = true;  // IEEE equality: -0 and +0 are the same value (the bit helpers may differ there)
+      for (int k = 0; k < 4; ++k) same = same && d[k] == o[k];
+      if (!same) {
+        ++bad;
+        for (int k = 0; k < 4; ++k) worst = std::max(worst, std::fabs(d[k] - o[k]));
+      }
+    }
+    report("ppm_lean_equal", n, worst, bad);
+  }
+  // 2. the streamed parabolas equal the five-point ones bit for bit
+  {
+    long n = 0, bad = 0;
+    for (int line = 0; line < 5000; ++line) {
+      double q[40];
+      const int kind = line % 4;
+      for (int i = 0; i < 40; ++i)
+        q[i] = kind == 0 ? U(g) : kind == 1 ? std::sin(0.2 * i + line) :
+               kind == 2 ? (i < 20 ? 1.0 : 0.125) + 1e-3 * U(g) : std::round(3 * U(g)) / 3;
+      PPMStream<double> S;
+      S.prime(q[0], q[1], q[2], q[3]);
+      for (int j = 2; j < 38; ++j) {
+        const Para<double> a = S.next(q[j + 2]);
+        const Para<double> b = ppm_lean(q[j - 2], q[j - 1], q[j], q[j + 1], q[j + 2]);
+        ++n;
+        if (std::memcmp(&a, &b, sizeof(a)) != 0) ++bad;
+      }
+    }
+    report("ppm_stream_bits", n, 0.0, bad);
+  }
+  // 3. FP32 parabolas of the FP32-bulk path against the FP64 oracle
+  {
+    const long n = 200000;
+    long bad = 0;
+    double worst = 0;
+    for (long it = 0; it < n; ++it) {
+      double q[5], o[4];
+      stencil(g, it, q);
+      for (int i = 0; i < 5; ++i) q[i] = (double)(float)q[i];
+      o_ppm(q, 0, o);
+      const Para<float> a = ppm_direct<float>(q[0], q[1], q[2], q[3], q[4]);
+      const Para<float> b = ppm_lean<float>(q[0], q[1], q[2], q[3], q[4]);
+      double sc = 0;
+      for (int i = 0; i < 5; ++i) sc = std::max(sc, std::fabs(q[i]));
+      const double da[4] = {a.L, a.R, a.d, a.q6}, db[4] = {b.L, b.R, b.d, b.q6};
+      for (int k = 0; k < 4; ++k) {
+        const double e = std::max(std::fabs(da[k] - o[k]), std::fabs(db[k] - o[k])) / (sc + 1e-300);
+        worst = std::max(worst, e);
+        if (e > 1e-5) ++bad;
+      }
+    }
+    report("ppm_fp32", n, worst, bad);
+  }
+  // 4. Riemann solve at a face (both precisions) against the oracle's face solve
+  {
+    const long n = 200000;
+    long bad64 = 0, bad32 = 0;
+    double w64 = 0, w32 = 0;
+    for (long it = 0; it < n; ++it) {
+      double wl5[5], wr5[5], sl[30], sr[30];
+      auto state = [&](double* w) {
+        w[0] = std::exp(2 * U(g));
+        w[1] = std::exp(2 * U(g));
+        w[2] = 1.4 + 0.3 * U(g);
+        const bool no_perp = it % 4 == 1;
+        w[3] = no_perp ? 0.0 : U(g);
+        w[4] = no_perp ? 0.0 : U(g);
+      };
+      state(wl5);
+      state(wr5);
+      const double Bn = (it % 7 == 0) ? 0.0 : 2 * U(g);
+      for (int i = 0; i < 30; ++i) {
+        sl[i] = U(g);
+        sr[i] = U(g);
+      }
+      const double tau_h = 0.05 * (1 + U(g));
+      double o[6];
+      o_face_solve(wl5, wr5, Bn, sl, sr, tau_h, 0, 0, o);
+      double sc = 0;
+      for (int m = 0; m < 6; ++m) sc = std::max(sc, std::fabs(o[m]));
+      {
+        double wl[6], wr[6], qs[6];
+        for (int i = 0; i < 5; ++i) {
+          wl[i] = wl5[i];
+          wr[i] = wr5[i];
+        }
+        wl[5] = std::sqrt(wl5[0]);
+        wr[5] = std::sqrt(wr5[0]);
+        Para<double> pl[6], pr[6];
+        for (int v = 0; v < 6; ++v) {
+          pl[v] = ppm_lean(sl[5 * v], sl[5 * v + 1], sl[5 * v + 2], sl[5 * v + 3], sl[5 * v + 4]);
+          pr[v] = ppm_lean(sr[5 * v], sr[5 * v + 1], sr[5 * v + 2], sr[5 * v + 3], sr[5 * v + 4]);
+        }
+        riemann(wl, wr, Bn, pl, pr, tau_h, qs);
+        for (int m = 0; m < 6; ++m) {
+          const double e = std::fabs(qs[m] - o[m]) / (sc + 1e-300);
+          w64 = std::max(w64, e);
+          if (e > 1e-12) ++bad64;
+        }
+      }
+      {
+        float wl[6], wr[6], qs[6];
+        for (int i = 0; i < 5; ++i) {
+          wl[i] = (float)wl5[i];
+          wr[i] = (float)wr5[i];
+        }
+        wl[5] = std::sqrt(wl[0]);
+        wr[5] = std::sqrt(wr[0]);
+        Para<float> pl[6], pr[6];
+        for (int v = 0; v < 6; ++v) {
+          pl[v] = ppm_direct<float>(sl[5 * v], sl[5 * v + 1], sl[5 * v + 2], sl[5 * v + 3], sl[5 * v + 4]);
+          pr[v] = ppm_direct<float>(sr[5 * v], sr[5 * v + 1], sr[5 * v + 2], sr[5 * v + 3], sr[5 * v + 4]);
+        }
+        riemann<float>(wl, wr, (float)Bn, pl, pr, (float)tau_h, qs);
+        for (int m = 0; m < 6; ++m) {
+          const double e = std::fabs(qs[m] - o[m]) / (sc + 1e-300);
+          w32 = std::max(w32, e);
+          if (e > 1e-4) ++bad32;
+        }
+      }
+    }
+    report("riemann_fp64", n, w64, bad64);
+    report("riemann_fp32", n, w32, bad32);
+  }
+  // 5. chemistry of one cell (FP64) against the oracle's
+  {
+    const double dx = 2.0;
+    osim* s = osim_create(4, 4, 4, 5.0 / 3.0, dx);
+    Phys ph{};
+    ph.dx = dx;
+    ph.ih = 1.0 / dx;
+    ph.chem = 1;
+    ph.lshield = 0.0;
+    ph.bdop = 3.0;
+    ph.xnorm = 5e14;
+    ph.taud = 1e-21;
+    ph.ibdop = 1.0 / ph.bdop;
+    ph.ixnorm = 1.0 / ph.xnorm;
+    const long n = 300000;
+    long bad = 0;
+    double worst = 0;
+    for (long it = 0; it < n; ++it) {
+      const double rho = std::exp(10 * U01(g) - 3);
+      const double rh2 = rho * U01(g) * (it % 3 ? 1.0 : 1e-6);
+      const double eint = rho * std::exp(14 * U01(g) - 6);
+      const double tau = std::exp(10 * U01(g) - 12);
+      double o[8];
+      osim_chem_cell(s, rho, eint, rh2, tau, o);
+      const double a = chem_cell(ph, rho, eint, rh2, tau);
+      const double e = std::fabs(a - o[0]) / std::max(std::fabs(o[0]), 1e-12 * rho);
+      worst = std::max(worst, e);
+      if (e > 1e-12) ++bad;
+    }
+    osim_destroy(s);
+    report("chemistry", n, worst, bad);
+  }
+  // 6. CFL denominator (FP64) against the oracle's
+  {
+    const long n = 300000;
+    long bad = 0;
+    double worst = 0;
+    for (long it = 0; it < n; ++it) {
+      const double rho = std::exp(4 * U(g));
+      const double m[3] = {10 * U(g), 10 * U(g), 10 * U(g)};
+      const double Bv[3] = {3 * U(g), (it % 5 == 0) ? 0.0 : 3 * U(g), (it % 7 == 0) ? 0.0 : 3 * U(g)};
+      const double gam = 1.4 + 0.3 * U01(g), p = std::exp(4 * U(g));
+      const double w[9] = {rho, m[0] / rho, m[1] / rho, m[2] / rho, Bv[0], Bv[1], Bv[2], p, gam};
+      const double o = o_cfl_denominator(w);
+      const double a = cfl_denominator(rho, m[0], m[1], m[2], Bv[0], Bv[1], Bv[2], gam * p);
+      const double e = std::fabs(a - o) / o;
+      worst = std::max(worst, e);
+      if (e > 1e-13) ++bad;
+    }
+    report("cfl", n, worst, bad);
+  }
+  return 0;
+}

@@ -1,0 +1,87 @@
+"""The CUDA path's device arithmetic compiled for the host and checked against the oracle on the CPU.
+
+The per-face and per-cell functions of mhd_device.cuh (PPM parabolas, the streamed parabolas, the
+Riemann solve, the chemistry of one cell, the CFL denominator) are plain C++ apart from a block of
+inline-PTX integer-pipe helpers; this test replaces that block with portable C++ of the same
+definitions, compiles tests/host_math/device_math_vs_oracle.cpp against it and the oracle library,
+and checks: the FP64 parabolas equal the oracle's exactly (Sec. 2.1; -0 and +0 count as equal), the streamed ones equal
+the five-point ones bit for bit, the Riemann solve (Sec. 2.4, App. A) is within 1e-12 of the
+oracle's in FP64 and 1e-4 in FP32, the chemistry (Sec. 2.7, App. D) within 1e-12 and the CFL
+denominator (Sec. 2.3) within 1e-13.  The host build uses -ffp-contract=off like the oracle; the
+GPU build contracts to FMA, whose effect the GPU parity tests bound."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "paper_1608_08748_gb300", "csrc", "mhd_device.cuh")
+HARNESS = os.path.join(ROOT, "tests", "host_math", "device_math_vs_oracle.cpp")
+BEGIN, END = "// ---- begin integer-pipe helpers ----", "// ---- end integer-pipe helpers ----"
+
+# portable C++ with the definitions of the inline-PTX helpers (sign, magnitude and ordering of the
+# bit patterns of doubles; the float overloads are the plain operations)
+PORTABLE = r'''
+static inline long long bits_(double x) { long long b; std::memcpy(&b, &x, 8); return b; }
+static inline double from_bits_(long long b) { double x; std::memcpy(&x, &b, 8); return x; }
+static const long long SIGN_ = (long long)0x8000000000000000ULL, MAG_ = 0x7fffffffffffffffLL;
+inline double abs_b(double x) { return from_bits_(bits_(x) & MAG_); }
+inline float abs_b(float x) { return std::fabs(x); }
+inline double neg_b(double x) { return from_bits_(bits_(x) ^ SIGN_); }
+inline float neg_b(float x) { return -x; }
+inline double with_sign_b(double m, double s) { return from_bits_(bits_(m) | (bits_(s) & SIGN_)); }
+inline float with_sign_b(float m, float s) { return std::copysign(m, s); }
+inline double min_nn(double a, double b) { return bits_(a) < bits_(b) ? a : b; }
+inline float min_nn(float a, float b) { return a < b ? a : b; }
+inline bool gt_nn(double a, double b) { return bits_(a) > bits_(b); }
+inline bool gt_nn(float a, float b) { return a > b; }
+inline bool same_sign(double a, double b) {
+  long long x = bits_(a), y = bits_(b);
+  return (x ^ y) >= 0 && (x & MAG_) != 0 && (y & MAG_) != 0;
+}
+inline bool same_sign(float a, float b) { return a * b > 0.f; }
+inline bool sign_bit_b(double x) { return bits_(x) < 0; }
+inline bool sign_bit_b(float x) { return std::signbit(x); }
+'''
+
+BOUNDS = {"ppm_lean_equal": 0, "ppm_stream_bits": 0, "ppm_fp32": 0, "riemann_fp64": 0, "riemann_fp32": 0,
+          "chemistry": 0, "cfl": 0}
+
+
+def _cuda_include():
+    for d in [os.environ.get("CUDA_HOME", ""), "/usr/local/cuda"]:
+        if d and os.path.exists(os.path.join(d, "include", "cuda_runtime.h")):
+            return os.path.join(d, "include")
+    return None
+
+
+@pytest.fixture(scope="module")
+def results(tmp_path_factory):
+    inc = _cuda_include()
+    if shutil.which("g++") is None or inc is None:
+        pytest.skip("needs g++ and the CUDA headers")
+    from oracle import oracle as O
+    lib = O.build()
+    src = open(HEADER).read()
+    a, b = src.index(BEGIN), src.index(END)
+    tmp = tmp_path_factory.mktemp("host_math")
+    copy = tmp / "mhd_device_host.cuh"
+    copy.write_text(src[:a] + PORTABLE + src[b + len(END):])
+    exe = tmp / "device_math_vs_oracle"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-w", f"-I{inc}",
+                    f'-DMHD_DEVICE_HOST_COPY="{copy}"', HARNESS, lib, f"-Wl,-rpath,{os.path.dirname(lib)}",
+                    "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=600).stdout
+    res = {}
+    for line in out.splitlines():
+        name, n, worst, beyond = line.split()
+        res[name] = (int(n), float(worst), int(beyond))
+    return res
+
+
+@pytest.mark.parametrize("name", sorted(BOUNDS))
+def test_device_math_matches_oracle(results, name):
+    n, worst, beyond = results[name]
+    assert n > 0
+    assert beyond == BOUNDS[name], (name, n, worst, beyond)
