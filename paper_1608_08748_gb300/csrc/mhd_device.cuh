@@ -253,12 +253,17 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
   if (gt_nn(abs_b(s0), T(0.01) * mn) && !same_sign(Dp, Dm)) {
     const T num = Dm - Dp, den = T(3) * s0;  // eta = num / den, den != 0 here
     const T num_s = sign_bit_b(den) ? neg_b(num) : num;
-    if (gt_nn(num_s, T(0.05) * abs_b(den))) {
+    const T qLp = qc - T(0.5) * h0, qRp = qc + T(0.5) * h0;
+    if (sizeof(T) == 8 && gt_nn(num_s, T(0.1) * abs_b(den))) {
+      // eta > 1/10: hbar = 1, the flattened values themselves (no FP64 division; in FP32 the
+      // division is cheaper than the branch)
+      qL = qLp;
+      qR = qRp;
+    } else if (gt_nn(num_s, T(0.05) * abs_b(den))) {
       const T eta = num / den;
       T hb = T(20) * (eta - T(0.05));
       hb = hb < T(1) ? hb : T(1);
       if (hb > T(0)) {
-        const T qLp = qc - T(0.5) * h0, qRp = qc + T(0.5) * h0;
         qL = hb * qLp + (T(1) - hb) * qL;
         qR = hb * qRp + (T(1) - hb) * qR;
       }
@@ -278,8 +283,9 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
 // discontinuities).  Written for few FP64 operations: the slopes are carried halved, the
 // differences q_{i+1} - q_{i-1} and the second differences are formed once, min(|q_{i+1}|,
 // |q_{i-1}|, |q_{i+1}| + |q_{i-1}|) is min(|q_{i+1}|, |q_{i-1}|), and eta = -(D+ - D-) / (3 dq) is
-// divided out only where it can exceed 1/20 (elsewhere hbar = 0 and Step 4 changes nothing;
-// hbar = 20 (eta - 1/20) is continuous there, so the test's rounding cannot move the result).
+// divided out only where it lies between 1/20 and 1/10 (below, hbar = 0 and Step 4 changes
+// nothing; above, hbar = 1 and the flattened values replace the edges; hbar = 20 (eta - 1/20)
+// clamped to [0, 1] is continuous at both ends, so the tests' rounding cannot move the result).
 template <typename T>
 __device__ __forceinline__ Para<T> ppm_lean(T qm2, T qm1, T qc, T qp1, T qp2) {
   const T THIRD = T(1.0 / 3.0);  // twice 1/6, exactly
@@ -456,49 +462,53 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
 #pragma unroll
   for (int m = 0; m < 6; ++m) qs[m] = T(0);
   const T TWO_THIRDS = T(2.0 / 3.0);
-  // one wave at a time, k ascending: s_k = L_k . qbar_k (qbar_k the domain-of-dependence average
-  // on the upwind side), q* += R_k s_k
-  auto magnetosonic = [&](const T L[6], const T R[6], const Para<T> P[6], T speed, bool right_moving) {
+  // s_k = L_k . qbar_k (qbar_k the domain-of-dependence average on the upwind side), q* = sum R_k s_k.
+  // The +c and -c waves of a pair share y, and their rows up to the sign S of the velocity entries:
+  // with s_+ = L . qbar_+ (left cell, right end) and s_- = (S L) . qbar_- (right cell, left end),
+  // R s_+ + (S R) s_- is R (s_+ - s_-) on v_n, v_t1, v_t2 and R (s_+ + s_-) on B_t1, B_t2, P.
+  auto magnetosonic_pair = [&](const T L[6], const T R[6], T speed) {
     const T y = speed * tau_h;
     const T hy = T(0.5) * y, w = T(1) - TWO_THIRDS * y;
-    T sa = T(0), sb = T(0);
+    T pa = T(0), pb = T(0), ma = T(0), mb = T(0);
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
-      // avg_right_end / avg_left_end of Sec. 2.4
-      const T qb = right_moving ? P[m].R - hy * (P[m].d - P[m].q6 * w)
-                                : P[m].L + hy * (P[m].d + P[m].q6 * w);
-      if (m < 3) sa = sa + L[m] * qb;
-      else sb = sb + L[m] * qb;
+      // avg_right_end of the left cell, avg_left_end of the right cell (Sec. 2.4)
+      const T qp = pl[m].R - hy * (pl[m].d - pl[m].q6 * w);
+      const T qm = pr[m].L + hy * (pr[m].d + pr[m].q6 * w);
+      if (m < 3) {
+        pa = pa + L[m] * qp;
+        ma = ma + L[m] * qm;
+      } else {
+        pb = pb + L[m] * qp;
+        mb = mb + L[m] * qm;
+      }
     }
-    const T sk = right_moving ? sa + sb : sb - sa;
+    const T sp = pa + pb, sm = mb - ma;
+    const T dif = sp - sm, sum = sp + sm;
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
-      const T Rm = (m < 3 && !right_moving) ? -R[m] : R[m];
-      qs[m] = qs[m] + Rm * sk;
-    }
+    for (int m = 0; m < 6; ++m) qs[m] = qs[m] + R[m] * (m < 3 ? dif : sum);
   };
-  auto alfven = [&](const Para<T> P[6], bool right_moving) {
+  // Alfven pair: the v_t rows are shared, the B_t rows change sign
+  auto alfven_pair = [&]() {
     const T y = ca * tau_h;
     const T hy = T(0.5) * y, w = T(1) - TWO_THIRDS * y;
-    T qb[5];
+    T qp[5], qm[5];
 #pragma unroll
-    for (int m = 1; m < 5; ++m)
-      qb[m] = right_moving ? P[m].R - hy * (P[m].d - P[m].q6 * w) : P[m].L + hy * (P[m].d + P[m].q6 * w);
-    const T sa = Av[0] * qb[1] + Av[1] * qb[2];
-    const T sb = AL[0] * qb[3] + AL[1] * qb[4];
-    const T sk = right_moving ? sa + sb : sa - sb;
-    qs[1] = qs[1] + Av[0] * sk;
-    qs[2] = qs[2] + Av[1] * sk;
-    const T sgn = right_moving ? T(1) : T(-1);
-    qs[3] = qs[3] + (sgn * AR[0]) * sk;
-    qs[4] = qs[4] + (sgn * AR[1]) * sk;
+    for (int m = 1; m < 5; ++m) {
+      qp[m] = pl[m].R - hy * (pl[m].d - pl[m].q6 * w);
+      qm[m] = pr[m].L + hy * (pr[m].d + pr[m].q6 * w);
+    }
+    const T sp = (Av[0] * qp[1] + Av[1] * qp[2]) + (AL[0] * qp[3] + AL[1] * qp[4]);
+    const T sm = (Av[0] * qm[1] + Av[1] * qm[2]) - (AL[0] * qm[3] + AL[1] * qm[4]);
+    const T sum = sp + sm, dif = sp - sm;
+    qs[1] = qs[1] + Av[0] * sum;
+    qs[2] = qs[2] + Av[1] * sum;
+    qs[3] = qs[3] + AR[0] * dif;
+    qs[4] = qs[4] + AR[1] * dif;
   };
-  magnetosonic(Lf, Rf, pl, cf, true);   // wave 1: +c_f, left cell
-  magnetosonic(Lf, Rf, pr, cf, false);  // wave 2: -c_f, right cell
-  magnetosonic(Ls, Rs, pl, cs, true);   // wave 3: +c_s
-  magnetosonic(Ls, Rs, pr, cs, false);  // wave 4: -c_s
-  alfven(pl, true);                     // wave 5: +c_a
-  alfven(pr, false);                    // wave 6: -c_a
+  magnetosonic_pair(Lf, Rf, cf);  // waves 1, 2: +-c_f
+  magnetosonic_pair(Ls, Rs, cs);  // waves 3, 4: +-c_s
+  alfven_pair();                  // waves 5, 6: +-c_a
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -6,6 +6,7 @@
 #include "mhd_runtime.cuh"
 
 namespace mhd_rt {
+template cudaError_t prepare_kernels<float>();
 template void launch_euler_stage<float>(Exec<float>&, cudaStream_t);
 template void launch_lag_stage<float>(Exec<float>&, cudaStream_t);
 template void launch_step<float>(Exec<float>&, cudaStream_t);

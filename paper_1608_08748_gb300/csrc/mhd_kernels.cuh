@@ -101,35 +101,43 @@ __global__ void __launch_bounds__(512) kb_prim(const Box<T>* __restrict__ boxes,
 }
 
 // ------------------------------------------------------------------------------------------------
-// The FP64 Eulerian pencils keep each primitive's PPMStream in this thread's slots of dynamic
-// shared memory between faces (9 values x 6 primitives; value k of primitive v at
+// Eulerian pencils that stream their parabolas (the FP64 path: its bound is FP64 instructions)
+template <typename T>
+__host__ __device__ constexpr bool euler_streams() { return sizeof(T) == 8; }
+
+// The Eulerian pencils that stream their parabolas keep each primitive's PPMStream in this thread's
+// slots of dynamic shared memory between faces (9 values x 6 primitives; value k of primitive v at
 // [(9 v + k) blockDim.x + threadIdx.x], so a warp's accesses are consecutive).
-__device__ __forceinline__ double& stream_slot(int v, int k) {
-  extern __shared__ double stream_smem[];
-  return stream_smem[(9 * v + k) * blockDim.x + threadIdx.x];
+template <typename T>
+__device__ __forceinline__ T& stream_slot(int v, int k) {
+  extern __shared__ __align__(16) unsigned char stream_smem_raw[];
+  T* sm = reinterpret_cast<T*>(stream_smem_raw);
+  return sm[(9 * v + k) * blockDim.x + threadIdx.x];
 }
-__device__ __forceinline__ void stream_save(const PPMStream<double>& S, int v) {
-  stream_slot(v, 0) = S.qm;
-  stream_slot(v, 1) = S.q0;
-  stream_slot(v, 2) = S.qp;
-  stream_slot(v, 3) = S.dp;
-  stream_slot(v, 4) = S.h0;
-  stream_slot(v, 5) = S.eL;
-  stream_slot(v, 6) = S.Cm;
-  stream_slot(v, 7) = S.C0;
-  stream_slot(v, 8) = S.s0;
+template <typename T>
+__device__ __forceinline__ void stream_save(const PPMStream<T>& S, int v) {
+  stream_slot<T>(v, 0) = S.qm;
+  stream_slot<T>(v, 1) = S.q0;
+  stream_slot<T>(v, 2) = S.qp;
+  stream_slot<T>(v, 3) = S.dp;
+  stream_slot<T>(v, 4) = S.h0;
+  stream_slot<T>(v, 5) = S.eL;
+  stream_slot<T>(v, 6) = S.Cm;
+  stream_slot<T>(v, 7) = S.C0;
+  stream_slot<T>(v, 8) = S.s0;
 }
-__device__ __forceinline__ PPMStream<double> stream_load(int v) {
-  PPMStream<double> S;
-  S.qm = stream_slot(v, 0);
-  S.q0 = stream_slot(v, 1);
-  S.qp = stream_slot(v, 2);
-  S.dp = stream_slot(v, 3);
-  S.h0 = stream_slot(v, 4);
-  S.eL = stream_slot(v, 5);
-  S.Cm = stream_slot(v, 6);
-  S.C0 = stream_slot(v, 7);
-  S.s0 = stream_slot(v, 8);
+template <typename T>
+__device__ __forceinline__ PPMStream<T> stream_load(int v) {
+  PPMStream<T> S;
+  S.qm = stream_slot<T>(v, 0);
+  S.q0 = stream_slot<T>(v, 1);
+  S.qp = stream_slot<T>(v, 2);
+  S.dp = stream_slot<T>(v, 3);
+  S.h0 = stream_slot<T>(v, 4);
+  S.eL = stream_slot<T>(v, 5);
+  S.Cm = stream_slot<T>(v, 6);
+  S.C0 = stream_slot<T>(v, 7);
+  S.s0 = stream_slot<T>(v, 8);
   return S;
 }
 
@@ -161,10 +169,10 @@ __device__ __forceinline__ void euler_pencil(const Box<T>& B, idx_t p) {
     idx_t cell[5];
 #pragma unroll
     for (int o = 0; o < 5; ++o) cell[o] = cell_at(f0 - 3 + o);
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (euler_streams<T>()) {
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
-        PPMStream<double> S;
+        PPMStream<T> S;
         S.prime(qv[v][cell[0]], qv[v][cell[1]], qv[v][cell[2]], qv[v][cell[3]]);
         pl[v] = S.next(qv[v][cell[4]]);  // cell f0 - 1
         stream_save(S, v);
@@ -179,10 +187,10 @@ __device__ __forceinline__ void euler_pencil(const Box<T>& B, idx_t p) {
     idx_t cell[5];
 #pragma unroll
     for (int o = 0; o < 5; ++o) cell[o] = cell_at(i - 2 + o);
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (euler_streams<T>()) {
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
-        PPMStream<double> S = stream_load(v);
+        PPMStream<T> S = stream_load<T>(v);
         pr[v] = S.next(qv[v][cell[4]]);  // cell i
         stream_save(S, v);
       }

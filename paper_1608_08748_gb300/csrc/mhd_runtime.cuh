@@ -33,9 +33,9 @@ inline int report_class(int tag) { return tag >= PROF_KC_BASE ? profile_class(ta
 template <typename T>
 constexpr bool lag_in_pencils() { return sizeof(T) == 8; }
 
-// shared memory per thread of the Eulerian pencils: the FP64 path keeps six PPMStreams there
+// shared memory per thread of the Eulerian pencils: six PPMStreams where they stream
 template <typename T>
-constexpr size_t euler_pencil_smem() { return sizeof(T) == 8 ? 6 * 9 * sizeof(double) : 0; }
+constexpr size_t euler_pencil_smem() { return euler_streams<T>() ? 6 * 9 * sizeof(T) : 0; }
 
 template <typename T>
 inline int class_domain(int kc) {
@@ -171,6 +171,24 @@ void default_cfgs(Exec<T>& X) {
   X.cfg[KC_LFACE].block = 128;
 }
 
+// Kernel attributes of the current device: dynamic shared memory above the 48 KB default for the
+// Eulerian pencils that stream their parabolas (up to 256 threads per block).  A kernel template
+// instantiated in two translation units is two kernels, so this is instantiated where the launches
+// of T are (the float launchers live in their own translation unit).
+template <typename T>
+cudaError_t prepare_kernels() {
+  if constexpr (euler_pencil_smem<T>() > 0) {
+    const int bytes = (int)(256 * euler_pencil_smem<T>());
+    cudaError_t e = cudaFuncSetAttribute(kb_euler_pencil<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kb_euler_pencil<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kb_euler_pencil<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+  }
+  return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t exec_init(Exec<T>& X, const std::vector<Box<T>>& boxes) {
   X.h = boxes;
@@ -178,14 +196,10 @@ cudaError_t exec_init(Exec<T>& X, const std::vector<Box<T>>& boxes) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&X.nsm, cudaDevAttrMultiProcessorCount, dev);
-  if constexpr (euler_pencil_smem<T>() > 0) {  // up to 256 threads per block
-    const int bytes = (int)(256 * euler_pencil_smem<T>());
-    cudaFuncSetAttribute(kb_euler_pencil<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(kb_euler_pencil<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(kb_euler_pencil<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  }
+  cudaError_t e = prepare_kernels<T>();
+  if (e != cudaSuccess) return e;
   default_cfgs(X);
-  cudaError_t e = cudaMalloc(&X.d, sizeof(Box<T>) * (size_t)X.nb);
+  e = cudaMalloc(&X.d, sizeof(Box<T>) * (size_t)X.nb);
   if (e != cudaSuccess) return e;
   e = cudaMemcpy(X.d, X.h.data(), sizeof(Box<T>) * (size_t)X.nb, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
@@ -376,6 +390,7 @@ cudaError_t diag_partial(mhd_sim* S, Box<T>& B) {
 
 // The FP32 instances live in mhd_f32.cu.
 #ifndef MHD_RT_F32_TU
+extern template cudaError_t prepare_kernels<float>();
 extern template void launch_euler_stage<float>(Exec<float>&, cudaStream_t);
 extern template void launch_lag_stage<float>(Exec<float>&, cudaStream_t);
 extern template void launch_step<float>(Exec<float>&, cudaStream_t);
