@@ -211,6 +211,26 @@ def fp32_leg(M, I, torch, n=256, steps=10, warm=3, err_steps=5):
             "kernels": {k: v["ms_total"] / 2 for k, v in prof.items()}}
 
 
+def heatcool_leg(M, I, torch, n=128, steps=10, warm=3):
+    """The heating/cooling stage (Sec. 2.8) on the FP64 128^3 turbulence box with 5 % of the
+    hydrogen molecular: Mcell-updates/s with the stage on and off, and the post kernel (chemistry,
+    heating/cooling, regularisation, CFL) per step."""
+    ic = I.turbulence(n, mach=5.0, beta=1.0, seed=1)
+    ic["rho_h2"] = 0.05 * ic["rho"]
+    out = {"workload": f"mhd_turbulence_h2chem_heatcool_{n}^3_fp64", "unit": METRIC, "steps": steps,
+           "warmup": warm}
+    for on in (1, 0):
+        s = M.from_ic(ic, heatcool=on)
+        ms = timed_steps(torch, s, steps, warm)
+        prof = M.profile(s, CFL, 2)
+        key = "on" if on else "off"
+        out[key] = {"value": n ** 3 * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+                    "post_ms_per_step": prof["post"]["ms_total"] / 2}
+        del s
+    out["value"] = out["on"]["value"]
+    return out
+
+
 def batched_leg(M, I, torch, steps=20, warm=3):
     """Config 4: 64 turbulence boxes, axes from {16..96}, FP32 bulk, one launch per kernel class
     per step (CUDA graph), launch shapes autotuned first."""
@@ -290,7 +310,7 @@ def run_leg(args):
     B.build()
     import paper_1608_08748_gb300 as M
     from paper_1608_08748_gb300 import inputs as I
-    fn = {"fp32": fp32_leg, "batched": batched_leg, "serving": serving_leg}[args.leg]
+    fn = {"fp32": fp32_leg, "batched": batched_leg, "serving": serving_leg, "heatcool": heatcool_leg}[args.leg]
     print(json.dumps({args.leg: fn(M, I, torch)}), flush=True)
 
 
@@ -395,6 +415,7 @@ def run_ours(args):
         extras["fp32_bulk"] = fp32_leg(M, I, torch)
         extras["batched"] = batched_leg(M, I, torch)
         extras["serving"] = serving_leg(M, I, torch, big=args.serving_big)
+        extras["heatcool"] = heatcool_leg(M, I, torch)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, secs = oracle_rate(48, 8)
@@ -426,8 +447,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the FP32-bulk (256^3), batched-ensemble and serving legs")
-    ap.add_argument("--leg", choices=["main", "fp32", "batched", "serving"], default="main",
+                    help="skip the FP32-bulk (256^3), batched-ensemble, serving and heating/cooling legs")
+    ap.add_argument("--leg", choices=["main", "fp32", "batched", "serving", "heatcool"], default="main",
                     help="run one secondary leg alone (for profiling)")
     ap.add_argument("--serving-big", action="store_true",
                     help="include the 512^3 request class (probability 0.005) in the serving leg")

@@ -64,7 +64,11 @@ enum mhd_option {
   MHD_OPT_CHEM_BDOP = 9,     /* Doppler parameter b of f_shield in km/s (default 3) */
   MHD_OPT_CHEM_XNORM = 10,   /* N_H2 normaliser of f_shield in cm^-2 (default 5e14) */
   MHD_OPT_CHEM_TAUD = 11,    /* dust optical depth per unit column, cm^2 (default 1e-21) */
-  MHD_OPT_GRAPH = 14         /* 1 (default): replay each step from a captured CUDA graph; 0: launch */
+  MHD_OPT_GRAPH = 14,        /* 1 (default): replay each step from a captured CUDA graph; 0: launch */
+  MHD_OPT_HEATCOOL = 15      /* 0 off (default); 1 the Sec. 2.8 heating/cooling stage after the
+                                chemistry (needs MHD_OPT_CHEM = 1): rho E and rho eps change by
+                                tau (Gamma_1 + Gamma_4 - Lambda_2 - Lambda_3) of App. D, FP64, the
+                                change limited to at most half of rho eps */
 };
 
 enum mhd_dtype { MHD_F64 = 0, MHD_F32 = 1 };
@@ -130,7 +134,7 @@ int mhd_sync(mhd_sim* s);
 int mhd_diagnostics(mhd_sim* s, mhd_diag* out);
 
 /* One stage alone with a given tau (per-stage parity checks): 1 Eulerian + Flux-CT, 2 Lagrangian,
-   3 chemistry, 4 regularisation. */
+   3 chemistry, 4 regularisation, 5 heating/cooling (with MHD_OPT_HEATCOOL on). */
 int mhd_stage(mhd_sim* s, int which, double tau);
 
 /* Kernel classes reported by mhd_profile (index into its output arrays). */

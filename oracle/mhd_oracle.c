@@ -71,7 +71,8 @@ enum {
   O_CHEM_BDOP = 9,                    /* Doppler parameter b in km/s */
   O_CHEM_XNORM = 10,                  /* N_H2 normaliser of f_shield, cm^-2 */
   O_CHEM_TAUD = 11,                   /* dust optical depth per column, cm^2 */
-  O_THREADS = 12
+  O_THREADS = 12,
+  O_HEATCOOL = 13                     /* 0 off (default), 1 Sec. 2.8 heating/cooling (needs chemistry) */
 };
 
 enum { O_OK = 0, O_EINVAL = -1, O_ENOMEM = -2, O_ENONPHYS = -4 };
@@ -81,6 +82,7 @@ static const double KB_CGS = 1.380649e-16;
 static const double MH_CGS = 1.6735575e-24;
 static const double PC_CGS = 3.0856775814913673e18;
 static const double KMS_CGS = 1.0e5;
+static const double KB_EV = 8.617333262e-5; /* Boltzmann constant in eV/K (A27) */
 
 typedef struct {
   int n[3];   /* nx, ny, nz */
@@ -88,7 +90,7 @@ typedef struct {
   size_t next; /* extended cell count */
   int bc[3];
   double gamma, dx;
-  int chem, step4_as_written, iface_edge, regul_mode, threads;
+  int chem, step4_as_written, iface_edge, regul_mode, threads, heatcool;
   double lshield, bdop, xnorm, taud;
   double t;
   long nsteps, nvel_branch;
@@ -457,6 +459,7 @@ int osim_set_option(osim* s, int key, double v) {
     case O_CHEM_XNORM: if (!(v > 0.0)) return O_EINVAL; s->xnorm = v; return O_OK;
     case O_CHEM_TAUD: if (v < 0.0) return O_EINVAL; s->taud = v; return O_OK;
     case O_THREADS: if (v < 1.0) return O_EINVAL; s->threads = (int)v; return O_OK;
+    case O_HEATCOOL: if (v != 0.0 && v != 1.0) return O_EINVAL; s->heatcool = (int)v; return O_OK;
     default: return O_EINVAL;
   }
 }
@@ -887,6 +890,81 @@ static void chemistry(osim* s, double tau) {
       }
 }
 
+/* ---------------------------------------------------------------- Sec. 2.8 + App. D heating/cooling */
+/* Heating and cooling of the H/H2 gas, erg cm^-3 s^-1, at the state (rho, rho eps, rho_H2) in code
+   units (readings A24-A29):
+   - T from the composition as in the chemistry (n_H = rho - rho_H2, n_H2 = rho_H2 / 2, n = rho);
+   - Gamma_1 = 7.2e-12 erg x (k1' n n_H) / (1 + n_cr / n), n_cr = 10^(4 - 0.416 x - 0.327 x^2): the
+     H2 formation heating, the printed numerator read as the formation rate of reaction 1 and the
+     printed polynomial over n as the critical density (A25);
+   - Lambda_2 = n_H2 L_H / (1 + L_H / L_L) with the two-branch L_H and L_L as printed (A26);
+   - Lambda_3 = n_H2 L_H / (1 + L_H / L_L), L_H = 1.1e-13 exp(-6744 / T),
+     L_L = 8.18e-13 (n_H k_H + n_H2 k_H2), k_H2 = 6.29e-15 x 1.38 f(T) / f(4500),
+     f(T) = sqrt(T) a exp(a), a = 1 + 1 / (k_B T) with k_B in eV/K, and k_H = k_H2 (A27);
+   - Gamma_4 = 6.4e-13 erg x k4 n_H2 (A28);
+   x = log10(T / 1e4) throughout (A15 iv). */
+typedef struct { double T, G1, L2, L3, G4, net; } heatcool_terms;
+
+static double log_f_A27(double T) {
+  double a = 1.0 + 1.0 / (KB_EV * T);
+  return 0.5 * log(T) + log(a) + a;
+}
+
+static heatcool_terms heatcool_at(const osim* s, double rho, double eint, double rh2) {
+  const double P0 = MH_CGS * KMS_CGS * KMS_CGS;
+  double nH = rho - rh2, nH2 = 0.5 * rh2, n = rho;
+  double g = gamma_eff(rho, rh2);
+  double p = (g - 1.0) * eint * P0;
+  double T = p / ((nH + nH2) * KB_CGS);
+  chem_rates r = chem_rates_at(s, T, nH, nH2, n);
+  double x = log10(T / 1e4);
+  heatcool_terms h;
+  h.T = T;
+  /* Gamma_1 (A25) */
+  double ncr = pow(10.0, 4.0 - 0.416 * x - 0.327 * x * x);
+  h.G1 = 7.2e-12 * r.C / (1.0 + ncr / n);
+  /* Lambda_2 (A26) */
+  double LH2 = T > 1087.0 ? 3.9e-19 * exp(-6118.0 / T) : pow(10.0, -19.24 + 0.474 * x - 1.247 * x * x);
+  double LL2 = (pow(nH2, 0.77) + 1.2 * pow(nH, 0.77)) *
+               (T > 4031.0 ? 1.38e-22 * exp(-9243.0 / T) : pow(10.0, -22.9 - 0.553 * x - 1.148 * x * x));
+  h.L2 = nH2 * LH2 / (1.0 + LH2 / LL2);
+  /* Lambda_3 (A27) */
+  double LH3 = 1.1e-13 * exp(-6744.0 / T);
+  double kH2 = 6.29e-15 * 1.38 * exp(log_f_A27(T) - log_f_A27(4500.0));
+  double LL3 = 8.18e-13 * (nH * kH2 + nH2 * kH2);
+  h.L3 = nH2 * LH3 / (1.0 + LH3 / LL3);
+  /* Gamma_4 (A28) */
+  h.G4 = 6.4e-13 * r.k4 * nH2;
+  h.net = (h.G1 + h.G4) - (h.L2 + h.L3);
+  return h;
+}
+
+/* Sec. 2.8: d(rho E)/dt = d(rho eps)/dt = Gamma - Lambda by one Euler step; returns the change of
+   rho E and rho eps in code units, limited so that rho eps keeps at least half its value (A29) */
+static double heatcool_delta(const osim* s, double rho, double eint, double rh2, double tau,
+                             heatcool_terms* out) {
+  const double P0 = MH_CGS * KMS_CGS * KMS_CGS; /* code energy density unit, erg cm^-3 */
+  const double T0 = PC_CGS / KMS_CGS;           /* code time unit, s */
+  heatcool_terms h = heatcool_at(s, rho, eint, rh2);
+  double d = tau * T0 * h.net / P0;
+  if (d < -0.5 * eint) d = -0.5 * eint;
+  if (out) *out = h;
+  return d;
+}
+
+static void heatcool(osim* s, double tau) {
+  const int* n = s->n;
+#pragma omp parallel for schedule(static) num_threads(s->threads)
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        size_t c = IX(s, i + NG, j + NG, k + NG);
+        double d = heatcool_delta(s, s->rho[c], s->eint[c], s->rh2[c], tau, NULL);
+        s->E[c] = s->E[c] + d;
+        s->eint[c] = s->eint[c] + d;
+      }
+}
+
 /* ---------------------------------------------------------------- Sec. 2.9 regularisation */
 static long regularise(osim* s) {
   const int* n = s->n;
@@ -981,19 +1059,21 @@ static int check_physical(osim* s) {
 }
 
 /* run one stage alone (debugging and per-stage parity): 1 Eulerian, 2 Lagrangian,
-   3 chemistry, 4 regularisation */
+   3 chemistry, 4 regularisation, 5 heating/cooling */
 int osim_stage(osim* s, int which, double tau) {
   switch (which) {
     case 1: eulerian_stage(s, tau); break;
     case 2: lagrangian_stage(s, tau); break;
     case 3: if (s->chem) chemistry(s, tau); break;
     case 4: s->nvel_branch += regularise(s); break;
+    case 5: if (s->chem && s->heatcool) heatcool(s, tau); break;
     default: return O_EINVAL;
   }
   return check_physical(s);
 }
 
-/* one full step (Sec. 2 stage order, stages 1-4 and 6); t_end > 0 truncates tau (A18) */
+/* one full step (Sec. 2 stage order, stages 1-6 without gravity; stage 5 only with the option on);
+   t_end > 0 truncates tau (A18) */
 int osim_step(osim* s, double cfl, double t_end, double* dt) {
   double tau = osim_tau(s, cfl);
   if (t_end > 0.0 && tau > t_end - s->t) tau = t_end - s->t;
@@ -1001,6 +1081,7 @@ int osim_step(osim* s, double cfl, double t_end, double* dt) {
   eulerian_stage(s, tau);
   lagrangian_stage(s, tau);
   if (s->chem) chemistry(s, tau);
+  if (s->chem && s->heatcool) heatcool(s, tau);
   s->nvel_branch += regularise(s);
   s->t += tau;
   s->nsteps += 1;
@@ -1119,6 +1200,19 @@ void osim_chem_cell(const osim* s, double rho, double eint, double rh2, double t
   out[5] = r.k4;
   out[6] = r.C;
   out[7] = r.D;
+}
+
+/* heating/cooling of one cell with the simulation's parameters:
+   out = (change of rho E and rho eps in code units, T, Gamma_1, Lambda_2, Lambda_3, Gamma_4, net) */
+void osim_heatcool_cell(const osim* s, double rho, double eint, double rh2, double tau, double out[7]) {
+  heatcool_terms h;
+  out[0] = heatcool_delta(s, rho, eint, rh2, tau, &h);
+  out[1] = h.T;
+  out[2] = h.G1;
+  out[3] = h.L2;
+  out[4] = h.L3;
+  out[5] = h.G4;
+  out[6] = h.net;
 }
 
 /* App. D rates at a given temperature and composition (for the rate pins) */

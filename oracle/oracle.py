@@ -26,7 +26,7 @@ _lib = None
 OPT = {
     "bc_x": 1, "bc_y": 2, "bc_z": 3, "chem": 4, "step4_as_written": 5, "iface_edge": 6,
     "regul_mode": 7, "chem_lshield": 8, "chem_bdop": 9, "chem_xnorm": 10, "chem_taud": 11,
-    "threads": 12,
+    "threads": 12, "heatcool": 13,
 }
 OK, EINVAL, ENOMEM, ENONPHYS = 0, -1, -2, -4
 
@@ -80,6 +80,7 @@ def lib():
         L.o_gamma_eff.restype = d
         L.o_gamma_eff.argtypes = [d, d]
         L.osim_chem_cell.argtypes = [vp, d, d, d, d, _dp]
+        L.osim_heatcool_cell.argtypes = [vp, d, d, d, d, _dp]
         L.osim_chem_rates.argtypes = [vp, d, d, d, _dp]
         _lib = L
     return _lib
@@ -179,6 +180,13 @@ class Sim:
         out = np.zeros(8)
         self.L.osim_chem_cell(self.h, float(rho), float(eint), float(rh2), float(tau), out)
         return dict(zip(["rho_h2", "T", "k1p", "k2", "k3", "k4", "C", "D"], out))
+
+    def heatcool_cell(self, rho, eint, rh2, tau):
+        """Sec. 2.8 heating/cooling of one cell: the change of rho E and rho eps (code units) and the
+        terms in erg cm^-3 s^-1."""
+        out = np.zeros(7)
+        self.L.osim_heatcool_cell(self.h, float(rho), float(eint), float(rh2), float(tau), out)
+        return dict(zip(["delta", "T", "G1", "L2", "L3", "G4", "net"], out))
 
     def chem_rates(self, T, nH, nH2):
         out = np.zeros(7)

@@ -241,6 +241,7 @@ mhd_sim* mhd_create(int nx, int ny, int nz, double gamma, double dx) {
   S->ph.ibdop = 1.0 / 3.0;
   S->ph.ixnorm = 1.0 / 5e14;
   S->ph.taud = 1e-21;
+  S->ph.heatcool = 0;
   auto bail = [&](const char* what, cudaError_t e) {
     fail(e == cudaErrorMemoryAllocation ? MHD_ENOMEM : MHD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     mhd_destroy(S);
@@ -332,6 +333,10 @@ int mhd_set_option(mhd_sim* S, int key, double v) {
       break;
     case MHD_OPT_GRAPH:
       S->use_graph = v != 0.0;
+      break;
+    case MHD_OPT_HEATCOOL:
+      if (v != 0.0 && v != 1.0) return fail(MHD_EINVAL, "heating/cooling must be 0 (off) or 1 (on)");
+      S->ph.heatcool = (int)v;
       break;
     default:
       return fail(MHD_EINVAL, "unknown option key " + std::to_string(key));
@@ -533,7 +538,8 @@ int mhd_sync(mhd_sim* S) {
 
 int mhd_stage(mhd_sim* S, int which, double tau) {
   if (!valid(S)) return fail(MHD_EINVAL, "mhd_stage: null sim");
-  if (which < 1 || which > 4 || !(tau > 0.0)) return fail(MHD_EINVAL, "mhd_stage: which in 1..4, tau > 0");
+  if (which < 1 || which > 5 || !(tau > 0.0)) return fail(MHD_EINVAL, "mhd_stage: which in 1..5, tau > 0");
+  const int cell_stages = which == 3 ? 1 : (which == 5 ? 2 : 0);
   int rc;
   if ((rc = set_params(S, 1.0, 0.0, 1, tau)) != MHD_OK) return rc;
   S->params_dirty = true;
@@ -541,12 +547,12 @@ int mhd_stage(mhd_sim* S, int which, double tau) {
     launch_small(S->x32, S->stream, 0);
     if (which == 1) launch_euler_stage(S->x32, S->stream);
     if (which == 2) launch_lag_stage(S->x32, S->stream);
-    if (which >= 3) launch_post(S->x32, S->stream, which == 3, which == 4, 1);
+    if (which >= 3) launch_post(S->x32, S->stream, cell_stages, which == 4, 1);
   } else {
     launch_small(S->x64, S->stream, 0);
     if (which == 1) launch_euler_stage(S->x64, S->stream);
     if (which == 2) launch_lag_stage(S->x64, S->stream);
-    if (which >= 3) launch_post(S->x64, S->stream, which == 3, which == 4, 1);
+    if (which >= 3) launch_post(S->x64, S->stream, cell_stages, which == 4, 1);
   }
   CK(cudaGetLastError());
   if ((rc = refresh_cfl(S)) != MHD_OK) return rc;

@@ -31,6 +31,7 @@ struct Phys {
   double lshield;    // shielding length, code units
   double bdop, xnorm, taud;
   double ibdop, ixnorm;  // 1 / bdop, 1 / xnorm
+  int heatcool;          // Sec. 2.8 heating/cooling stage on (needs chem)
 };
 
 // Device-resident scalars of a simulation: tau never crosses to the host inside a step.
@@ -587,6 +588,62 @@ __device__ __forceinline__ double chem_cell(const Phys& ph, double rho, double e
   if (nH2n < 0.0) nH2n = 0.0;
   if (nH2n > 0.5 * n) nH2n = 0.5 * n;
   return 2.0 * nH2n;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Sec. 2.8 + App. D: heating and cooling of one cell, d(rho E)/dt = d(rho eps)/dt = Gamma - Lambda by
+// one Euler step; returns the change of rho E and rho eps in code units.  FP64.  Readings:
+//   Gamma_1 = 7.2e-12 erg (k1' n n_H) / (1 + n_cr / n), n_cr = 10^(4 - 0.416 x - 0.327 x^2) (the H2
+//     formation heating: the printed numerator read as the formation rate, the printed polynomial
+//     over n as the critical density);
+//   Lambda_2 = n_H2 L_H / (1 + L_H / L_L) with the printed two-branch L_H, L_L;
+//   Lambda_3 = n_H2 L_H / (1 + L_H / L_L), L_H = 1.1e-13 exp(-6744 / T),
+//     L_L = 8.18e-13 (n_H + n_H2) k_H2 (k_H, undefined in the paper, read as k_H2),
+//     k_H2 = 6.29e-15 1.38 f(T) / f(4500), f(T) = sqrt(T) a e^a, a = 1 + 1 / (k_B T), k_B in eV/K;
+//   Gamma_4 = 6.4e-13 erg k4 n_H2;
+//   x = log10(T / 1e4); T, k1' and k4 as in chem_cell, from the state after the chemistry update;
+//   the change is limited to at most half of rho eps (the explicit step of a cooling time shorter
+//   than tau would drive rho eps negative).
+__device__ __forceinline__ double heatcool_delta(const Phys& ph, double rho, double eint, double rh2,
+                                                 double tau) {
+  const double P0 = ChemConst::MH * ChemConst::KMS * ChemConst::KMS;  // erg cm^-3
+  const double T0 = ChemConst::PC / ChemConst::KMS;                  // s
+  const double KB_EV = 8.617333262e-5;                               // eV / K
+  const double nH = rho - rh2, nH2 = 0.5 * rh2, n = rho;
+  const double T = ((2.0 * P0) * eint) / ((3.0 * nH + 5.0 * nH2) * ChemConst::KB);
+  const double x = log10(T * 1e-4);
+  // k1' and k4 (App. D, as in chem_cell)
+  const double t2 = T * 0.01, s2 = sqrt(t2);
+  const double k1p = 3e-17 * s2 / (((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2));
+  const double Ls = (ph.lshield > 0.0 ? ph.lshield : ph.dx) * ChemConst::PC;
+  const double NH = nH * Ls, NH2 = nH2 * Ls;
+  const double fdust = exp(-(ph.taud * (NH + NH2)));
+  const double xs = NH2 * ph.ixnorm;
+  const double u = 1.0 + xs * ph.ibdop;
+  const double isx = rsqrt(1.0 + xs);
+  const double fsh = 0.965 / (u * u) + (0.035 * isx) * exp(-8.5e-4 * ((1.0 + xs) * isx));
+  const double k4 = (3.3 * 1.7e-11) * fsh * fdust;
+  // Gamma_1
+  const double ncr = exp10(4.0 - 0.416 * x - 0.327 * x * x);
+  const double G1 = 7.2e-12 * (k1p * n * nH) / (1.0 + ncr / n);
+  // Lambda_2
+  const double LH2 = T > 1087.0 ? 3.9e-19 * exp(-6118.0 / T) : exp10(-19.24 + 0.474 * x - 1.247 * x * x);
+  const double LL2 = (pow(nH2, 0.77) + 1.2 * pow(nH, 0.77)) *
+                     (T > 4031.0 ? 1.38e-22 * exp(-9243.0 / T) : exp10(-22.9 - 0.553 * x - 1.148 * x * x));
+  const double L2 = nH2 * LH2 / (1.0 + LH2 / LL2);
+  // Lambda_3
+  const double LH3 = 1.1e-13 * exp(-6744.0 / T);
+  const double a = 1.0 + 1.0 / (KB_EV * T), a0 = 1.0 + 1.0 / (KB_EV * 4500.0);
+  const double lnf = (0.5 * log(T) + log(a)) + a, lnf0 = (0.5 * log(4500.0) + log(a0)) + a0;
+  const double kH2 = (6.29e-15 * 1.38) * exp(lnf - lnf0);
+  const double LL3 = 8.18e-13 * ((nH + nH2) * kH2);
+  const double L3 = nH2 * LH3 / (1.0 + LH3 / LL3);
+  // Gamma_4
+  const double G4 = 6.4e-13 * k4 * nH2;
+  const double net = (G1 + G4) - (L2 + L3);
+  double d = (tau * T0) * net / P0;
+  if (d < -0.5 * eint) d = -0.5 * eint;
+  return d;
 }
 
 }  // namespace mhd

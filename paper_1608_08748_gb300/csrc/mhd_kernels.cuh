@@ -506,12 +506,14 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// Per cell, after the Lagrangian stage: chemistry (Sec. 2.7, FP64), regularisation (Sec. 2.9),
-// the non-physical check, and the CFL denominator of the new state for the next tau (Sec. 2.3).
-// do_chem / do_reg select the stages (the full step runs both); do_chem = do_reg = 0 computes
-// only the CFL denominator.  Returns the flags via the warp-aggregated atomics of the caller.
+// Per cell, after the Lagrangian stage: chemistry (Sec. 2.7, FP64), heating/cooling (Sec. 2.8,
+// FP64, when on), regularisation (Sec. 2.9), the non-physical check, and the CFL denominator of the
+// new state for the next tau (Sec. 2.3).  cell_stages selects the per-cell stages (bit 0
+// chemistry, bit 1 heating/cooling; the full step runs both), do_reg the regularisation;
+// cell_stages = do_reg = 0 computes only the CFL denominator.  Returns the flags via the
+// warp-aggregated atomics of the caller.
 template <typename T>
-__device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, int do_chem, int do_reg,
+__device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, int cell_stages, int do_reg,
                                           double& D, int& bad, unsigned& vb) {
   const Geom& g = B.g;
   const Phys& ph = B.ph;
@@ -519,8 +521,13 @@ __device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, int do_chem,
   int q[3];
   decode(c, g.n[0], g.n[1], q);
   const double tau = B.sc->tau;
-  if (do_chem && ph.chem)
+  if ((cell_stages & 1) && ph.chem)
     s.rh2[c] = (T)chem_cell(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c], tau);
+  if ((cell_stages & 2) && ph.chem && ph.heatcool) {
+    const double d = heatcool_delta(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c], tau);
+    s.E[c] = (T)((double)s.E[c] + d);
+    s.eint[c] = (T)((double)s.eint[c] + d);
+  }
   idx_t up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
   T Bc[3];
 #pragma unroll
@@ -566,7 +573,7 @@ __device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, int do_chem,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) kb_post(const Box<T>* __restrict__ boxes, Tiles tl, int do_chem,
+__global__ void __launch_bounds__(512) kb_post(const Box<T>* __restrict__ boxes, Tiles tl, int cell_stages,
                                                int do_reg, int check) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
@@ -574,7 +581,7 @@ __global__ void __launch_bounds__(512) kb_post(const Box<T>* __restrict__ boxes,
     double D = 0.0;
     int bad = 0;
     unsigned vb = 0;
-    if (c < B.g.N) post_cell(B, c, do_chem, do_reg, D, bad, vb);
+    if (c < B.g.N) post_cell(B, c, cell_stages, do_reg, D, bad, vb);
     if (!check) bad = 0;
     D = warp_max(D);
     int anybad = __any_sync(0xffffffffu, bad);

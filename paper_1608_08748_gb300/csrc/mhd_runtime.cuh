@@ -274,11 +274,11 @@ void launch_lag_stage(Exec<T>& X, cudaStream_t st) {
   }
 }
 
-// chemistry / regularisation / check / CFL of the new state (do_chem = do_reg = check = 0: only
-// the CFL denominator)
+// per-cell stages (bit 0 chemistry, bit 1 heating/cooling) / regularisation / check / CFL of the
+// new state (cell_stages = do_reg = check = 0: only the CFL denominator)
 template <typename T>
-void launch_post(Exec<T>& X, cudaStream_t st, int do_chem, int do_reg, int check) {
-  launch_k(X, st, KC_POST, DOM_CELLS, kb_post<T>, do_chem, do_reg, check);
+void launch_post(Exec<T>& X, cudaStream_t st, int cell_stages, int do_reg, int check) {
+  launch_k(X, st, KC_POST, DOM_CELLS, kb_post<T>, cell_stages, do_reg, check);
 }
 
 template <typename T>
@@ -286,7 +286,7 @@ void launch_step(Exec<T>& X, cudaStream_t st) {
   launch_small(X, st, 0);
   launch_euler_stage(X, st);
   launch_lag_stage(X, st);
-  launch_post(X, st, 1, 1, 1);
+  launch_post(X, st, 3, 1, 1);
   launch_small(X, st, 1);
 }
 

@@ -15,7 +15,8 @@ import numpy as np
 from . import build as _build
 
 OPT = {"bc_x": 1, "bc_y": 2, "bc_z": 3, "chem": 4, "precision": 5, "regul_mode": 7,
-       "chem_lshield": 8, "chem_bdop": 9, "chem_xnorm": 10, "chem_taud": 11, "graph": 14}
+       "chem_lshield": 8, "chem_bdop": 9, "chem_xnorm": 10, "chem_taud": 11, "graph": 14,
+       "heatcool": 15}
 STATUS = {0: "MHD_OK", 1: "MHD_PENDING", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA",
           -4: "MHD_ENONPHYS", -5: "MHD_ETIMEOUT", -6: "MHD_ENOTFOUND", -7: "MHD_ECAPACITY"}
 F64, F32 = 0, 1

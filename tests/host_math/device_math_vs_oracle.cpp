@@ -18,6 +18,8 @@ struct osim;
 osim* osim_create(int nx, int ny, int nz, double gamma, double dx);
 void osim_destroy(osim* s);
 void osim_chem_cell(const osim* s, double rho, double eint, double rh2, double tau, double out[8]);
+void osim_heatcool_cell(const osim* s, double rho, double eint, double rh2, double tau, double out[7]);
+int osim_set_option(osim* s, int key, double v);
 void o_ppm(const double q[5], int step4_as_written, double out[4]);
 void o_face_solve(const double wl[5], const double wr[5], double Bn, const double sl[30], const double sr[30],
                   double tau_h, int edge, int step4_as_written, double out[6]);
@@ -195,6 +197,7 @@ int main() {
     ph.taud = 1e-21;
     ph.ibdop = 1.0 / ph.bdop;
     ph.ixnorm = 1.0 / ph.xnorm;
+    ph.heatcool = 1;
     const long n = 300000;
     long bad = 0;
     double worst = 0;
@@ -210,8 +213,28 @@ int main() {
       worst = std::max(worst, e);
       if (e > 1e-12) ++bad;
     }
-    osim_destroy(s);
     report("chemistry", n, worst, bad);
+    // 5b. heating/cooling of one cell (FP64, Sec. 2.8) against the oracle's
+    osim_set_option(s, 13, 1.0);
+    long badh = 0;
+    double worsth = 0;
+    for (long it = 0; it < n; ++it) {
+      const double rho = std::exp(12 * U01(g) - 4);
+      const double rh2 = rho * U01(g) * (it % 3 ? 1.0 : 1e-6) * (it % 11 == 0 ? 0.0 : 1.0);
+      const double eint = rho * std::exp(14 * U01(g) - 8);
+      const double tau = std::exp(10 * U01(g) - 12);
+      double o[7];
+      osim_heatcool_cell(s, rho, eint, rh2, tau, o);
+      const double a = heatcool_delta(ph, rho, eint, rh2, tau);
+      // relative to the gross exchange tau (Gamma_1 + Gamma_4 + Lambda_2 + Lambda_3) in code units:
+      // the net change cancels near equilibrium
+      const double gross = tau * (3.0856775814913673e18 / 1e5) * (o[2] + o[3] + o[4] + o[5]) / (1.6735575e-24 * 1e10);
+      const double e = std::fabs(a - o[0]) / std::max(std::max(std::fabs(o[0]), gross), 1e-300);
+      worsth = std::max(worsth, e);
+      if (e > 1e-12) ++badh;
+    }
+    osim_destroy(s);
+    report("heatcool", n, worsth, badh);
   }
   // 6. CFL denominator (FP64) against the oracle's
   {

@@ -14,6 +14,7 @@ SRC = os.path.join(ROOT, "oracle", "mhd_oracle.c")
 sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 import test_oracle_cfl_chem as T_cc  # noqa: E402
+import test_oracle_heatcool as T_hc  # noqa: E402
 import test_oracle_physics as T_ph  # noqa: E402
 import test_oracle_ppm as T_ppm  # noqa: E402
 import test_oracle_riemann as T_rs  # noqa: E402
@@ -50,6 +51,12 @@ MUTATIONS = [
     ("gamma_eff_weights_swapped", "return (5.0 * nH + 7.0 * nH2) / (3.0 * nH + 5.0 * nH2);",
      "return (7.0 * nH + 5.0 * nH2) / (5.0 * nH + 3.0 * nH2);"),
     ("face_b_average_index", "s->b[d][c] = 0.5 * (Bc[d][srclo] + Bc[d][src]);", "s->b[d][c] = Bc[d][src];"),
+    ("lambda2_high_T_constant", "3.9e-19 * exp(-6118.0 / T)", "3.9e-19 * exp(-6181.0 / T)"),
+    ("lambda2_low_density_exponent", "(pow(nH2, 0.77) + 1.2 * pow(nH, 0.77))", "(pow(nH2, 0.77) + 1.2 * pow(nH, 0.7))"),
+    ("gamma1_critical_density_inverted", "h.G1 = 7.2e-12 * r.C / (1.0 + ncr / n);", "h.G1 = 7.2e-12 * r.C / (1.0 + n / ncr);"),
+    ("gamma4_energy", "h.G4 = 6.4e-13 * r.k4 * nH2;", "h.G4 = 6.4e-12 * r.k4 * nH2;"),
+    ("heatcool_limiter", "if (d < -0.5 * eint) d = -0.5 * eint;", "if (d < -0.25 * eint) d = -0.25 * eint;"),
+    ("heatcool_energy_only_total", "        s->E[c] = s->E[c] + d;\n", "        s->E[c] = s->E[c] + 2.0 * d;\n"),
 ]
 
 
@@ -71,6 +78,14 @@ def load_mutant(tmp_path, name, old, new):
 
 def pins(O):
     """A fast selection of the pins, each run against module O."""
+    hc = lambda: O.Sim(4, 4, 4, 5.0 / 3.0, 2.0, chem=1, heatcool=1)
+    yield "heatcool_branches", lambda: [T_hc.test_lambda2_branches_join(hc(), T, r) for T, r in
+                                        [(1087.0, 1e8), (4031.0, 1e-6)]]
+    yield "heatcool_limits", lambda: T_hc.test_lambda2_density_limits(hc())
+    yield "heatcool_gamma1", lambda: T_hc.test_gamma1_critical_density_limits(O, hc())
+    yield "heatcool_gamma4", lambda: T_hc.test_gamma4_per_photodissociation(hc())
+    yield "heatcool_step", lambda: T_hc.test_euler_step_is_linear_and_limited(hc())
+    yield "heatcool_box", lambda: T_hc.test_box_stage_changes_only_the_energies(O)
     st = T_rs.random_states(5, 7)
     yield "eigen", lambda: [T_rs.test_eigen_identities(O, s, 1e-11) for s in st]
     yield "linear_riemann", lambda: [T_rs.test_flat_riemann_matches_numpy_linear_solution(O, k) for k in range(3)]
