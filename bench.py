@@ -231,6 +231,23 @@ def heatcool_leg(M, I, torch, n=128, steps=10, warm=3):
     return out
 
 
+def gravity_leg(M, I, torch, n=128, steps=10, warm=3):
+    """Self-gravity (Sec. 2.10 Poisson solve by cuFFT each step, gravity terms in the Eulerian stage)
+    on the FP64 128^3 turbulence box with G in code units (pc, km/s, m_H cm^-3): Mcell-updates/s
+    with and without it."""
+    G_CODE = 6.6743e-8 * 1.6735575e-24 * (3.0856775814913673e18 / 1e5) ** 2
+    ic = I.turbulence(n, mach=5.0, beta=1.0, seed=1)
+    out = {"workload": f"mhd_turbulence_h2chem_gravity_{n}^3_fp64", "unit": METRIC, "steps": steps,
+           "warmup": warm, "G_code": G_CODE}
+    for on in (1, 0):
+        s = M.from_ic(ic, grav_g=G_CODE if on else 0.0)
+        ms = timed_steps(torch, s, steps, warm)
+        out["on" if on else "off"] = {"value": n ** 3 * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps}
+        del s
+    out["value"] = out["on"]["value"]
+    return out
+
+
 def batched_leg(M, I, torch, steps=20, warm=3):
     """Config 4: 64 turbulence boxes, axes from {16..96}, FP32 bulk, one launch per kernel class
     per step (CUDA graph), launch shapes autotuned first."""
@@ -310,7 +327,8 @@ def run_leg(args):
     B.build()
     import paper_1608_08748_gb300 as M
     from paper_1608_08748_gb300 import inputs as I
-    fn = {"fp32": fp32_leg, "batched": batched_leg, "serving": serving_leg, "heatcool": heatcool_leg}[args.leg]
+    fn = {"fp32": fp32_leg, "batched": batched_leg, "serving": serving_leg, "heatcool": heatcool_leg,
+          "gravity": gravity_leg}[args.leg]
     print(json.dumps({args.leg: fn(M, I, torch)}), flush=True)
 
 
@@ -416,6 +434,7 @@ def run_ours(args):
         extras["batched"] = batched_leg(M, I, torch)
         extras["serving"] = serving_leg(M, I, torch, big=args.serving_big)
         extras["heatcool"] = heatcool_leg(M, I, torch)
+        extras["gravity"] = gravity_leg(M, I, torch)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, secs = oracle_rate(48, 8)
@@ -447,8 +466,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the FP32-bulk (256^3), batched-ensemble, serving and heating/cooling legs")
-    ap.add_argument("--leg", choices=["main", "fp32", "batched", "serving", "heatcool"], default="main",
+                    help="skip the FP32-bulk (256^3), batched-ensemble, serving, heating/cooling and gravity legs")
+    ap.add_argument("--leg", choices=["main", "fp32", "batched", "serving", "heatcool", "gravity"],
+                    default="main",
                     help="run one secondary leg alone (for profiling)")
     ap.add_argument("--serving-big", action="store_true",
                     help="include the 512^3 request class (probability 0.005) in the serving leg")

@@ -65,10 +65,17 @@ enum mhd_option {
   MHD_OPT_CHEM_XNORM = 10,   /* N_H2 normaliser of f_shield in cm^-2 (default 5e14) */
   MHD_OPT_CHEM_TAUD = 11,    /* dust optical depth per unit column, cm^2 (default 1e-21) */
   MHD_OPT_GRAPH = 14,        /* 1 (default): replay each step from a captured CUDA graph; 0: launch */
-  MHD_OPT_HEATCOOL = 15      /* 0 off (default); 1 the Sec. 2.8 heating/cooling stage after the
+  MHD_OPT_HEATCOOL = 15,     /* 0 off (default); 1 the Sec. 2.8 heating/cooling stage after the
                                 chemistry (needs MHD_OPT_CHEM = 1): rho E and rho eps change by
                                 tau (Gamma_1 + Gamma_4 - Lambda_2 - Lambda_3) of App. D, FP64, the
                                 change limited to at most half of rho eps */
+  MHD_OPT_GRAV_G = 16        /* gravitational constant G in code units (0: no self-gravity, the
+                                default; 1.0635e-4 is G in pc, km/s, m_H cm^-3).  Each step first
+                                solves the Poisson equation of Sec. 2.10 for the density (27-point
+                                scheme in harmonic space, cuFFT, periodic boundaries required) and
+                                the Eulerian stage adds -rho grad Phi and -rho v . grad Phi (central
+                                differences).  Such a sim steps without graph capture and cannot
+                                join a batch. */
 };
 
 enum mhd_dtype { MHD_F64 = 0, MHD_F32 = 1 };
@@ -136,6 +143,11 @@ int mhd_diagnostics(mhd_sim* s, mhd_diag* out);
 /* One stage alone with a given tau (per-stage parity checks): 1 Eulerian + Flux-CT, 2 Lagrangian,
    3 chemistry, 4 regularisation, 5 heating/cooling (with MHD_OPT_HEATCOOL on). */
 int mhd_stage(mhd_sim* s, int which, double tau);
+
+/* The gravitational potential of the current density (Sec. 2.10, MHD_OPT_GRAV_G > 0): nx*ny*nz
+   doubles in C order [k][j][i], host or device pointer, owned by the caller.  MHD_EINVAL when
+   self-gravity is off, no state is loaded or a boundary is not periodic. */
+int mhd_get_potential(mhd_sim* s, double* out);
 
 /* Kernel classes reported by mhd_profile (index into its output arrays). */
 enum mhd_kernel_class {

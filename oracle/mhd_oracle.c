@@ -72,7 +72,8 @@ enum {
   O_CHEM_XNORM = 10,                  /* N_H2 normaliser of f_shield, cm^-2 */
   O_CHEM_TAUD = 11,                   /* dust optical depth per column, cm^2 */
   O_THREADS = 12,
-  O_HEATCOOL = 13                     /* 0 off (default), 1 Sec. 2.8 heating/cooling (needs chemistry) */
+  O_HEATCOOL = 13,                    /* 0 off (default), 1 Sec. 2.8 heating/cooling (needs chemistry) */
+  O_GRAV_G = 14                       /* G in code units for self-gravity (0: off, the default; periodic) */
 };
 
 enum { O_OK = 0, O_EINVAL = -1, O_ENOMEM = -2, O_ENONPHYS = -4 };
@@ -92,6 +93,7 @@ typedef struct {
   double gamma, dx;
   int chem, step4_as_written, iface_edge, regul_mode, threads, heatcool;
   double lshield, bdop, xnorm, taud;
+  double grav_g;     /* gravitational constant in code units (0: no self-gravity) */
   double t;
   long nsteps, nvel_branch;
   /* state on the extended grid */
@@ -104,6 +106,7 @@ typedef struct {
   double *accL[7];   /* Lagrangian accumulators */
   double *eA[3], *eB[3]; /* per-direction EMF contributions of the faces */
   double *edge[3];   /* edge EMFs E_x, E_y, E_z */
+  double *phi;       /* gravitational potential (extended grid) */
 } osim;
 
 /* ---------------------------------------------------------------- indexing */
@@ -420,6 +423,7 @@ osim* osim_create(int nx, int ny, int nz, double gamma, double dx) {
   for (int i = 0; i < 7; ++i) if (!(s->accL[i] = xalloc(n))) goto fail;
   for (int i = 0; i < 3; ++i)
     if (!(s->eA[i] = xalloc(n)) || !(s->eB[i] = xalloc(n)) || !(s->edge[i] = xalloc(n))) goto fail;
+  if (!(s->phi = xalloc(n))) goto fail;
   return s;
 fail:;
   extern void osim_destroy(osim*);
@@ -438,6 +442,7 @@ void osim_destroy(osim* s) {
   for (int i = 0; i < 6; ++i) free(s->acc[i]);
   for (int i = 0; i < 7; ++i) free(s->accL[i]);
   for (int i = 0; i < 3; ++i) { free(s->eA[i]); free(s->eB[i]); free(s->edge[i]); }
+  free(s->phi);
   free(s);
 }
 
@@ -460,6 +465,7 @@ int osim_set_option(osim* s, int key, double v) {
     case O_CHEM_TAUD: if (v < 0.0) return O_EINVAL; s->taud = v; return O_OK;
     case O_THREADS: if (v < 1.0) return O_EINVAL; s->threads = (int)v; return O_OK;
     case O_HEATCOOL: if (v != 0.0 && v != 1.0) return O_EINVAL; s->heatcool = (int)v; return O_OK;
+    case O_GRAV_G: if (v < 0.0) return O_EINVAL; s->grav_g = v; return O_OK;
     default: return O_EINVAL;
   }
 }
@@ -741,6 +747,15 @@ static void eulerian_update(osim* s, double a, double bb, double g, double tau) 
         R[3] = s->acc[3][c] * ih;
         /* rho eps source -(gamma - 1) rho eps div V (A12); acc[4] * ih = -div V */
         R[4] = ((g_cell - 1.0) * s->eint[c]) * (s->acc[4][c] * ih);
+        if (s->grav_g > 0.0) {
+          /* Sec. 2.4: the gravity terms -rho grad Phi and -rho v . grad Phi by central differences
+             of the potential of the step (A31) */
+          for (int d = 0; d < 3; ++d) {
+            double gd = -(s->phi[c + ST(s, d)] - s->phi[c - ST(s, d)]) * (0.5 * ih);
+            R[d] = R[d] + s->rho[c] * gd;
+            R[3] = R[3] + s->m[d][c] * gd;
+          }
+        }
         double* q[5] = {s->m[0], s->m[1], s->m[2], s->E, s->eint};
         double* q0[5] = {s->m0[0], s->m0[1], s->m0[2], s->E0, s->eint0};
         for (int v = 0; v < 5; ++v) q[v][c] = (a * q0[v][c] + bb * q[v][c]) + g * (tau * R[v]);
@@ -1023,6 +1038,88 @@ static const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
 static const double RK_G[3] = {1.0, 0.25, 2.0 / 3.0};
 
 /* Eulerian stage with Flux-CT inside each RK substage (A10) */
+/* ---------------------------------------------------------------- Sec. 2.10 Poisson equation */
+/* One-dimensional discrete Fourier transform along axis d of the complex field (re, im) on the
+   interior grid (x fastest): X_k = sum_j x_j exp(sign 2 pi i j k / N), plain O(N^2) sums with the
+   phase of (j k mod N) from a table. */
+static void dft_axis(const osim* s, double* re, double* im, int d, int sign) {
+  const int nx = s->n[0], ny = s->n[1], nz = s->n[2];
+  const int N = s->n[d];
+  const size_t stride = d == 0 ? 1 : (d == 1 ? (size_t)nx : (size_t)nx * ny);
+  const int lines = nx * ny * nz / N;
+  double* cs = (double*)malloc(sizeof(double) * N);
+  double* sn = (double*)malloc(sizeof(double) * N);
+  for (int m = 0; m < N; ++m) {
+    cs[m] = cos(2.0 * M_PI * m / N);
+    sn[m] = sign * sin(2.0 * M_PI * m / N);
+  }
+#pragma omp parallel for schedule(static) num_threads(s->threads)
+  for (int l = 0; l < lines; ++l) {
+    /* first element of line l: the other two indices enumerate the lines */
+    size_t base;
+    if (d == 0) base = (size_t)l * nx;
+    else if (d == 1) base = (size_t)(l / nx) * nx * ny + (size_t)(l % nx);
+    else base = (size_t)l;
+    double* xr = (double*)malloc(sizeof(double) * N);
+    double* xi = (double*)malloc(sizeof(double) * N);
+    for (int j = 0; j < N; ++j) {
+      xr[j] = re[base + j * stride];
+      xi[j] = im[base + j * stride];
+    }
+    for (int k = 0; k < N; ++k) {
+      double sr = 0.0, si = 0.0;
+      for (int j = 0; j < N; ++j) {
+        int m = (int)(((long)j * k) % N);
+        sr += xr[j] * cs[m] - xi[j] * sn[m];
+        si += xr[j] * sn[m] + xi[j] * cs[m];
+      }
+      re[base + k * stride] = sr;
+      im[base + k * stride] = si;
+    }
+    free(xr);
+    free(xi);
+  }
+  free(cs);
+  free(sn);
+}
+
+/* Sec. 2.10: the potential of the 27-point scheme in harmonic space,
+   Phi_jmn = -(2/3) pi G h^2 rho_jmn / (1 - c_j c_m c_n), c_j = (3 - 2 sin^2(pi j / N)) / 3, the mean
+   (j = m = n = 0) mode zero (A30); the potential of the periodic box. */
+static void poisson(osim* s) {
+  const int nx = s->n[0], ny = s->n[1], nz = s->n[2];
+  const size_t N = (size_t)nx * ny * nz;
+  double* re = (double*)malloc(sizeof(double) * N);
+  double* im = (double*)calloc(N, sizeof(double));
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) re[((size_t)k * ny + j) * nx + i] = s->rho[IX(s, i + NG, j + NG, k + NG)];
+  for (int d = 0; d < 3; ++d) dft_axis(s, re, im, d, -1);
+  const double h = s->dx;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t c = ((size_t)k * ny + j) * nx + i;
+        if (i == 0 && j == 0 && k == 0) {
+          re[c] = 0.0;
+          im[c] = 0.0;
+          continue;
+        }
+        double si = sin(M_PI * i / nx), sj = sin(M_PI * j / ny), sk = sin(M_PI * k / nz);
+        double cx = (3.0 - 2.0 * si * si) / 3.0, cy = (3.0 - 2.0 * sj * sj) / 3.0, cz = (3.0 - 2.0 * sk * sk) / 3.0;
+        double f = -(2.0 / 3.0) * M_PI * s->grav_g * h * h / (1.0 - cx * cy * cz);
+        re[c] *= f;
+        im[c] *= f;
+      }
+  for (int d = 0; d < 3; ++d) dft_axis(s, re, im, d, +1);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) s->phi[IX(s, i + NG, j + NG, k + NG)] = re[((size_t)k * ny + j) * nx + i] / (double)N;
+  fill_ghosts(s, s->phi);
+  free(re);
+  free(im);
+}
+
 static void eulerian_stage(osim* s, double tau) {
   const double tau_h = tau / s->dx;
   save_Qn(s, 0);
@@ -1062,7 +1159,10 @@ static int check_physical(osim* s) {
    3 chemistry, 4 regularisation, 5 heating/cooling */
 int osim_stage(osim* s, int which, double tau) {
   switch (which) {
-    case 1: eulerian_stage(s, tau); break;
+    case 1:
+      if (s->grav_g > 0.0) poisson(s);
+      eulerian_stage(s, tau);
+      break;
     case 2: lagrangian_stage(s, tau); break;
     case 3: if (s->chem) chemistry(s, tau); break;
     case 4: s->nvel_branch += regularise(s); break;
@@ -1078,6 +1178,10 @@ int osim_step(osim* s, double cfl, double t_end, double* dt) {
   double tau = osim_tau(s, cfl);
   if (t_end > 0.0 && tau > t_end - s->t) tau = t_end - s->t;
   if (!(tau > 0.0)) return O_EINVAL;
+  if (s->grav_g > 0.0) {
+    if (s->bc[0] || s->bc[1] || s->bc[2]) return O_EINVAL; /* self-gravity of a periodic box */
+    poisson(s); /* stage 7 of the previous step: the potential of rho^n (A31) */
+  }
   eulerian_stage(s, tau);
   lagrangian_stage(s, tau);
   if (s->chem) chemistry(s, tau);
@@ -1200,6 +1304,17 @@ void osim_chem_cell(const osim* s, double rho, double eint, double rh2, double t
   out[5] = r.k4;
   out[6] = r.C;
   out[7] = r.D;
+}
+
+/* the gravitational potential of the current density (Sec. 2.10), interior cells, x fastest */
+int osim_potential(osim* s, double* out) {
+  if (!(s->grav_g > 0.0)) return O_EINVAL;
+  poisson(s);
+  for (int k = 0; k < s->n[2]; ++k)
+    for (int j = 0; j < s->n[1]; ++j)
+      for (int i = 0; i < s->n[0]; ++i)
+        out[((size_t)k * s->n[1] + j) * s->n[0] + i] = s->phi[IX(s, i + NG, j + NG, k + NG)];
+  return O_OK;
 }
 
 /* heating/cooling of one cell with the simulation's parameters:

@@ -26,7 +26,7 @@ _lib = None
 OPT = {
     "bc_x": 1, "bc_y": 2, "bc_z": 3, "chem": 4, "step4_as_written": 5, "iface_edge": 6,
     "regul_mode": 7, "chem_lshield": 8, "chem_bdop": 9, "chem_xnorm": 10, "chem_taud": 11,
-    "threads": 12, "heatcool": 13,
+    "threads": 12, "heatcool": 13, "grav_g": 14,
 }
 OK, EINVAL, ENOMEM, ENONPHYS = 0, -1, -2, -4
 
@@ -81,6 +81,7 @@ def lib():
         L.o_gamma_eff.argtypes = [d, d]
         L.osim_chem_cell.argtypes = [vp, d, d, d, d, _dp]
         L.osim_heatcool_cell.argtypes = [vp, d, d, d, d, _dp]
+        L.osim_potential.argtypes = [vp, _dp]
         L.osim_chem_rates.argtypes = [vp, d, d, d, _dp]
         _lib = L
     return _lib
@@ -180,6 +181,13 @@ class Sim:
         out = np.zeros(8)
         self.L.osim_chem_cell(self.h, float(rho), float(eint), float(rh2), float(tau), out)
         return dict(zip(["rho_h2", "T", "k1p", "k2", "k3", "k4", "C", "D"], out))
+
+    def potential(self):
+        """Sec. 2.10 potential of the current density (needs the grav_g option)."""
+        out = np.zeros(self.shape)
+        if self.L.osim_potential(self.h, out.reshape(-1)) != OK:
+            raise ValueError("no self-gravity (grav_g = 0)")
+        return out
 
     def heatcool_cell(self, rho, eint, rh2, tau):
         """Sec. 2.8 heating/cooling of one cell: the change of rho E and rho eps (code units) and the

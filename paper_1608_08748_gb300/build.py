@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmhd.so")
-SOURCES = ["mhd.cu", "mhd_noalloc.cu", "mhd_server.cu"]
+SOURCES = ["mhd.cu", "mhd_noalloc.cu", "mhd_server.cu", "mhd_gravity.cu"]
 # FP32-bulk launchers: compiled separately with contraction on
 SOURCES_F32 = ["mhd_f32.cu"]
 HEADERS = ["mhd_device.cuh", "mhd_kernels.cuh", "mhd_runtime.cuh"]
@@ -22,7 +22,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(SRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "mhd.h")]
+    deps = [os.path.join(SRC, f) for f in SOURCES + SOURCES_F32 + HEADERS] + [os.path.join(ROOT, "include", "mhd.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if p.wait() != 0:
             raise subprocess.CalledProcessError(p.returncode, cmd)
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcufft"]
     if verbose:
         print(" ".join(link))
     subprocess.run(link, check=True)

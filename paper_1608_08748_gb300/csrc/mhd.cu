@@ -75,6 +75,7 @@ void carve(mhd_sim* S, Box<T>& B) {
   for (int d = 0; d < 3; ++d)
     for (int v = 0; v < 7; ++v) B.fo[d].f[v] = take(NF);
   for (int d = 0; d < 3; ++d) B.e[d] = take(NF);
+  B.phi = nullptr;
   B.g = S->g;
   B.ph = S->ph;
   B.sc = S->sc;
@@ -138,8 +139,22 @@ void launch_sim_step(mhd_sim* S) {
 }
 
 int enqueue_step(mhd_sim* S) {
-  int rc = ensure_exec(S);
+  int rc;
+  const bool grav = S->ph.grav_g > 0.0;
+  if (grav) {
+    if (S->g.bc[0] || S->g.bc[1] || S->g.bc[2]) return fail(MHD_EINVAL, "self-gravity needs periodic boundaries");
+    if ((rc = grav_prepare(S)) != MHD_OK) return rc;
+  }
+  rc = ensure_exec(S);
   if (rc != MHD_OK) return rc;
+  if (grav) {
+    // the potential of rho^n (stage 7 of the previous step), then the step; launched directly, so
+    // the cuFFT transforms stay outside a captured graph
+    if ((rc = grav_solve(S)) != MHD_OK) return rc;
+    launch_sim_step(S);
+    CK(cudaGetLastError());
+    return MHD_OK;
+  }
   if (S->use_graph) {
     if (!S->graph_valid) {
       drop_graph(S);
@@ -242,6 +257,7 @@ mhd_sim* mhd_create(int nx, int ny, int nz, double gamma, double dx) {
   S->ph.ixnorm = 1.0 / 5e14;
   S->ph.taud = 1e-21;
   S->ph.heatcool = 0;
+  S->ph.grav_g = 0.0;
   auto bail = [&](const char* what, cudaError_t e) {
     fail(e == cudaErrorMemoryAllocation ? MHD_ENOMEM : MHD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     mhd_destroy(S);
@@ -279,6 +295,7 @@ void mhd_destroy(mhd_sim* S) {
   drop_graph(S);
   exec_free(S->x64);
   exec_free(S->x32);
+  grav_free(S);
   if (S->pool) cudaFree(S->pool);
   if (S->staging) cudaFree(S->staging);
   if (S->sc) cudaFree(S->sc);
@@ -337,6 +354,10 @@ int mhd_set_option(mhd_sim* S, int key, double v) {
     case MHD_OPT_HEATCOOL:
       if (v != 0.0 && v != 1.0) return fail(MHD_EINVAL, "heating/cooling must be 0 (off) or 1 (on)");
       S->ph.heatcool = (int)v;
+      break;
+    case MHD_OPT_GRAV_G:
+      if (!(v >= 0.0)) return fail(MHD_EINVAL, "the gravitational constant must be >= 0");
+      S->ph.grav_g = v;
       break;
     default:
       return fail(MHD_EINVAL, "unknown option key " + std::to_string(key));
@@ -541,7 +562,13 @@ int mhd_stage(mhd_sim* S, int which, double tau) {
   if (which < 1 || which > 5 || !(tau > 0.0)) return fail(MHD_EINVAL, "mhd_stage: which in 1..5, tau > 0");
   const int cell_stages = which == 3 ? 1 : (which == 5 ? 2 : 0);
   int rc;
+  const bool grav = which == 1 && S->ph.grav_g > 0.0;
+  if (grav) {
+    if (S->g.bc[0] || S->g.bc[1] || S->g.bc[2]) return fail(MHD_EINVAL, "self-gravity needs periodic boundaries");
+    if ((rc = grav_prepare(S)) != MHD_OK) return rc;
+  }
   if ((rc = set_params(S, 1.0, 0.0, 1, tau)) != MHD_OK) return rc;
+  if (grav && (rc = grav_solve(S)) != MHD_OK) return rc;
   S->params_dirty = true;
   if (S->precision) {
     launch_small(S->x32, S->stream, 0);
@@ -558,6 +585,18 @@ int mhd_stage(mhd_sim* S, int which, double tau) {
   if ((rc = refresh_cfl(S)) != MHD_OK) return rc;
   if ((rc = set_params(S, 1.0, 0.0, 0, 0.0)) != MHD_OK) return rc;
   return mhd_sync(S);
+}
+
+int mhd_get_potential(mhd_sim* S, double* out) {
+  if (!valid(S) || !out) return fail(MHD_EINVAL, "mhd_get_potential: null argument");
+  if (!(S->ph.grav_g > 0.0)) return fail(MHD_EINVAL, "mhd_get_potential: self-gravity is off");
+  if (!S->has_state) return fail(MHD_EINVAL, "mhd_get_potential: no state loaded");
+  if (S->g.bc[0] || S->g.bc[1] || S->g.bc[2]) return fail(MHD_EINVAL, "self-gravity needs periodic boundaries");
+  int rc;
+  if ((rc = grav_prepare(S)) != MHD_OK) return rc;
+  if ((rc = ensure_exec(S)) != MHD_OK) return rc;
+  if ((rc = grav_solve(S)) != MHD_OK) return rc;
+  return grav_copy(S, out);
 }
 
 int mhd_launches_per_step(mhd_sim* S) {
@@ -814,6 +853,10 @@ mhd_batch* mhd_batch_create(mhd_sim* const* sims, int n) {
     }
     if (sims[i]->precision != sims[0]->precision || sims[i]->device != sims[0]->device) {
       fail(MHD_EINVAL, "mhd_batch_create: sims differ in precision or device");
+      return nullptr;
+    }
+    if (sims[i]->ph.grav_g > 0.0) {
+      fail(MHD_EINVAL, "mhd_batch_create: self-gravity sims step alone (one Poisson solve per box)");
       return nullptr;
     }
   }

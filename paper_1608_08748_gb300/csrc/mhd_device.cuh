@@ -32,6 +32,7 @@ struct Phys {
   double bdop, xnorm, taud;
   double ibdop, ixnorm;  // 1 / bdop, 1 / xnorm
   int heatcool;          // Sec. 2.8 heating/cooling stage on (needs chem)
+  double grav_g;         // gravitational constant in code units (0: no self-gravity)
 };
 
 // Device-resident scalars of a simulation: tau never crosses to the host inside a step.

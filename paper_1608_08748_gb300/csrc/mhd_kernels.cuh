@@ -43,6 +43,7 @@ struct Box {
   FaceOut<T> fo[3];  // Eulerian face outputs; the Lagrangian fluxes reuse fo[d].f[0..6]
   T* e[3];
   int nv;            // advected fields of the Lagrangian stage (6, or 7 with rho_H2)
+  const T* phi;      // gravitational potential of the step (nullptr: no self-gravity)
 };
 
 struct Tiles {
@@ -312,6 +313,19 @@ __device__ __forceinline__ void euler_update_cell(const Box<T>& B, idx_t c, int 
 #pragma unroll
   for (int v = 0; v < 4; ++v) Rv[v] = acc[v] * ih;
   Rv[4] = ((B.w.g[c] - T(1)) * B.s.eint[c]) * (acc[4] * ih);  // -(gamma - 1) rho eps div V
+  if (B.phi) {
+    // self-gravity (Sec. 2): -rho grad Phi and -rho v . grad Phi, central differences of the
+    // potential of the step (periodic box)
+    const idx_t dn[3] = {cmap(g, q[0] - 1, q[1], q[2]), cmap(g, q[0], q[1] - 1, q[2]), cmap(g, q[0], q[1], q[2] - 1)};
+    const idx_t upc[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
+    const T rho = B.s.rho[c];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T gd = -(B.phi[upc[d]] - B.phi[dn[d]]) * (T(0.5) * ih);
+      Rv[d] = Rv[d] + rho * gd;
+      Rv[3] = Rv[3] + B.s.m[d][c] * gd;
+    }
+  }
   T* qq[5] = {B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint};
   T* q0[5] = {B.s0.m[0], B.s0.m[1], B.s0.m[2], B.s0.E, B.s0.eint};
 #pragma unroll

@@ -339,11 +339,19 @@ struct mhd_sim {
   double last_cfl = -1.0, last_tend = -1.0;
   bool has_state = false;
   int batched = 0;  // number of batches that reference this sim
+  void* grav = nullptr;  // self-gravity resources (mhd_gravity.cu), allocated on first use
 };
 
 namespace mhd_rt {
 
 // ------------------------------------------------------------------------------------------------
+// self-gravity (mhd_gravity.cu): allocate and point the box at the potential; enqueue the Poisson
+// solve of the current density; copy the potential out; release
+int grav_prepare(mhd_sim* S);
+int grav_solve(mhd_sim* S);
+int grav_copy(mhd_sim* S, double* out);
+void grav_free(mhd_sim* S);
+
 // per-sim (non-batched) helpers: state transfer and diagnostics
 template <typename T, typename In>
 cudaError_t load_state(mhd_sim* S, Box<T>& B, const In* const* p) {

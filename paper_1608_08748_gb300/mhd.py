@@ -16,7 +16,7 @@ from . import build as _build
 
 OPT = {"bc_x": 1, "bc_y": 2, "bc_z": 3, "chem": 4, "precision": 5, "regul_mode": 7,
        "chem_lshield": 8, "chem_bdop": 9, "chem_xnorm": 10, "chem_taud": 11, "graph": 14,
-       "heatcool": 15}
+       "heatcool": 15, "grav_g": 16}
 STATUS = {0: "MHD_OK", 1: "MHD_PENDING", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA",
           -4: "MHD_ENONPHYS", -5: "MHD_ETIMEOUT", -6: "MHD_ENOTFOUND", -7: "MHD_ECAPACITY"}
 F64, F32 = 0, 1
@@ -85,6 +85,7 @@ def lib():
         L.mhd_bytes_needed.argtypes = [i, i, i, i, i]
         L.mhd_profile.argtypes = [vp, d, i, C.POINTER(d), C.POINTER(C.c_int64)]
         L.mhd_launches_per_step.argtypes = [vp]
+        L.mhd_get_potential.argtypes = [vp, vp]
         L.mhd_batch_create.restype = vp
         L.mhd_batch_create.argtypes = [C.POINTER(vp), i]
         L.mhd_batch_destroy.argtypes = [vp]
@@ -230,6 +231,12 @@ class Sim:
 
     def stage(self, which, tau):
         _check(self.L.mhd_stage(self.h, int(which), float(tau)))
+
+    def potential(self):
+        """Sec. 2.10 gravitational potential of the current density (needs the grav_g option)."""
+        out = np.empty(self.shape)
+        _check(self.L.mhd_get_potential(self.h, out.ctypes.data))
+        return out
 
     def diagnostics(self):
         d = Diag()

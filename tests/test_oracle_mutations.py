@@ -14,6 +14,7 @@ SRC = os.path.join(ROOT, "oracle", "mhd_oracle.c")
 sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 import test_oracle_cfl_chem as T_cc  # noqa: E402
+import test_oracle_gravity as T_gr  # noqa: E402
 import test_oracle_heatcool as T_hc  # noqa: E402
 import test_oracle_physics as T_ph  # noqa: E402
 import test_oracle_ppm as T_ppm  # noqa: E402
@@ -57,6 +58,14 @@ MUTATIONS = [
     ("gamma4_energy", "h.G4 = 6.4e-13 * r.k4 * nH2;", "h.G4 = 6.4e-12 * r.k4 * nH2;"),
     ("heatcool_limiter", "if (d < -0.5 * eint) d = -0.5 * eint;", "if (d < -0.25 * eint) d = -0.25 * eint;"),
     ("heatcool_energy_only_total", "        s->E[c] = s->E[c] + d;\n", "        s->E[c] = s->E[c] + 2.0 * d;\n"),
+    ("poisson_symbol_factor", "double f = -(2.0 / 3.0) * M_PI * s->grav_g * h * h / (1.0 - cx * cy * cz);",
+     "double f = -(1.0 / 3.0) * M_PI * s->grav_g * h * h / (1.0 - cx * cy * cz);"),
+    ("poisson_symbol_sign", "double f = -(2.0 / 3.0) * M_PI * s->grav_g * h * h / (1.0 - cx * cy * cz);",
+     "double f = (2.0 / 3.0) * M_PI * s->grav_g * h * h / (1.0 - cx * cy * cz);"),
+    ("poisson_axis_table", "double cx = (3.0 - 2.0 * si * si) / 3.0, cy", "double cx = (3.0 - 1.0 * si * si) / 3.0, cy"),
+    ("gravity_energy_uses_rho", "            R[3] = R[3] + s->m[d][c] * gd;", "            R[3] = R[3] + s->rho[c] * gd;"),
+    ("gravity_central_difference", "double gd = -(s->phi[c + ST(s, d)] - s->phi[c - ST(s, d)]) * (0.5 * ih);",
+     "double gd = -(s->phi[c + ST(s, d)] - s->phi[c]) * ih;"),
 ]
 
 
@@ -86,6 +95,10 @@ def pins(O):
     yield "heatcool_gamma4", lambda: T_hc.test_gamma4_per_photodissociation(hc())
     yield "heatcool_step", lambda: T_hc.test_euler_step_is_linear_and_limited(hc())
     yield "heatcool_box", lambda: T_hc.test_box_stage_changes_only_the_energies(O)
+    yield "gravity_27pt", lambda: [T_gr.test_potential_satisfies_the_27_point_equation(O, sh) for sh in
+                                   [(8, 10, 12), (5, 7, 9)]]
+    yield "gravity_stage", lambda: T_gr.test_eulerian_stage_with_gravity_only(O)
+    yield "gravity_fall", lambda: T_gr.test_gas_falls_towards_the_density_peak(O)
     st = T_rs.random_states(5, 7)
     yield "eigen", lambda: [T_rs.test_eigen_identities(O, s, 1e-11) for s in st]
     yield "linear_riemann", lambda: [T_rs.test_flat_riemann_matches_numpy_linear_solution(O, k) for k in range(3)]
