@@ -275,7 +275,7 @@ def batched_leg(M, I, torch, steps=20, warm=3):
             "kernels": {k: v["ms_total"] / 2 for k, v in prof.items()}}
 
 
-def serving_leg(M, I, torch, duration=10.0, big=False):
+def serving_leg(M, I, torch, duration=10.0, big=False, policy="fifo"):
     """Config 5: Poisson arrivals (20 requests/s, seed 5) of turbulence runs, cubic n in
     {32..192} (and 512 with probability 0.005 when big), 20-200 steps, FP32 bulk, submitted in real
     time to the continuous-batching server.  Velocity fields: one cached solenoidal field per size,
@@ -287,6 +287,7 @@ def serving_leg(M, I, torch, duration=10.0, big=False):
     free, _ = torch.cuda.mem_get_info()
     budget = int(free * 0.6)
     srv = M.Server(budget, max_active=64)
+    srv.set_policy(policy)
     rng = np.random.default_rng(5)
     ids = []
     t0 = time.perf_counter()
@@ -317,7 +318,8 @@ def serving_leg(M, I, torch, duration=10.0, big=False):
             "stream_s": duration, "big_512": bool(big), "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "value": work / (last - first) / 1e6,
             "unit": METRIC, "wall_s": wall, "hbm_budget_bytes": budget, "peak_bytes": st["peak_bytes"],
-            "peak_active": st["peak_active"], "scheduler_iterations": st["iterations"], "failed": failed}
+            "peak_active": st["peak_active"], "scheduler_iterations": st["iterations"], "failed": failed,
+            "policy": policy}
 
 
 def run_leg(args):
@@ -329,7 +331,8 @@ def run_leg(args):
     from paper_1608_08748_gb300 import inputs as I
     fn = {"fp32": fp32_leg, "batched": batched_leg, "serving": serving_leg, "heatcool": heatcool_leg,
           "gravity": gravity_leg}[args.leg]
-    print(json.dumps({args.leg: fn(M, I, torch)}), flush=True)
+    kw = {"policy": args.serve_policy, "big": args.serving_big} if args.leg == "serving" else {}
+    print(json.dumps({args.leg: fn(M, I, torch, **kw)}), flush=True)
 
 
 def run_ours(args):
@@ -432,7 +435,7 @@ def run_ours(args):
     if world == 1 and not args.no_extras:
         extras["fp32_bulk"] = fp32_leg(M, I, torch)
         extras["batched"] = batched_leg(M, I, torch)
-        extras["serving"] = serving_leg(M, I, torch, big=args.serving_big)
+        extras["serving"] = serving_leg(M, I, torch, big=args.serving_big, policy=args.serve_policy)
         extras["heatcool"] = heatcool_leg(M, I, torch)
         extras["gravity"] = gravity_leg(M, I, torch)
     cpu = None
@@ -470,6 +473,8 @@ def main():
     ap.add_argument("--leg", choices=["main", "fp32", "batched", "serving", "heatcool", "gravity"],
                     default="main",
                     help="run one secondary leg alone (for profiling)")
+    ap.add_argument("--serve-policy", choices=["fifo", "smallest_work"], default="fifo",
+                    help="admission order of the serving leg")
     ap.add_argument("--serving-big", action="store_true",
                     help="include the 512^3 request class (probability 0.005) in the serving leg")
     args = ap.parse_args()

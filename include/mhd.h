@@ -230,6 +230,11 @@ typedef struct mhd_result {
 
 /* hbm_budget_bytes: device memory the admitted requests may use together; max_active >= 1. */
 mhd_server* mhd_server_create(size_t hbm_budget_bytes, int max_active);
+/* Admission order of waiting requests: MHD_SERVE_FIFO (the default; the oldest waits until it
+   fits) or MHD_SERVE_SMALLEST_WORK (among the requests that fit, the fewest cell-updates,
+   cells x steps, first).  Results do not depend on the policy, only their latencies. */
+enum mhd_serve_policy { MHD_SERVE_FIFO = 0, MHD_SERVE_SMALLEST_WORK = 1 };
+int mhd_server_set_policy(mhd_server* srv, int policy);
 /* Stops the scheduler after the running step; unfinished requests are dropped. */
 void mhd_server_destroy(mhd_server* srv);
 /* >= 0: request id; < 0: MHD_EINVAL, or MHD_ECAPACITY if it can never fit the budget. */

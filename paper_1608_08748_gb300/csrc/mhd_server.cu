@@ -53,6 +53,7 @@ struct Group {
 struct mhd_server {
   size_t budget = 0;
   int max_active = 1;
+  int policy = MHD_SERVE_FIFO;
   int device = 0;
   std::mutex mu;
   std::condition_variable cv, cv_done;
@@ -140,15 +141,40 @@ void scheduler(mhd_server* S) {
     {
       std::unique_lock<std::mutex> lk(S->mu);
       if (S->stop) break;
-      // strict arrival order: the head waits until it fits
-      while (!S->waiting.empty()) {
-        Req* q = S->reqs[S->waiting.front()].get();
-        if (S->nactive >= S->max_active || S->used + q->bytes > S->budget) break;
-        S->waiting.pop_front();
-        S->used += q->bytes;
-        S->nactive += 1;
-        q->st = RUNNING;
-        admit.push_back(q);
+      if (S->policy == MHD_SERVE_FIFO) {
+        // strict arrival order: the head waits until it fits
+        while (!S->waiting.empty()) {
+          Req* q = S->reqs[S->waiting.front()].get();
+          if (S->nactive >= S->max_active || S->used + q->bytes > S->budget) break;
+          S->waiting.pop_front();
+          S->used += q->bytes;
+          S->nactive += 1;
+          q->st = RUNNING;
+          admit.push_back(q);
+        }
+      } else {
+        // smallest work first: among the waiting requests that fit, the fewest cell-updates
+        // (cells x steps), ties by arrival
+        while (!S->waiting.empty() && S->nactive < S->max_active) {
+          auto best = S->waiting.end();
+          double best_work = 0.0;
+          for (auto it = S->waiting.begin(); it != S->waiting.end(); ++it) {
+            const Req* q = S->reqs[*it].get();
+            if (S->used + q->bytes > S->budget) continue;
+            const double work = (double)q->res.cells * q->r.nsteps;
+            if (best == S->waiting.end() || work < best_work) {
+              best = it;
+              best_work = work;
+            }
+          }
+          if (best == S->waiting.end()) break;
+          Req* q = S->reqs[*best].get();
+          S->waiting.erase(best);
+          S->used += q->bytes;
+          S->nactive += 1;
+          q->st = RUNNING;
+          admit.push_back(q);
+        }
       }
       if (admit.empty() && S->nactive == 0) {
         S->cv.wait(lk, [&] { return S->stop || !S->waiting.empty(); });
@@ -280,6 +306,14 @@ void mhd_server_destroy(mhd_server* S) {
   S->cv.notify_all();
   if (S->th.joinable()) S->th.join();
   delete S;
+}
+
+int mhd_server_set_policy(mhd_server* S, int policy) {
+  if (!S || (policy != MHD_SERVE_FIFO && policy != MHD_SERVE_SMALLEST_WORK))
+    return mhd_rt::set_error(MHD_EINVAL, "mhd_server_set_policy: policy must be MHD_SERVE_FIFO or MHD_SERVE_SMALLEST_WORK");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->policy = policy;
+  return MHD_OK;
 }
 
 int64_t mhd_submit(mhd_server* S, const mhd_request* r) {

@@ -106,6 +106,7 @@ def lib():
         L.mhd_server_clock.restype = d
         L.mhd_server_clock.argtypes = [vp]
         L.mhd_server_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(i)]
+        L.mhd_server_set_policy.argtypes = [vp, i]
         _lib = L
     return _lib
 
@@ -340,6 +341,10 @@ class Server:
 
     def __del__(self):
         self.close()
+
+    def set_policy(self, policy):
+        """Admission order: "fifo" (the default) or "smallest_work" (fewest cells x steps first)."""
+        _check(self.L.mhd_server_set_policy(self.h, {"fifo": 0, "smallest_work": 1}[policy]))
 
     def submit(self, ic, nsteps, cfl=0.4, precision=1):
         """Queue a request built from an initial-condition dict; returns its id."""

@@ -41,9 +41,11 @@ def solo(M, k):
     return s.get_state()
 
 
-def test_served_results_equal_solo_runs(M):
+@pytest.mark.parametrize("policy", ["fifo", "smallest_work"])
+def test_served_results_equal_solo_runs(M, policy):
     budget = sum(M.bytes_needed(*s[::-1], p, 1) for s, p, _, _ in REQS[:3])  # ~3 at a time
     srv = M.Server(budget, max_active=3)
+    srv.set_policy(policy)
     ids = []
     t0 = time.time()
     for k, (shape, prec, steps, delay) in enumerate(REQS):
