@@ -245,8 +245,10 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
     const bool ext = !same_sign(qL - qc, qc - qR);
     const T a = dq * q6, b = dq * dq;
     const bool up = gt_nn(a, b), dn = !up && gt_nn(neg_b(a), b);
-    const T qLm = ext ? qc : (up ? T(3) * qc - T(2) * qR : qL);
-    const T qRm = ext ? qc : (dn ? T(3) * qc - T(2) * qL : qR);
+    // the two overshoot fixes are exclusive: one candidate 3 qc - 2 q from the opposite edge
+    const T cand = T(3) * qc - T(2) * (up ? qR : qL);
+    const T qLm = ext ? qc : (up ? cand : qL);
+    const T qRm = ext ? qc : (dn ? cand : qR);
     qL = qLm;
     qR = qRm;
   }

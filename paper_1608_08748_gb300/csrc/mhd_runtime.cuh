@@ -248,13 +248,18 @@ void launch_small(Exec<T>& X, cudaStream_t st, int which, double cfl = 0, double
 
 template <typename T>
 void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
+  // self-gravity: a box with a potential (such sims step alone, never in a batch)
+  const bool grav = X.nb == 1 && X.h[0].phi != nullptr;
   for (int r = 0; r < 3; ++r) {
     launch_k(X, st, KC_PRIM, DOM_CELLS, kb_prim<T>);
     launch_ks(X, st, KC_EFACE, DOM_PENCIL_X, euler_pencil_smem<T>(), kb_euler_pencil<T, 0>);
     launch_ks(X, st, KC_EFACE, DOM_PENCIL_Y, euler_pencil_smem<T>(), kb_euler_pencil<T, 1>);
     launch_ks(X, st, KC_EFACE, DOM_PENCIL_Z, euler_pencil_smem<T>(), kb_euler_pencil<T, 2>);
     launch_k(X, st, KC_EDGES, DOM_LATTICE, kb_edges<T>);
-    launch_k(X, st, KC_EUPD, DOM_CELLS, kb_euler_update<T>, r);
+    if (grav)
+      launch_k(X, st, KC_EUPD, DOM_CELLS, kb_euler_update<T, true>, r);
+    else
+      launch_k(X, st, KC_EUPD, DOM_CELLS, kb_euler_update<T, false>, r);
   }
 }
 
