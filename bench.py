@@ -35,14 +35,14 @@ METRIC = "Mcell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # algorithmic FP64 flops of one Eulerian face, counted from the kernel source with an FMA as two
 # flops and a division, square root or reciprocal square root as one (compares and selects not
-# counted): the parabolas of the six primitives of one new cell, streamed along the pencil (6 x 35:
-# differences, halved slope, edge value and second difference 11, Steps 2-5 21, the Step 4 test 3),
+# counted): the parabolas of the six primitives of one new cell, streamed along the pencil (6 x 32:
+# differences, halved slope, edge value and second difference 11, Steps 2-5 18, the Step 4 test 3),
 # the Riemann solve (Roe average, speeds and eigenvector rows 116; the three wave pairs'
 # domain-of-dependence averages with L q and R s 244) and the fluxes (25)
-FLOPS_PER_EULER_FACE = 595
+FLOPS_PER_EULER_FACE = 577
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one x-direction Eulerian face launch
 # at 128^3, from one ncu capture of this kernel (set to None whenever the kernel changes)
-EULER_FACE_TRAFFIC_BYTES = 330.4e6
+EULER_FACE_TRAFFIC_BYTES = None
 
 
 def reduce_max(x, dist=None, device="cpu"):
