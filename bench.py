@@ -231,6 +231,28 @@ def heatcool_leg(M, I, torch, n=128, steps=10, warm=3):
     return out
 
 
+def ions_leg(M, I, torch, n=128, steps=10, warm=3):
+    """The ionisation network (reactions 5-8 with H+ and e, Sec. 4.3 / App. D) with heating/cooling
+    (Gamma_1-Lambda_8) on the FP64 128^3 turbulence box with 5 % of the hydrogen molecular and an
+    ion fraction of 1e-3: Mcell-updates/s with the ions on and off (heating/cooling on in both), and
+    the post kernel per step."""
+    ic = I.turbulence(n, mach=5.0, beta=1.0, seed=1)
+    ic["rho_h2"] = 0.05 * ic["rho"]
+    ic["rho_hp"] = 1e-3 * ic["rho"]
+    out = {"workload": f"mhd_turbulence_h2chem_ions_heatcool_{n}^3_fp64", "unit": METRIC, "steps": steps,
+           "warmup": warm}
+    for on in (1, 0):
+        s = M.from_ic(ic, heatcool=1, ions=on)
+        ms = timed_steps(torch, s, steps, warm)
+        prof = M.profile(s, CFL, 2)
+        out["on" if on else "off"] = {"value": n ** 3 * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+                                      "post_ms_per_step": prof["post"]["ms_total"] / 2,
+                                      "lag_face_ms_per_step": prof["lag_face"]["ms_total"] / 2}
+        del s
+    out["value"] = out["on"]["value"]
+    return out
+
+
 def gravity_leg(M, I, torch, n=128, steps=10, warm=3):
     """Self-gravity (Sec. 2.10 Poisson solve by cuFFT each step, gravity terms in the Eulerian stage)
     on the FP64 128^3 turbulence box with G in code units (pc, km/s, m_H cm^-3): Mcell-updates/s
@@ -330,7 +352,7 @@ def run_leg(args):
     import paper_1608_08748_gb300 as M
     from paper_1608_08748_gb300 import inputs as I
     fn = {"fp32": fp32_leg, "batched": batched_leg, "serving": serving_leg, "heatcool": heatcool_leg,
-          "gravity": gravity_leg}[args.leg]
+          "gravity": gravity_leg, "ions": ions_leg}[args.leg]
     kw = {"policy": args.serve_policy, "big": args.serving_big} if args.leg == "serving" else {}
     print(json.dumps({args.leg: fn(M, I, torch, **kw)}), flush=True)
 
@@ -438,6 +460,7 @@ def run_ours(args):
         extras["serving"] = serving_leg(M, I, torch, big=args.serving_big, policy=args.serve_policy)
         extras["heatcool"] = heatcool_leg(M, I, torch)
         extras["gravity"] = gravity_leg(M, I, torch)
+        extras["ions"] = ions_leg(M, I, torch)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, secs = oracle_rate(48, 8)
@@ -470,7 +493,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP32-bulk (256^3), batched-ensemble, serving, heating/cooling and gravity legs")
-    ap.add_argument("--leg", choices=["main", "fp32", "batched", "serving", "heatcool", "gravity"],
+    ap.add_argument("--leg", choices=["main", "fp32", "batched", "serving", "heatcool", "gravity", "ions"],
                     default="main",
                     help="run one secondary leg alone (for profiling)")
     ap.add_argument("--serve-policy", choices=["fifo", "smallest_work"], default="fifo",

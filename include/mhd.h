@@ -7,7 +7,8 @@
  *   tau from the CFL rule (Sec. 2.3) -> Eulerian stage, three SSP-RK3 substages (Sec. 2.2) of the
  *   characteristic Riemann solver on piecewise-parabolic data (Sec. 2.1, 2.4, App. A) with Flux-CT
  *   inside each substage (Sec. 2.5, App. C) -> Lagrangian advection stage, three SSP-RK3 substages
- *   (Sec. 2.6) -> H/H2 chemistry (Sec. 2.7, App. D reactions 1-4) -> regularisation (Sec. 2.9).
+ *   (Sec. 2.6) -> H/H2 chemistry (Sec. 2.7, App. D reactions 1-4; 1-8 with H+ and electrons when
+ *   MHD_OPT_IONS is on) -> heating/cooling when on (Sec. 2.8) -> regularisation (Sec. 2.9).
  * Every step runs in CUDA kernels of this library; there is no CPU path.
  *
  * Conventions
@@ -69,13 +70,23 @@ enum mhd_option {
                                 chemistry (needs MHD_OPT_CHEM = 1): rho E and rho eps change by
                                 tau (Gamma_1 + Gamma_4 - Lambda_2 - Lambda_3) of App. D, FP64, the
                                 change limited to at most half of rho eps */
-  MHD_OPT_GRAV_G = 16        /* gravitational constant G in code units (0: no self-gravity, the
+  MHD_OPT_GRAV_G = 16,       /* gravitational constant G in code units (0: no self-gravity, the
                                 default; 1.0635e-4 is G in pc, km/s, m_H cm^-3).  Each step first
                                 solves the Poisson equation of Sec. 2.10 for the density (27-point
                                 scheme in harmonic space, cuFFT, periodic boundaries required) and
                                 the Eulerian stage adds -rho grad Phi and -rho v . grad Phi (central
                                 differences).  Such a sim steps without graph capture and cannot
                                 join a batch. */
+  MHD_OPT_IONS = 17          /* 0 off (default); 1 reactions 5-8 of Sec. 4.3 / App. D with H+ and
+                                electrons (needs MHD_OPT_CHEM = 1): one more advected density
+                                rho_H+ = n_H+ (code density units; n_e = n_H+, neutral
+                                n_H = rho - rho_H2 - rho_H+), gamma_eff counting H, H+ and e as
+                                monatomic particles, and the creation k5 n_H + k6 n_H n_e and
+                                destruction (k7 n_e + k8 n) n_H+ of H+ by the semi-implicit
+                                update of Sec. 2.7 with rates frozen at the stage start, H2
+                                first.  With MHD_OPT_HEATCOOL, Gamma_5 - Lambda_6 - Lambda_7 -
+                                Lambda_8 join the heating/cooling.  mhd_set_state zeroes rho_H+;
+                                mhd_set_ions loads it. */
 };
 
 enum mhd_dtype { MHD_F64 = 0, MHD_F32 = 1 };
@@ -129,6 +140,12 @@ int mhd_get_state(mhd_sim* s, mhd_fields* out);
 int mhd_get_full(mhd_sim* s, double* eint, double* bx, double* by, double* bz, int on_device);
 int mhd_set_full(mhd_sim* s, const double* eint, const double* bx, const double* by,
                  const double* bz, int on_device);
+
+/* rho_H+ (float64, C order, nx*ny*nz values, host or device per on_device) in and out.  Set after
+   mhd_set_state (which zeroes it); recomputes the first tau.  Used by the steps only with
+   MHD_OPT_IONS on.  MHD_EINVAL for a null pointer or (set) no loaded state. */
+int mhd_set_ions(mhd_sim* s, const double* rho_hp, int on_device);
+int mhd_get_ions(mhd_sim* s, double* rho_hp, int on_device);
 
 /* One full step with tau = CFL-limited (Sec. 2.3).  dt_taken may be NULL: then the call only
    enqueues work and does not synchronise (errors of the step surface at the next synchronising

@@ -15,7 +15,9 @@
  *   one step       tau from the CFL rule [Sec. 2.3] (truncated at t_end when asked),
  *                  Eulerian stage with Flux-CT inside each SSP-RK3 substage [Sec. 2.2, 2.4, 2.5,
  *                  App. A, App. C], Lagrangian stage with SSP-RK3 [Sec. 2.6], H/H2 chemistry
- *                  [Sec. 2.7, App. D reactions 1-4], regularisation [Sec. 2.9].
+ *                  [Sec. 2.7, App. D reactions 1-4; with the ion option also reactions 5-8 with
+ *                  H+ and e], heating/cooling when on [Sec. 2.8], regularisation [Sec. 2.9];
+ *                  self-gravity when on [Sec. 2.10].
  *   PPM            local parabola, Steps 1-5 [Sec. 2.1]; domain-of-dependence averages [Sec. 2.4].
  *
  * Readings taken where the paper is garbled or silent (each documented at its use):
@@ -48,6 +50,13 @@
  *   A18 tau = min(tau_CFL, t_end - t) when a target time is given.
  *   A19 code units: 1 pc, m_H cm^-3, 1 km/s.
  *   A23 no positivity floors; rho <= 0, p <= 0 or a non-finite value is reported.
+ *   A24-A31 heating/cooling and self-gravity readings (at their use).
+ *   A32 ions: one more advected density rho_H+ = n_H+ (proton mass = m_H), n_e = n_H+ (charge
+ *       neutrality of pure hydrogen), neutral atoms n_H = rho - rho_H2 - rho_H+.
+ *   A33 gamma_eff of Sec. 4.3 with electrons: its n_H counts every nucleus outside H2 (n_H +
+ *       n_H+), so gamma = (5 n_1 + 7 n_H2) / (3 n_1 + 5 n_H2), n_1 = n_H + n_H+ + n_e; T counts
+ *       every particle, p = (n_H + n_H2 + n_H+ + n_e) k_B T.
+ *   A34-A37 rates of reactions 5-8 (at ion_rates_at); A38 the H+ update; A39 Gamma_5, Lambda_6-8.
  */
 #include <math.h>
 #include <stddef.h>
@@ -73,7 +82,8 @@ enum {
   O_CHEM_TAUD = 11,                   /* dust optical depth per column, cm^2 */
   O_THREADS = 12,
   O_HEATCOOL = 13,                    /* 0 off (default), 1 Sec. 2.8 heating/cooling (needs chemistry) */
-  O_GRAV_G = 14                       /* G in code units for self-gravity (0: off, the default; periodic) */
+  O_GRAV_G = 14,                      /* G in code units for self-gravity (0: off, the default; periodic) */
+  O_IONS = 15                         /* 0 off (default), 1 reactions 5-8 with H+ and e (needs chemistry) */
 };
 
 enum { O_OK = 0, O_EINVAL = -1, O_ENOMEM = -2, O_ENONPHYS = -4 };
@@ -91,19 +101,19 @@ typedef struct {
   size_t next; /* extended cell count */
   int bc[3];
   double gamma, dx;
-  int chem, step4_as_written, iface_edge, regul_mode, threads, heatcool;
+  int chem, step4_as_written, iface_edge, regul_mode, threads, heatcool, ions;
   double lshield, bdop, xnorm, taud;
   double grav_g;     /* gravitational constant in code units (0: no self-gravity) */
   double t;
   long nsteps, nvel_branch;
   /* state on the extended grid */
-  double *rho, *m[3], *E, *eint, *rh2, *b[3];
+  double *rho, *m[3], *E, *eint, *rh2, *rhp, *b[3]; /* rhp: rho_H+ = n_H+ (A32) */
   /* RK register Q^n and scratch */
-  double *rho0, *m0[3], *E0, *eint0, *rh20, *b0[3];
+  double *rho0, *m0[3], *E0, *eint0, *rh20, *rhp0, *b0[3];
   double *w[9];      /* primitives: rho, v0, v1, v2, B0, B1, B2, p, gamma */
-  double *fo[7];     /* face outputs of the current direction */
+  double *fo[8];     /* face outputs of the current direction */
   double *acc[6];    /* accumulated flux differences: m0, m1, m2, E, div v, (rho_H2 / rho) */
-  double *accL[7];   /* Lagrangian accumulators */
+  double *accL[8];   /* Lagrangian accumulators */
   double *eA[3], *eB[3]; /* per-direction EMF contributions of the faces */
   double *edge[3];   /* edge EMFs E_x, E_y, E_z */
   double *phi;       /* gravitational potential (extended grid) */
@@ -381,14 +391,29 @@ static double cfl_denominator(double rho, double vx, double vy, double vz, doubl
 }
 
 /* ---------------------------------------------------------------- Sec. 2 closure + App. D gamma */
-/* effective adiabatic index of the H/H2 mixture (Sec. 4.3, n_e = 0) */
-static double gamma_eff(double rho, double rh2) {
-  double nH = rho - rh2, nH2 = 0.5 * rh2;
-  return (5.0 * nH + 7.0 * nH2) / (3.0 * nH + 5.0 * nH2);
+/* effective adiabatic index of the mixture (Sec. 4.3): gamma = (5 n_1 + 7 n_H2) / (3 n_1 + 5 n_H2)
+   with n_1 the monatomic particles.  With H+ and electrons (A33) n_1 = n_H + n_H+ + n_e, where
+   n_H = rho - rho_H2 - rho_H+ are the neutral atoms, n_H+ = n_e = rho_H+; without them
+   (rho_H+ = 0) n_1 = n_H = rho - rho_H2. */
+static double gamma_eff(double rho, double rh2, double rhp) {
+  double n1 = (rho - rh2 - rhp) + 2.0 * rhp, nH2 = 0.5 * rh2;
+  return (5.0 * n1 + 7.0 * nH2) / (3.0 * n1 + 5.0 * nH2);
 }
 
+static double cell_rhp(const osim* s, size_t c) { return s->ions ? s->rhp[c] : 0.0; }
+
 static double cell_gamma(const osim* s, size_t c) {
-  return s->chem ? gamma_eff(s->rho[c], s->rh2[c]) : s->gamma;
+  return s->chem ? gamma_eff(s->rho[c], s->rh2[c], cell_rhp(s, c)) : s->gamma;
+}
+
+/* temperature of the gas (K) from rho eps (code units) and the composition: p = (gamma - 1) rho eps
+   P0 = (n_H + n_H2 + n_H+ + n_e) k_B T (A15 v, A33) */
+static double temperature(double rho, double eint, double rh2, double rhp) {
+  const double P0 = MH_CGS * KMS_CGS * KMS_CGS; /* code pressure unit, erg cm^-3 */
+  double nH = rho - rh2 - rhp, nH2 = 0.5 * rh2, nHp = rhp, ne = rhp;
+  double g = gamma_eff(rho, rh2, rhp);
+  double p = (g - 1.0) * eint * P0;
+  return p / ((((nH + nH2) + nHp) + ne) * KB_CGS);
 }
 
 /* ---------------------------------------------------------------- allocation */
@@ -412,15 +437,15 @@ osim* osim_create(int nx, int ny, int nz, double gamma, double dx) {
   s->threads = omp_get_max_threads();
 #endif
   size_t n = s->next;
-  double** all[] = {&s->rho, &s->m[0], &s->m[1], &s->m[2], &s->E, &s->eint, &s->rh2, &s->b[0],
-                    &s->b[1], &s->b[2], &s->rho0, &s->m0[0], &s->m0[1], &s->m0[2], &s->E0,
-                    &s->eint0, &s->rh20, &s->b0[0], &s->b0[1], &s->b0[2]};
+  double** all[] = {&s->rho, &s->m[0], &s->m[1], &s->m[2], &s->E, &s->eint, &s->rh2, &s->rhp,
+                    &s->b[0], &s->b[1], &s->b[2], &s->rho0, &s->m0[0], &s->m0[1], &s->m0[2],
+                    &s->E0, &s->eint0, &s->rh20, &s->rhp0, &s->b0[0], &s->b0[1], &s->b0[2]};
   for (size_t i = 0; i < sizeof(all) / sizeof(all[0]); ++i)
     if (!(*all[i] = xalloc(n))) goto fail;
   for (int i = 0; i < 9; ++i) if (!(s->w[i] = xalloc(n))) goto fail;
-  for (int i = 0; i < 7; ++i) if (!(s->fo[i] = xalloc(n))) goto fail;
+  for (int i = 0; i < 8; ++i) if (!(s->fo[i] = xalloc(n))) goto fail;
   for (int i = 0; i < 6; ++i) if (!(s->acc[i] = xalloc(n))) goto fail;
-  for (int i = 0; i < 7; ++i) if (!(s->accL[i] = xalloc(n))) goto fail;
+  for (int i = 0; i < 8; ++i) if (!(s->accL[i] = xalloc(n))) goto fail;
   for (int i = 0; i < 3; ++i)
     if (!(s->eA[i] = xalloc(n)) || !(s->eB[i] = xalloc(n)) || !(s->edge[i] = xalloc(n))) goto fail;
   if (!(s->phi = xalloc(n))) goto fail;
@@ -433,14 +458,14 @@ fail:;
 
 void osim_destroy(osim* s) {
   if (!s) return;
-  double* all[] = {s->rho, s->m[0], s->m[1], s->m[2], s->E, s->eint, s->rh2, s->b[0], s->b[1],
-                   s->b[2], s->rho0, s->m0[0], s->m0[1], s->m0[2], s->E0, s->eint0, s->rh20,
-                   s->b0[0], s->b0[1], s->b0[2]};
+  double* all[] = {s->rho, s->m[0], s->m[1], s->m[2], s->E, s->eint, s->rh2, s->rhp, s->b[0],
+                   s->b[1], s->b[2], s->rho0, s->m0[0], s->m0[1], s->m0[2], s->E0, s->eint0,
+                   s->rh20, s->rhp0, s->b0[0], s->b0[1], s->b0[2]};
   for (size_t i = 0; i < sizeof(all) / sizeof(all[0]); ++i) free(all[i]);
   for (int i = 0; i < 9; ++i) free(s->w[i]);
-  for (int i = 0; i < 7; ++i) free(s->fo[i]);
+  for (int i = 0; i < 8; ++i) free(s->fo[i]);
   for (int i = 0; i < 6; ++i) free(s->acc[i]);
-  for (int i = 0; i < 7; ++i) free(s->accL[i]);
+  for (int i = 0; i < 8; ++i) free(s->accL[i]);
   for (int i = 0; i < 3; ++i) { free(s->eA[i]); free(s->eB[i]); free(s->edge[i]); }
   free(s->phi);
   free(s);
@@ -466,6 +491,7 @@ int osim_set_option(osim* s, int key, double v) {
     case O_THREADS: if (v < 1.0) return O_EINVAL; s->threads = (int)v; return O_OK;
     case O_HEATCOOL: if (v != 0.0 && v != 1.0) return O_EINVAL; s->heatcool = (int)v; return O_OK;
     case O_GRAV_G: if (v < 0.0) return O_EINVAL; s->grav_g = v; return O_OK;
+    case O_IONS: if (v != 0.0 && v != 1.0) return O_EINVAL; s->ions = (int)v; return O_OK;
     default: return O_EINVAL;
   }
 }
@@ -510,6 +536,7 @@ int osim_set_state(osim* s, const double* rho, const double* mx, const double* m
         s->m[2][c] = mz[src];
         s->E[c] = E[src];
         s->rh2[c] = rh2 ? rh2[src] : 0.0;
+        s->rhp[c] = 0.0;
         const int ii[3] = {i, j, k};
         for (int d = 0; d < 3; ++d) {
           /* face d at index ii[d] sits between cells ii[d]-1 and ii[d] */
@@ -593,6 +620,23 @@ int osim_get_full(osim* s, double* eint, double* bx, double* by, double* bz) {
         by[dst] = s->b[1][c];
         bz[dst] = s->b[2][c];
       }
+  return O_OK;
+}
+
+/* rho_H+ (A32) of every cell, C order: set after set_state, which zeroes it */
+int osim_set_ions(osim* s, const double* rhp) {
+  const int nx = s->n[0], ny = s->n[1], nz = s->n[2];
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) s->rhp[IX(s, i + NG, j + NG, k + NG)] = rhp[((size_t)k * ny + j) * nx + i];
+  return O_OK;
+}
+
+int osim_get_ions(osim* s, double* rhp) {
+  const int nx = s->n[0], ny = s->n[1], nz = s->n[2];
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) rhp[((size_t)k * ny + j) * nx + i] = s->rhp[IX(s, i + NG, j + NG, k + NG)];
   return O_OK;
 }
 
@@ -771,11 +815,11 @@ static void eulerian_update(osim* s, double a, double bb, double g, double tau) 
 }
 
 /* ---------------------------------------------------------------- Sec. 2.6 Lagrangian stage */
-/* advected conserved densities q in {rho, m_x, m_y, m_z, rho E, rho eps, rho_H2} */
+/* advected conserved densities q in {rho, m_x, m_y, m_z, rho E, rho eps, rho_H2, rho_H+} */
 static int lag_fields(osim* s, double** q, double** q0) {
-  double* a[7] = {s->rho, s->m[0], s->m[1], s->m[2], s->E, s->eint, s->rh2};
-  double* a0[7] = {s->rho0, s->m0[0], s->m0[1], s->m0[2], s->E0, s->eint0, s->rh20};
-  int nv = s->chem ? 7 : 6;
+  double* a[8] = {s->rho, s->m[0], s->m[1], s->m[2], s->E, s->eint, s->rh2, s->rhp};
+  double* a0[8] = {s->rho0, s->m0[0], s->m0[1], s->m0[2], s->E0, s->eint0, s->rh20, s->rhp0};
+  int nv = s->chem ? (s->ions ? 8 : 7) : 6;
   for (int v = 0; v < nv; ++v) {
     q[v] = a[v];
     q0[v] = a0[v];
@@ -785,7 +829,7 @@ static int lag_fields(osim* s, double** q, double** q0) {
 
 static void lagrangian_rhs(osim* s, double tau_h) {
   const int* n = s->n;
-  double *q[7], *q0[7];
+  double *q[8], *q0[8];
   const int nv = lag_fields(s, q, q0);
   for (int v = 0; v < nv; ++v) fill_ghosts(s, q[v]);
   for (int v = 0; v < nv; ++v) memset(s->accL[v], 0, s->next * sizeof(double));
@@ -830,7 +874,7 @@ static void lagrangian_rhs(osim* s, double tau_h) {
 static void lagrangian_update(osim* s, double a, double bb, double g, double tau) {
   const int* n = s->n;
   const double ih = 1.0 / s->dx;
-  double *q[7], *q0[7];
+  double *q[8], *q0[8];
   const int nv = lag_fields(s, q, q0);
 #pragma omp parallel for schedule(static) num_threads(s->threads)
   for (int k = 0; k < n[2]; ++k)
@@ -876,21 +920,64 @@ static chem_rates chem_rates_at(const osim* s, double T, double nH, double nH2, 
   return r;
 }
 
-/* one cell: returns the new rho_H2; rates are evaluated once from the state at stage start */
-static double chem_cell(const osim* s, double rho, double eint, double rh2, double tau,
-                        chem_rates* out) {
-  const double P0 = MH_CGS * KMS_CGS * KMS_CGS; /* code pressure unit, erg cm^-3 */
-  const double T0 = PC_CGS / KMS_CGS;           /* code time unit, s */
-  double nH = rho - rh2, nH2 = 0.5 * rh2, n = rho;
-  double g = gamma_eff(rho, rh2);
-  double p = (g - 1.0) * eint * P0;
-  double T = p / ((nH + nH2) * KB_CGS);
+/* App. D rates of reactions 5-8 (H+ and e) at temperature T (K), readings A34-A37:
+   k5 = 6e-18 s^-1 per H atom (cosmic-ray ionisation; the printed density factor read as a stray,
+        as Gamma_5 = 1.92e-28 n = k5 x 20 eV x n shows);
+   k6 = exp(sum_j c_j (ln T_eV)^j), j = 0..8, the collisional ionisation fit in the natural logarithm
+        of the temperature in eV;
+   k7 = 10^(P(x) / Q(x)), x = log10 T, the printed quartics;
+   k8 = the printed grain-recombination fit, log = log10, "a(-b)" = a 10^-b;
+   creation and destruction of H+ per unit volume: C = k5 n_H + k6 n_H n_e, D n_H+ with
+   D = k7 n_e + k8 n (A38). */
+typedef struct { double k5, k6, k7, k8, C, D; } ion_rates;
+
+static ion_rates ion_rates_at(double T, double nH, double ne, double n) {
+  static const double c6[9] = {-32.7, 13.5, -5.7, 1.5, -0.3, 3.4e-2, -2.6e-3, 1.1e-4, -2.1e-6};
+  ion_rates r;
+  r.k5 = 6e-18;
+  double L = log(T * KB_EV), acc = 0.0, Lj = 1.0;
+  for (int j = 0; j < 9; ++j) {
+    acc += c6[j] * Lj;
+    Lj *= L;
+  }
+  r.k6 = exp(acc);
+  double x = log10(T);
+  double P = -10.78 + 4.68 * x - 0.87 * x * x + 0.08 * x * x * x - 3.87e-3 * x * x * x * x;
+  double Q = 1.0 - 0.38 * x + 0.06 * x * x - 5.1e-3 * x * x * x + 2.4e-4 * x * x * x * x;
+  r.k7 = pow(10.0, P / Q);
+  r.k8 = 12.25e-14 / (1.0 + 8.074e-6 * pow(10.0, 2.756) *
+                                (1.0 + 5.087e2 * pow(T, 1.586e-2) * pow(10.0, -1.8892 - 4.4e-5 * log10(T))));
+  r.C = r.k5 * nH + r.k6 * nH * ne;
+  r.D = r.k7 * ne + r.k8 * n;
+  return r;
+}
+
+/* one cell (Sec. 2.7): returns the new rho_H2 and, with the ions on, stores the new rho_H+ in
+   *rhp_new.  The rates are evaluated once from the state at stage start (A15, A38); each species
+   takes the printed semi-implicit update n' = n + tau (C - D n) / (1 + tau D): H2 first, then H+ from
+   the stage-start n_H and n_e; n_H = n - 2 n_H2 - n_H+ and n_e = n_H+ close the composition. */
+static double chem_cell(const osim* s, double rho, double eint, double rh2, double rhp, double tau,
+                        chem_rates* out, ion_rates* iout, double* rhp_new) {
+  const double T0 = PC_CGS / KMS_CGS; /* code time unit, s */
+  double nH = rho - rh2 - rhp, nH2 = 0.5 * rh2, n = rho;
+  double T = temperature(rho, eint, rh2, rhp);
   chem_rates r = chem_rates_at(s, T, nH, nH2, n);
   double ts = tau * T0;
   double nH2n = nH2 + ts * (r.C - r.D * nH2) / (1.0 + ts * r.D);
   if (nH2n < 0.0) nH2n = 0.0;
   if (nH2n > 0.5 * n) nH2n = 0.5 * n;
   if (out) *out = r;
+  if (s->ions) {
+    double nHp = rhp, ne = rhp;
+    ion_rates q = ion_rates_at(T, nH, ne, n);
+    double nHpn = nHp + ts * (q.C - q.D * nHp) / (1.0 + ts * q.D);
+    if (nHpn < 0.0) nHpn = 0.0;
+    if (nHpn > n - 2.0 * nH2n) nHpn = n - 2.0 * nH2n;
+    if (iout) *iout = q;
+    if (rhp_new) *rhp_new = nHpn;
+  } else if (rhp_new) {
+    *rhp_new = rhp;
+  }
   return 2.0 * nH2n;
 }
 
@@ -901,7 +988,9 @@ static void chemistry(osim* s, double tau) {
     for (int j = 0; j < n[1]; ++j)
       for (int i = 0; i < n[0]; ++i) {
         size_t c = IX(s, i + NG, j + NG, k + NG);
-        s->rh2[c] = chem_cell(s, s->rho[c], s->eint[c], s->rh2[c], tau, NULL);
+        double rhp = cell_rhp(s, c);
+        s->rh2[c] = chem_cell(s, s->rho[c], s->eint[c], s->rh2[c], rhp, tau, NULL, NULL, &rhp);
+        if (s->ions) s->rhp[c] = rhp;
       }
 }
 
@@ -917,20 +1006,23 @@ static void chemistry(osim* s, double tau) {
      L_L = 8.18e-13 (n_H k_H + n_H2 k_H2), k_H2 = 6.29e-15 x 1.38 f(T) / f(4500),
      f(T) = sqrt(T) a exp(a), a = 1 + 1 / (k_B T) with k_B in eV/K, and k_H = k_H2 (A27);
    - Gamma_4 = 6.4e-13 erg x k4 n_H2 (A28);
-   x = log10(T / 1e4) throughout (A15 iv). */
-typedef struct { double T, G1, L2, L3, G4, net; } heatcool_terms;
+   with the ions on (A39), also
+   - Gamma_5 = 1.92e-28 n (cosmic-ray heating, as printed);
+   - Lambda_6 = 2.18e-11 erg x k6 n_H n_e (13.6 eV per collisional ionisation);
+   - Lambda_7 = 4.65e-30 T^0.94 psi^(0.74 / T^0.068) n_e n_H+, psi = exp(-0.75e-20 (N_H + N_H2))
+     sqrt(T) / n_e (the printed sqrt(t) read as sqrt(T)), 0 where n_e = 0;
+   - Lambda_8 = 5.7e-26 (T / 1e4)^0.8 n_e n_H+;
+   x = log10(T / 1e4) throughout (A15 iv); n_H the neutral atoms. */
+typedef struct { double T, G1, L2, L3, G4, G5, L6, L7, L8, net; } heatcool_terms;
 
 static double log_f_A27(double T) {
   double a = 1.0 + 1.0 / (KB_EV * T);
   return 0.5 * log(T) + log(a) + a;
 }
 
-static heatcool_terms heatcool_at(const osim* s, double rho, double eint, double rh2) {
-  const double P0 = MH_CGS * KMS_CGS * KMS_CGS;
-  double nH = rho - rh2, nH2 = 0.5 * rh2, n = rho;
-  double g = gamma_eff(rho, rh2);
-  double p = (g - 1.0) * eint * P0;
-  double T = p / ((nH + nH2) * KB_CGS);
+static heatcool_terms heatcool_at(const osim* s, double rho, double eint, double rh2, double rhp) {
+  double nH = rho - rh2 - rhp, nH2 = 0.5 * rh2, n = rho;
+  double T = temperature(rho, eint, rh2, rhp);
   chem_rates r = chem_rates_at(s, T, nH, nH2, n);
   double x = log10(T / 1e4);
   heatcool_terms h;
@@ -950,17 +1042,30 @@ static heatcool_terms heatcool_at(const osim* s, double rho, double eint, double
   h.L3 = nH2 * LH3 / (1.0 + LH3 / LL3);
   /* Gamma_4 (A28) */
   h.G4 = 6.4e-13 * r.k4 * nH2;
-  h.net = (h.G1 + h.G4) - (h.L2 + h.L3);
+  h.G5 = h.L6 = h.L7 = h.L8 = 0.0;
+  if (s->ions) {
+    double nHp = rhp, ne = rhp;
+    ion_rates q = ion_rates_at(T, nH, ne, n);
+    h.G5 = 1.92e-28 * n;
+    h.L6 = 2.18e-11 * q.k6 * nH * ne;
+    if (ne > 0.0) {
+      double Ls = (s->lshield > 0.0 ? s->lshield : s->dx) * PC_CGS;
+      double psi = exp(-0.75e-20 * (nH * Ls + nH2 * Ls)) * sqrt(T) / ne;
+      h.L7 = 4.65e-30 * pow(T, 0.94) * pow(psi, 0.74 / pow(T, 0.068)) * ne * nHp;
+    }
+    h.L8 = 5.7e-26 * pow(T / 1e4, 0.8) * ne * nHp;
+  }
+  h.net = (h.G1 + h.G4 + h.G5) - (h.L2 + h.L3 + h.L6 + h.L7 + h.L8);
   return h;
 }
 
 /* Sec. 2.8: d(rho E)/dt = d(rho eps)/dt = Gamma - Lambda by one Euler step; returns the change of
    rho E and rho eps in code units, limited so that rho eps keeps at least half its value (A29) */
-static double heatcool_delta(const osim* s, double rho, double eint, double rh2, double tau,
-                             heatcool_terms* out) {
+static double heatcool_delta(const osim* s, double rho, double eint, double rh2, double rhp,
+                             double tau, heatcool_terms* out) {
   const double P0 = MH_CGS * KMS_CGS * KMS_CGS; /* code energy density unit, erg cm^-3 */
   const double T0 = PC_CGS / KMS_CGS;           /* code time unit, s */
-  heatcool_terms h = heatcool_at(s, rho, eint, rh2);
+  heatcool_terms h = heatcool_at(s, rho, eint, rh2, rhp);
   double d = tau * T0 * h.net / P0;
   if (d < -0.5 * eint) d = -0.5 * eint;
   if (out) *out = h;
@@ -974,7 +1079,7 @@ static void heatcool(osim* s, double tau) {
     for (int j = 0; j < n[1]; ++j)
       for (int i = 0; i < n[0]; ++i) {
         size_t c = IX(s, i + NG, j + NG, k + NG);
-        double d = heatcool_delta(s, s->rho[c], s->eint[c], s->rh2[c], tau, NULL);
+        double d = heatcool_delta(s, s->rho[c], s->eint[c], s->rh2[c], cell_rhp(s, c), tau, NULL);
         s->E[c] = s->E[c] + d;
         s->eint[c] = s->eint[c] + d;
       }
@@ -1028,6 +1133,7 @@ static void save_Qn(osim* s, int lagrangian) {
   if (lagrangian) {
     memcpy(s->rho0, s->rho, bytes);
     memcpy(s->rh20, s->rh2, bytes);
+    memcpy(s->rhp0, s->rhp, bytes);
   } else {
     for (int d = 0; d < 3; ++d) memcpy(s->b0[d], s->b[d], bytes);
   }
@@ -1147,7 +1253,7 @@ static int check_physical(osim* s) {
       for (int i = 0; i < n[0]; ++i) {
         size_t c = IX(s, i + NG, j + NG, k + NG);
         double v[] = {s->rho[c], s->m[0][c], s->m[1][c], s->m[2][c], s->E[c], s->eint[c], s->rh2[c],
-                      s->b[0][c], s->b[1][c], s->b[2][c]};
+                      s->rhp[c], s->b[0][c], s->b[1][c], s->b[2][c]};
         for (size_t q = 0; q < sizeof(v) / sizeof(v[0]); ++q)
           if (!isfinite(v[q])) bad = 1;
         if (!(s->rho[c] > 0.0) || !(s->eint[c] > 0.0)) bad = 1;
@@ -1290,13 +1396,17 @@ double o_cfl_denominator(const double w[9]) {
   return cfl_denominator(w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7], w[8]);
 }
 
-double o_gamma_eff(double rho, double rh2) { return gamma_eff(rho, rh2); }
+double o_gamma_eff(double rho, double rh2) { return gamma_eff(rho, rh2, 0.0); }
+double o_gamma_eff_ions(double rho, double rh2, double rhp) { return gamma_eff(rho, rh2, rhp); }
+double o_temperature(double rho, double eint, double rh2, double rhp) {
+  return temperature(rho, eint, rh2, rhp);
+}
 
 /* chemistry of one cell with the simulation's parameters:
    out = (rho_H2 new, T, k1', k2, k3, k4, C, D) */
 void osim_chem_cell(const osim* s, double rho, double eint, double rh2, double tau, double out[8]) {
   chem_rates r;
-  out[0] = chem_cell(s, rho, eint, rh2, tau, &r);
+  out[0] = chem_cell(s, rho, eint, rh2, 0.0, tau, &r, NULL, NULL);
   out[1] = r.T;
   out[2] = r.k1p;
   out[3] = r.k2;
@@ -1321,7 +1431,7 @@ int osim_potential(osim* s, double* out) {
    out = (change of rho E and rho eps in code units, T, Gamma_1, Lambda_2, Lambda_3, Gamma_4, net) */
 void osim_heatcool_cell(const osim* s, double rho, double eint, double rh2, double tau, double out[7]) {
   heatcool_terms h;
-  out[0] = heatcool_delta(s, rho, eint, rh2, tau, &h);
+  out[0] = heatcool_delta(s, rho, eint, rh2, 0.0, tau, &h);
   out[1] = h.T;
   out[2] = h.G1;
   out[3] = h.L2;
@@ -1335,4 +1445,33 @@ void osim_chem_rates(const osim* s, double T, double nH, double nH2, double out[
   chem_rates r = chem_rates_at(s, T, nH, nH2, nH + 2.0 * nH2);
   double v[7] = {r.k1p, r.k2, r.k3, r.k4, r.C, r.D, r.T};
   for (int k = 0; k < 7; ++k) out[k] = v[k];
+}
+
+/* chemistry of one cell with H+ (the sim's ion option decides whether reactions 5-8 run):
+   out = (rho_H2 new, rho_H+ new, T, k1', k2, k3, k4, C, D, k5, k6, k7, k8, C_H+, D_H+) */
+void osim_chem_cell_ions(const osim* s, double rho, double eint, double rh2, double rhp, double tau,
+                         double out[15]) {
+  chem_rates r;
+  ion_rates q = {0, 0, 0, 0, 0, 0};
+  double rhpn = rhp;
+  out[0] = chem_cell(s, rho, eint, rh2, rhp, tau, &r, &q, &rhpn);
+  double v[14] = {rhpn, r.T, r.k1p, r.k2, r.k3, r.k4, r.C, r.D, q.k5, q.k6, q.k7, q.k8, q.C, q.D};
+  for (int k = 0; k < 14; ++k) out[k + 1] = v[k];
+}
+
+/* App. D rates of reactions 5-8 at a given temperature and composition: out = (k5, k6, k7, k8, C, D) */
+void o_ion_rates(double T, double nH, double ne, double n, double out[6]) {
+  ion_rates q = ion_rates_at(T, nH, ne, n);
+  double v[6] = {q.k5, q.k6, q.k7, q.k8, q.C, q.D};
+  for (int k = 0; k < 6; ++k) out[k] = v[k];
+}
+
+/* heating/cooling of one cell with H+: out = (change of rho E and rho eps in code units, T, Gamma_1,
+   Lambda_2, Lambda_3, Gamma_4, Gamma_5, Lambda_6, Lambda_7, Lambda_8, net) */
+void osim_heatcool_cell_ions(const osim* s, double rho, double eint, double rh2, double rhp,
+                             double tau, double out[11]) {
+  heatcool_terms h;
+  out[0] = heatcool_delta(s, rho, eint, rh2, rhp, tau, &h);
+  double v[10] = {h.T, h.G1, h.L2, h.L3, h.G4, h.G5, h.L6, h.L7, h.L8, h.net};
+  for (int k = 0; k < 10; ++k) out[k + 1] = v[k];
 }

@@ -26,7 +26,7 @@ _lib = None
 OPT = {
     "bc_x": 1, "bc_y": 2, "bc_z": 3, "chem": 4, "step4_as_written": 5, "iface_edge": 6,
     "regul_mode": 7, "chem_lshield": 8, "chem_bdop": 9, "chem_xnorm": 10, "chem_taud": 11,
-    "threads": 12, "heatcool": 13, "grav_g": 14,
+    "threads": 12, "heatcool": 13, "grav_g": 14, "ions": 15,
 }
 OK, EINVAL, ENOMEM, ENONPHYS = 0, -1, -2, -4
 
@@ -83,6 +83,15 @@ def lib():
         L.osim_heatcool_cell.argtypes = [vp, d, d, d, d, _dp]
         L.osim_potential.argtypes = [vp, _dp]
         L.osim_chem_rates.argtypes = [vp, d, d, d, _dp]
+        L.osim_set_ions.argtypes = [vp, _dp]
+        L.osim_get_ions.argtypes = [vp, _dp]
+        L.osim_chem_cell_ions.argtypes = [vp, d, d, d, d, d, _dp]
+        L.osim_heatcool_cell_ions.argtypes = [vp, d, d, d, d, d, _dp]
+        L.o_ion_rates.argtypes = [d, d, d, d, _dp]
+        L.o_gamma_eff_ions.restype = d
+        L.o_gamma_eff_ions.argtypes = [d, d, d]
+        L.o_temperature.restype = d
+        L.o_temperature.argtypes = [d, d, d, d]
         _lib = L
     return _lib
 
@@ -201,6 +210,29 @@ class Sim:
         self.L.osim_chem_rates(self.h, float(T), float(nH), float(nH2), out)
         return dict(zip(["k1p", "k2", "k3", "k4", "C", "D", "T"], out))
 
+    def set_ions(self, rho_hp):
+        """rho_H+ (= n_H+, code density units) of every cell; call after set_state."""
+        self.L.osim_set_ions(self.h, _f64(rho_hp).reshape(-1))
+
+    def get_ions(self):
+        out = np.zeros(self.shape)
+        self.L.osim_get_ions(self.h, out.reshape(-1))
+        return out
+
+    def chem_cell_ions(self, rho, eint, rh2, rhp, tau):
+        """Sec. 2.7 chemistry of one cell with H+ (reactions 5-8 when the ions option is on)."""
+        out = np.zeros(15)
+        self.L.osim_chem_cell_ions(self.h, float(rho), float(eint), float(rh2), float(rhp), float(tau), out)
+        keys = ["rho_h2", "rho_hp", "T", "k1p", "k2", "k3", "k4", "C", "D", "k5", "k6", "k7", "k8",
+                "C_hp", "D_hp"]
+        return dict(zip(keys, out))
+
+    def heatcool_cell_ions(self, rho, eint, rh2, rhp, tau):
+        out = np.zeros(11)
+        self.L.osim_heatcool_cell_ions(self.h, float(rho), float(eint), float(rh2), float(rhp), float(tau), out)
+        keys = ["delta", "T", "G1", "L2", "L3", "G4", "G5", "L6", "L7", "L8", "net"]
+        return dict(zip(keys, out))
+
 
 def ppm(q5, step4_as_written=False):
     out = np.zeros(4)
@@ -230,8 +262,22 @@ def cfl_denominator(rho, v, B, p, gam):
     return lib().o_cfl_denominator(_f64([rho, v[0], v[1], v[2], B[0], B[1], B[2], p, gam]))
 
 
-def gamma_eff(rho, rh2):
-    return lib().o_gamma_eff(float(rho), float(rh2))
+def gamma_eff(rho, rh2, rhp=None):
+    if rhp is None:
+        return lib().o_gamma_eff(float(rho), float(rh2))
+    return lib().o_gamma_eff_ions(float(rho), float(rh2), float(rhp))
+
+
+def temperature(rho, eint, rh2, rhp=0.0):
+    """Gas temperature (K) of a cell in code units (rho in m_H cm^-3, rho eps in m_H cm^-3 km^2/s^2)."""
+    return lib().o_temperature(float(rho), float(eint), float(rh2), float(rhp))
+
+
+def ion_rates(T, nH, ne, n):
+    """App. D rates of reactions 5-8 and the H+ creation / destruction terms."""
+    out = np.zeros(6)
+    lib().o_ion_rates(float(T), float(nH), float(ne), float(n), out)
+    return dict(zip(["k5", "k6", "k7", "k8", "C", "D"], out))
 
 
 def run(ic, steps=None, t_end=None, cfl=0.4, **options):
@@ -241,6 +287,8 @@ def run(ic, steps=None, t_end=None, cfl=0.4, **options):
     opts.update(options)
     s = Sim(nx, ny, nz, ic["gamma"], ic["dx"], **opts)
     s.set_state(ic["rho"], ic["mom"], ic["E"], ic["B"], ic.get("rho_h2"))
+    if ic.get("rho_hp") is not None:
+        s.set_ions(ic["rho_hp"])
     if "bface" in ic:
         s.set_face_B(*ic["bface"])
     if t_end is not None:

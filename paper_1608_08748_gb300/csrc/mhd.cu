@@ -43,8 +43,8 @@ size_t pool_size(const Geom& g, int precision, int chem) {
   (void)chem;
   size_t es = precision ? sizeof(float) : sizeof(double);
   size_t cells = (size_t)g.N, faces = (size_t)g.NF;
-  // state 10, Q^n 10, primitives 9 (cells); face outputs 3 x 7 and edges 3 (lattice)
-  return es * (cells * 29 + faces * 24) + 64 * 64;
+  // state 11, Q^n 11, primitives 9 (cells); face outputs 3 x 8 and edges 3 (lattice)
+  return es * (cells * 31 + faces * 27) + 64 * 64;
 }
 
 // lay the box's arrays out in the pool and fill its descriptor
@@ -65,6 +65,7 @@ void carve(mhd_sim* S, Box<T>& B) {
     s->E = take(N);
     s->eint = take(N);
     s->rh2 = take(N);
+    s->rhp = take(N);
     for (int d = 0; d < 3; ++d) s->b[d] = take(N);
   }
   for (int d = 0; d < 3; ++d) B.w.v[d] = take(N);
@@ -73,13 +74,13 @@ void carve(mhd_sim* S, Box<T>& B) {
   B.w.g = take(N);
   B.w.sr = take(N);
   for (int d = 0; d < 3; ++d)
-    for (int v = 0; v < 7; ++v) B.fo[d].f[v] = take(NF);
+    for (int v = 0; v < 8; ++v) B.fo[d].f[v] = take(NF);
   for (int d = 0; d < 3; ++d) B.e[d] = take(NF);
   B.phi = nullptr;
   B.g = S->g;
   B.ph = S->ph;
   B.sc = S->sc;
-  B.nv = S->ph.chem ? 7 : 6;
+  B.nv = S->ph.chem ? (S->ph.ions ? 8 : 7) : 6;
 }
 
 // (re)build the single-box executor after a change of options
@@ -88,7 +89,7 @@ int rebuild_exec(mhd_sim* S, Box<T>& B, Exec<T>& X) {
   B.g = S->g;
   B.ph = S->ph;
   B.sc = S->sc;
-  B.nv = S->ph.chem ? 7 : 6;
+  B.nv = S->ph.chem ? (S->ph.ions ? 8 : 7) : 6;
   exec_free(X);
   X.prof = &S->prof;
   cudaError_t e = exec_init(X, std::vector<Box<T>>{B});
@@ -258,6 +259,7 @@ mhd_sim* mhd_create(int nx, int ny, int nz, double gamma, double dx) {
   S->ph.taud = 1e-21;
   S->ph.heatcool = 0;
   S->ph.grav_g = 0.0;
+  S->ph.ions = 0;
   auto bail = [&](const char* what, cudaError_t e) {
     fail(e == cudaErrorMemoryAllocation ? MHD_ENOMEM : MHD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     mhd_destroy(S);
@@ -358,6 +360,10 @@ int mhd_set_option(mhd_sim* S, int key, double v) {
     case MHD_OPT_GRAV_G:
       if (!(v >= 0.0)) return fail(MHD_EINVAL, "the gravitational constant must be >= 0");
       S->ph.grav_g = v;
+      break;
+    case MHD_OPT_IONS:
+      if (v != 0.0 && v != 1.0) return fail(MHD_EINVAL, "ions must be 0 (off) or 1 (on)");
+      S->ph.ions = (int)v;
       break;
     default:
       return fail(MHD_EINVAL, "unknown option key " + std::to_string(key));
@@ -474,6 +480,32 @@ int mhd_get_full(mhd_sim* S, double* eint, double* bx, double* by, double* bz, i
   CK(S->precision ? store_full(S, S->b32, dev) : store_full(S, S->b64, dev));
   if (!on_device)
     for (int q = 0; q < 4; ++q) CK(cudaMemcpyAsync(dst[q], dev[q], bytes, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return MHD_OK;
+}
+
+int mhd_get_ions(mhd_sim* S, double* rho_hp, int on_device) {
+  if (!valid(S) || !rho_hp) return fail(MHD_EINVAL, "mhd_get_ions: null argument");
+  const size_t bytes = (size_t)S->g.N * 8;
+  double* dev = on_device ? rho_hp : (double*)S->staging;
+  CK(S->precision ? store_ions(S, S->b32, dev) : store_ions(S, S->b64, dev));
+  if (!on_device) CK(cudaMemcpyAsync(rho_hp, dev, bytes, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return MHD_OK;
+}
+
+int mhd_set_ions(mhd_sim* S, const double* rho_hp, int on_device) {
+  if (!valid(S) || !rho_hp) return fail(MHD_EINVAL, "mhd_set_ions: null argument");
+  if (!S->has_state) return fail(MHD_EINVAL, "mhd_set_ions: load a state first (mhd_set_state zeroes rho_H+)");
+  const size_t bytes = (size_t)S->g.N * 8;
+  const double* dev = rho_hp;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(S->staging, rho_hp, bytes, cudaMemcpyHostToDevice, S->stream));
+    dev = (const double*)S->staging;
+  }
+  CK(S->precision ? load_ions(S, S->b32, dev) : load_ions(S, S->b64, dev));
+  int rc = refresh_cfl(S);  // gamma_eff, hence the sound speed, depends on rho_H+
+  if (rc != MHD_OK) return rc;
   CK(cudaStreamSynchronize(S->stream));
   return MHD_OK;
 }

@@ -33,6 +33,7 @@ struct Phys {
   double ibdop, ixnorm;  // 1 / bdop, 1 / xnorm
   int heatcool;          // Sec. 2.8 heating/cooling stage on (needs chem)
   double grav_g;         // gravitational constant in code units (0: no self-gravity)
+  int ions;              // reactions 5-8 with H+ and electrons on (needs chem)
 };
 
 // Device-resident scalars of a simulation: tau never crosses to the host inside a step.
@@ -54,6 +55,7 @@ struct State {
   T* E;
   T* eint;
   T* rh2;  // may be unused when chemistry is off
+  T* rhp;  // rho_H+ = n_H+ = n_e; used when the ions are on
   T* b[3];
 };
 
@@ -542,6 +544,14 @@ __device__ __forceinline__ T gamma_eff(T rho, T rh2) {
   return (T(5) * nH + T(7) * nH2) / (T(3) * nH + T(5) * nH2);
 }
 
+// ... and with H+ and electrons: the monatomic particles n_1 = n_H + n_H+ + n_e replace n_H, with
+// the neutral atoms n_H = rho - rho_H2 - rho_H+ and n_H+ = n_e = rho_H+ (rho_H+ = 0: the form above)
+template <typename T>
+__device__ __forceinline__ T gamma_eff(T rho, T rh2, T rhp) {
+  T n1 = (rho - rh2 - rhp) + T(2) * rhp, nH2 = T(0.5) * rh2;
+  return (T(5) * n1 + T(7) * nH2) / (T(3) * n1 + T(5) * nH2);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Sec. 2.7 + App. D: one cell of the H/H2 network (reactions 1-4), backward-differentiation
 // update of n_H2 with rates frozen over the step; returns the new rho_H2.  FP64.
@@ -554,16 +564,56 @@ struct ChemConst {
 
 // The App. D formulas in FP64 with few divisions (the rates agree with a term-by-term evaluation to
 // about 1e-14 relative):
-//   T = (gamma - 1) rho eps P0 / ((n_H + n_H2) k_B) with gamma - 1 = 2 (n_H + n_H2) / (3 n_H + 5 n_H2)
-//     = 2 P0 rho eps / ((3 n_H + 5 n_H2) k_B), and T, 1/T from one reciprocal of the product;
+//   T = (gamma - 1) rho eps P0 / (n_particles k_B) with gamma - 1 = 2 n_particles / (3 n_1 + 5 n_H2)
+//     = 2 P0 rho eps / ((3 n_1 + 5 n_H2) k_B), n_1 = n_H + n_H+ + n_e, and T, 1/T from one
+//     reciprocal of the product;
 //   1/sqrt(1 + x) from one reciprocal square root; 1/x_norm and 1/b_doppler precomputed.
-__device__ __forceinline__ double chem_cell(const Phys& ph, double rho, double eint, double rh2,
-                                            double tau) {
+struct ChemOut {
+  double rh2, rhp;  // new rho_H2 and rho_H+
+};
+
+// App. D rates of reactions 5-8 at T (ln T given): k5 = 6e-18 s^-1 per atom, k6 = exp(poly(ln T_eV))
+// (Horner), k7 = 10^(P(x) / Q(x)) with x = log10 T, k8 the grain-recombination fit with
+// T^0.01586 10^(-4.4e-5 log10 T) = T^(0.01586 - 4.4e-5).
+struct IonRates {
+  double k5, k6, k7, k8;
+};
+__device__ __forceinline__ IonRates ion_rates(double lnT) {
+  const double LN_KB_EV = -9.359149794515579;  // ln(8.617333262e-5 eV/K)
+  const double INV_LN10 = 0.43429448190325176;
+  IonRates r;
+  r.k5 = 6e-18;
+  const double L = lnT + LN_KB_EV;
+  double p = -2.1e-6;
+  p = fma(p, L, 1.1e-4);
+  p = fma(p, L, -2.6e-3);
+  p = fma(p, L, 3.4e-2);
+  p = fma(p, L, -0.3);
+  p = fma(p, L, 1.5);
+  p = fma(p, L, -5.7);
+  p = fma(p, L, 13.5);
+  p = fma(p, L, -32.7);
+  r.k6 = exp(p);
+  const double x = lnT * INV_LN10;
+  const double P = fma(fma(fma(fma(-3.87e-3, x, 0.08), x, -0.87), x, 4.68), x, -10.78);
+  const double Q = fma(fma(fma(fma(2.4e-4, x, -5.1e-3), x, 0.06), x, -0.38), x, 1.0);
+  r.k7 = exp10(P / Q);
+  const double A = 8.074e-6 * 570.1642722807472;  // 8.074e-6 10^2.756
+  const double Bc = 5.087e2 * 0.012906247820605376;  // 5.087e2 10^-1.8892
+  r.k8 = 12.25e-14 / (1.0 + A * (1.0 + Bc * exp((1.586e-2 - 4.4e-5) * lnT)));
+  return r;
+}
+
+// IONS: the kernel may see boxes with the ions on (ph.ions decides per box); without it the ion
+// code is compiled out and rhp must be 0.
+template <bool IONS>
+__device__ __forceinline__ ChemOut chem_cell(const Phys& ph, double rho, double eint, double rh2,
+                                             double rhp, double tau) {
   const double P0 = ChemConst::MH * ChemConst::KMS * ChemConst::KMS;  // code pressure, erg cm^-3
   const double T0 = ChemConst::PC / ChemConst::KMS;                  // code time, s
-  const double nH = rho - rh2, nH2 = 0.5 * rh2, n = rho;
+  const double nH = IONS ? rho - rh2 - rhp : rho - rh2, nH2 = 0.5 * rh2, n = rho;
   const double num = (2.0 * P0) * eint;
-  const double den = (3.0 * nH + 5.0 * nH2) * ChemConst::KB;
+  const double den = (3.0 * (IONS ? nH + 2.0 * rhp : nH) + 5.0 * nH2) * ChemConst::KB;
   const double r = 1.0 / (num * den);
   const double T = (num * num) * r, iT = (den * den) * r;
   // App. D rates
@@ -590,7 +640,22 @@ __device__ __forceinline__ double chem_cell(const Phys& ph, double rho, double e
   double nH2n = nH2 + ts * (C - D * nH2) / (1.0 + ts * D);
   if (nH2n < 0.0) nH2n = 0.0;
   if (nH2n > 0.5 * n) nH2n = 0.5 * n;
-  return 2.0 * nH2n;
+  ChemOut out;
+  out.rh2 = 2.0 * nH2n;
+  out.rhp = rhp;
+  if (IONS && ph.ions) {
+    // reactions 5-8: creation k5 n_H + k6 n_H n_e, destruction (k7 n_e + k8 n) n_H+, the same
+    // semi-implicit update from the stage-start densities; n_H+ <= n - 2 n_H2 (n_H >= 0)
+    const double ne = rhp;
+    const IonRates q = ion_rates(log(T));
+    const double Ci = (q.k5 + q.k6 * ne) * nH;
+    const double Di = q.k7 * ne + q.k8 * n;
+    double nHpn = rhp + ts * (Ci - Di * rhp) / (1.0 + ts * Di);
+    if (nHpn < 0.0) nHpn = 0.0;
+    if (nHpn > n - 2.0 * nH2n) nHpn = n - 2.0 * nH2n;
+    out.rhp = nHpn;
+  }
+  return out;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -607,13 +672,14 @@ __device__ __forceinline__ double chem_cell(const Phys& ph, double rho, double e
 //   x = log10(T / 1e4); T, k1' and k4 as in chem_cell, from the state after the chemistry update;
 //   the change is limited to at most half of rho eps (the explicit step of a cooling time shorter
 //   than tau would drive rho eps negative).
+template <bool IONS>
 __device__ __forceinline__ double heatcool_delta(const Phys& ph, double rho, double eint, double rh2,
-                                                 double tau) {
+                                                 double rhp, double tau) {
   const double P0 = ChemConst::MH * ChemConst::KMS * ChemConst::KMS;  // erg cm^-3
   const double T0 = ChemConst::PC / ChemConst::KMS;                  // s
   const double KB_EV = 8.617333262e-5;                               // eV / K
-  const double nH = rho - rh2, nH2 = 0.5 * rh2, n = rho;
-  const double T = ((2.0 * P0) * eint) / ((3.0 * nH + 5.0 * nH2) * ChemConst::KB);
+  const double nH = IONS ? rho - rh2 - rhp : rho - rh2, nH2 = 0.5 * rh2, n = rho;
+  const double T = ((2.0 * P0) * eint) / ((3.0 * (IONS ? nH + 2.0 * rhp : nH) + 5.0 * nH2) * ChemConst::KB);
   const double x = log10(T * 1e-4);
   // k1' and k4 (App. D, as in chem_cell)
   const double t2 = T * 0.01, s2 = sqrt(t2);
@@ -643,7 +709,24 @@ __device__ __forceinline__ double heatcool_delta(const Phys& ph, double rho, dou
   const double L3 = nH2 * LH3 / (1.0 + LH3 / LL3);
   // Gamma_4
   const double G4 = 6.4e-13 * k4 * nH2;
-  const double net = (G1 + G4) - (L2 + L3);
+  double net = (G1 + G4) - (L2 + L3);
+  if (IONS && ph.ions) {
+    // Gamma_5 = 1.92e-28 n; Lambda_6 = 2.18e-11 k6 n_H n_e; Lambda_7 = 4.65e-30 T^0.94 psi^beta n_e n_H+
+    // with psi = exp(-0.75e-20 (N_H + N_H2)) sqrt(T) / n_e and beta = 0.74 / T^0.068 (0 where
+    // n_e = 0); Lambda_8 = 5.7e-26 (T / 1e4)^0.8 n_e n_H+
+    const double ne = rhp, lnT = log(T);
+    const IonRates q = ion_rates(lnT);
+    const double G5 = 1.92e-28 * n;
+    const double L6 = 2.18e-11 * q.k6 * nH * ne;
+    double L7 = 0.0;
+    if (ne > 0.0) {
+      const double lnpsi = (-0.75e-20 * (NH + NH2) + 0.5 * lnT) - log(ne);
+      const double beta = 0.74 * exp(-0.068 * lnT);
+      L7 = 4.65e-30 * exp(0.94 * lnT + beta * lnpsi) * ne * rhp;
+    }
+    const double L8 = 5.7e-26 * exp(0.8 * (lnT - 9.210340371976184)) * ne * rhp;  // ln 1e4
+    net = (net + G5) - ((L6 + L7) + L8);
+  }
   double d = (tau * T0) * net / P0;
   if (d < -0.5 * eint) d = -0.5 * eint;
   return d;

@@ -22,4 +22,6 @@ template cudaError_t set_faces<float>(mhd_sim*, Box<float>&, const double* const
 template cudaError_t store_full<float>(mhd_sim*, Box<float>&, double* const*);
 template cudaError_t load_full<float>(mhd_sim*, Box<float>&, const double* const*);
 template cudaError_t diag_partial<float>(mhd_sim*, Box<float>&);
+template cudaError_t store_ions<float>(mhd_sim*, Box<float>&, double*);
+template cudaError_t load_ions<float>(mhd_sim*, Box<float>&, const double*);
 }  // namespace mhd_rt

@@ -25,7 +25,7 @@ struct Prim {
 // Eulerian face outputs of one direction: F_mn, F_mt1, F_mt2, F_E, V_n, eA, eB   (Sec. 2.4, 2.5)
 template <typename T>
 struct FaceOut {
-  T* f[7];
+  T* f[8];  // the Lagrangian fluxes use f[0..nv-1]
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -40,9 +40,9 @@ struct Box {
   Scalars* sc;
   State<T> s, s0;
   Prim<T> w;
-  FaceOut<T> fo[3];  // Eulerian face outputs; the Lagrangian fluxes reuse fo[d].f[0..6]
+  FaceOut<T> fo[3];  // Eulerian face outputs; the Lagrangian fluxes reuse fo[d].f[0..nv-1]
   T* e[3];
-  int nv;            // advected fields of the Lagrangian stage (6, or 7 with rho_H2)
+  int nv;            // advected fields of the Lagrangian stage (6; 7 with rho_H2; 8 with rho_H+)
   const T* phi;      // gravitational potential of the step (nullptr: no self-gravity)
 };
 
@@ -90,8 +90,8 @@ __device__ __forceinline__ void decode_pencil(idx_t p, const int ext[3], int c[3
 #define MHD_TILE_LOOP(tl) for (int t_ = blockIdx.x; t_ < (tl).n; t_ += gridDim.x)
 
 // ------------------------------------------------------------------------------------------------
-// primitives of one cell
-template <typename T>
+// primitives of one cell (IONS: the kernel may see boxes with H+, whose gamma_eff counts it)
+template <typename T, bool IONS>
 __device__ __forceinline__ void prim_cell(const Box<T>& B, idx_t c) {
   const Geom& g = B.g;
   int q[3];
@@ -101,7 +101,8 @@ __device__ __forceinline__ void prim_cell(const Box<T>& B, idx_t c) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) B.w.B[d][c] = T(0.5) * (B.s.b[d][c] + B.s.b[d][up[d]]);
   // gamma_eff in the bulk type: the FP32-bulk path's fluxes are FP32
-  T gmt = B.ph.chem ? gamma_eff(rho, B.s.rh2[c]) : (T)B.ph.gamma;
+  T gmt = !B.ph.chem ? (T)B.ph.gamma
+          : (IONS && B.ph.ions) ? gamma_eff(rho, B.s.rh2[c], B.s.rhp[c]) : gamma_eff(rho, B.s.rh2[c]);
 #pragma unroll
   for (int d = 0; d < 3; ++d) B.w.v[d][c] = B.s.m[d][c] / rho;
   B.w.p[c] = (gmt - T(1)) * B.s.eint[c];
@@ -109,12 +110,12 @@ __device__ __forceinline__ void prim_cell(const Box<T>& B, idx_t c) {
   B.w.sr[c] = sqrt(rho);
 }
 
-template <typename T>
+template <typename T, bool IONS>
 __global__ void __launch_bounds__(512) kb_prim(const Box<T>* __restrict__ boxes, Tiles tl) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
     idx_t c = tl.start[t_] + (idx_t)threadIdx.x;
-    if (c < B.g.N) prim_cell(B, c);
+    if (c < B.g.N) prim_cell<T, IONS>(B, c);
   }
 }
 
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(512) kb_euler_update(const Box<T>* __restrict_
 // ------------------------------------------------------------------------------------------------
 // Sec. 2.6 Lagrangian face flux for direction D: F = v_n q(-|v_n| tau) (v_n >= 0, left cell) or
 // v_n q(|v_n| tau) (right cell) with v_n the sqrt(rho)-weighted mean of the cell velocities.
-template <typename T, int D>
+template <typename T, int D, bool IONS>
 __device__ __forceinline__ void lag_face(const Box<T>& B, idx_t t) {
   const Geom& g = B.g;
   int ext[3] = {g.n[0], g.n[1], g.n[2]};
@@ -398,30 +399,36 @@ __device__ __forceinline__ void lag_face(const Box<T>& B, idx_t t) {
   idx_t st[5];
 #pragma unroll
   for (int o = 0; o < 5; ++o) st[o] = o0 == 0 ? cell[o] : cell[o + 1];
-#pragma unroll
-  for (int v = 0; v < 7; ++v) {
-    if (v >= nv) break;
-    const T* a = q[v];
+  auto flux = [&](const T* a, int v) {
     Para<T> P = ppm_lean(a[st[0]], a[st[1]], a[st[2]], a[st[3]], a[st[4]]);
     T qb = o0 == 0 ? avg_right_end(P, y) : avg_left_end(P, y);
     B.fo[D].f[v][f] = vn * qb;
+  };
+#pragma unroll
+  for (int v = 0; v < 7; ++v) {
+    if (v >= nv) break;
+    flux(q[v], v);
+  }
+  if (IONS) {
+#pragma unroll 1
+    for (int v = 7; v < nv; ++v) flux(B.s.rhp, v);  // rho_H+ (ions on)
   }
 }
 
-template <typename T, int D>
+template <typename T, int D, bool IONS>
 __global__ void __launch_bounds__(256) kb_lag_face(const Box<T>* __restrict__ boxes, Tiles tl) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
     idx_t t = tl.start[t_] + (idx_t)threadIdx.x;
     idx_t total = (idx_t)(B.g.n[0] + (D == 0)) * (B.g.n[1] + (D == 1)) * (B.g.n[2] + (D == 2));
-    if (t < total) lag_face<T, D>(B, t);
+    if (t < total) lag_face<T, D, IONS>(B, t);
   }
 }
 
 // The same fluxes for the faces i_D - 1/2, i_D in [s PENCIL, min((s+1) PENCIL, n_D + 1)), of one
 // pencil s: the face velocities first, then field by field the parabolas of the pencil's cells in
 // one PPMStream along D, each face taking the average of its upwind cell.
-template <typename T, int D>
+template <typename T, int D, bool IONS>
 __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
   const Geom& g = B.g;
   int ext[3] = {g.n[0], g.n[1], g.n[2]};
@@ -465,7 +472,8 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
   const int nv = B.nv;
 #pragma unroll 1
   for (int v = 0; v < nv; ++v) {
-    const T* a = v == 0 ? B.s.rho : v < 4 ? B.s.m[v - 1] : v == 4 ? B.s.E : v == 5 ? B.s.eint : B.s.rh2;
+    const T* a = v == 0 ? B.s.rho : v < 4 ? B.s.m[v - 1] : v == 4 ? B.s.E : v == 5 ? B.s.eint
+                 : (IONS && v == 7) ? B.s.rhp : B.s.rh2;
     T* out = B.fo[D].f[v] + fbase;
     PPMStream<T> S;
     S.prime(a[cell_at(f0 - 3)], a[cell_at(f0 - 2)], a[cell_at(f0 - 1)], a[cell_at(f0)]);
@@ -485,7 +493,7 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
   }
 }
 
-template <typename T, int D>
+template <typename T, int D, bool IONS>
 __global__ void __launch_bounds__(256, 1) kb_lag_pencil(const Box<T>* __restrict__ boxes, Tiles tl) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
@@ -493,11 +501,12 @@ __global__ void __launch_bounds__(256, 1) kb_lag_pencil(const Box<T>* __restrict
     idx_t total = (idx_t)(D == 0 ? pencil_segments(B.g.n[0]) : B.g.n[0]) *
                       (D == 1 ? pencil_segments(B.g.n[1]) : B.g.n[1]) *
                       (D == 2 ? pencil_segments(B.g.n[2]) : B.g.n[2]);
-    if (p < total) lag_pencil<T, D>(B, p);
+    if (p < total) lag_pencil<T, D, IONS>(B, p);
   }
 }
 
-template <typename T>
+// IONS: up to 8 advected fields (rho_H+ last), else up to 7
+template <typename T, bool IONS>
 __device__ __forceinline__ void lag_update_cell(const Box<T>& B, idx_t c, int r) {
   const Geom& g = B.g;
   int q[3];
@@ -507,11 +516,11 @@ __device__ __forceinline__ void lag_update_cell(const Box<T>& B, idx_t c, int r)
   const T ih = (T)B.ph.ih;
   idx_t f0 = fidx(g, q[0], q[1], q[2]);
   idx_t fup[3] = {fidx(g, q[0] + 1, q[1], q[2]), fidx(g, q[0], q[1] + 1, q[2]), fidx(g, q[0], q[1], q[2] + 1)};
-  T* qq[7] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2};
-  T* q0[7] = {B.s0.rho, B.s0.m[0], B.s0.m[1], B.s0.m[2], B.s0.E, B.s0.eint, B.s0.rh2};
+  T* qq[8] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2, B.s.rhp};
+  T* q0[8] = {B.s0.rho, B.s0.m[0], B.s0.m[1], B.s0.m[2], B.s0.E, B.s0.eint, B.s0.rh2, B.s0.rhp};
   const int nv = B.nv;
 #pragma unroll
-  for (int v = 0; v < 7; ++v) {
+  for (int v = 0; v < (IONS ? 8 : 7); ++v) {
     if (v >= nv) break;
     T acc = T(0);
 #pragma unroll
@@ -521,12 +530,12 @@ __device__ __forceinline__ void lag_update_cell(const Box<T>& B, idx_t c, int r)
   }
 }
 
-template <typename T>
+template <typename T, bool IONS>
 __global__ void __launch_bounds__(512) kb_lag_update(const Box<T>* __restrict__ boxes, Tiles tl, int r) {
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
     idx_t c = tl.start[t_] + (idx_t)threadIdx.x;
-    if (c < B.g.N) lag_update_cell(B, c, r);
+    if (c < B.g.N) lag_update_cell<T, IONS>(B, c, r);
   }
 }
 
@@ -544,19 +553,25 @@ __device__ __forceinline__ double warp_max(double v) {
 // chemistry, bit 1 heating/cooling; the full step runs both), do_reg the regularisation;
 // cell_stages = do_reg = 0 computes only the CFL denominator.  Returns the flags via the
 // warp-aggregated atomics of the caller.
-template <typename T>
+template <typename T, bool IONS>
 __device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, int cell_stages, int do_reg,
                                           double& D, int& bad, unsigned& vb) {
   const Geom& g = B.g;
   const Phys& ph = B.ph;
+  const bool ions = IONS && ph.ions;
   const State<T>& s = B.s;
   int q[3];
   decode(c, g.n[0], g.n[1], q);
   const double tau = B.sc->tau;
-  if ((cell_stages & 1) && ph.chem)
-    s.rh2[c] = (T)chem_cell(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c], tau);
+  if ((cell_stages & 1) && ph.chem) {
+    const ChemOut co = chem_cell<IONS>(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c],
+                                       ions ? (double)s.rhp[c] : 0.0, tau);
+    s.rh2[c] = (T)co.rh2;
+    if (ions) s.rhp[c] = (T)co.rhp;
+  }
   if ((cell_stages & 2) && ph.chem && ph.heatcool) {
-    const double d = heatcool_delta(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c], tau);
+    const double d = heatcool_delta<IONS>(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c],
+                                          ions ? (double)s.rhp[c] : 0.0, tau);
     s.E[c] = (T)((double)s.E[c] + d);
     s.eint[c] = (T)((double)s.eint[c] + d);
   }
@@ -599,12 +614,17 @@ __device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, int cell_sta
     if (!isfinite(vals[k])) bad = 1;
   if (!(rho > T(0)) || !(eint > T(0))) bad = 1;
   double gm = ph.chem ? gamma_eff((double)rho, (double)s.rh2[c]) : ph.gamma;
+  if (ions) {
+    const T rhp = s.rhp[c];
+    if (!isfinite(rhp)) bad = 1;
+    gm = gamma_eff((double)rho, (double)s.rh2[c], (double)rhp);
+  }
   if (!bad)  // FP64 CFL of the new state (FP32 fields widened)
     D = cfl_denominator((double)rho, (double)m[0], (double)m[1], (double)m[2], (double)Bc[0],
                         (double)Bc[1], (double)Bc[2], gm * ((gm - 1.0) * (double)eint));
 }
 
-template <typename T>
+template <typename T, bool IONS>
 __global__ void __launch_bounds__(512) kb_post(const Box<T>* __restrict__ boxes, Tiles tl, int cell_stages,
                                                int do_reg, int check) {
   MHD_TILE_LOOP(tl) {
@@ -613,7 +633,7 @@ __global__ void __launch_bounds__(512) kb_post(const Box<T>* __restrict__ boxes,
     double D = 0.0;
     int bad = 0;
     unsigned vb = 0;
-    if (c < B.g.N) post_cell(B, c, cell_stages, do_reg, D, bad, vb);
+    if (c < B.g.N) post_cell<T, IONS>(B, c, cell_stages, do_reg, D, bad, vb);
     if (!check) bad = 0;
     D = warp_max(D);
     int anybad = __any_sync(0xffffffffu, bad);
@@ -685,6 +705,7 @@ __global__ void k_load_cells(Geom g, State<T> s, const In* rho, const In* mx, co
   s.m[2][c] = (T)mz[c];
   s.E[c] = (T)E[c];
   if (s.rh2) s.rh2[c] = rh2 ? (T)rh2[c] : T(0);
+  if (s.rhp) s.rhp[c] = T(0);
 }
 
 // A17: face b_d(i_d - 1/2) = (B_d(i_d - 1) + B_d(i_d)) / 2 from cell-centred input (in FP64)
@@ -759,6 +780,19 @@ __global__ void k_store_full(Geom g, State<T> s, double* eint, double* bx, doubl
   bx[c] = (double)s.b[0][c];
   by[c] = (double)s.b[1][c];
   bz[c] = (double)s.b[2][c];
+}
+
+// rho_H+ in and out (FP64 interface)
+template <typename T>
+__global__ void k_load_ions(Geom g, State<T> s, const double* rhp) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < g.N) s.rhp[c] = (T)rhp[c];
+}
+
+template <typename T>
+__global__ void k_store_ions(Geom g, State<T> s, double* rhp) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < g.N) rhp[c] = (double)s.rhp[c];
 }
 
 template <typename T>

@@ -95,6 +95,7 @@ struct Exec {
   LaunchCfg cfg[NKC];
   int nsm = 152;
   Profiler* prof = nullptr;
+  bool ions = false;      // some box has H+ (reactions 5-8): the kernels with the ion code
 };
 
 template <typename T>
@@ -193,6 +194,8 @@ template <typename T>
 cudaError_t exec_init(Exec<T>& X, const std::vector<Box<T>>& boxes) {
   X.h = boxes;
   X.nb = (int)boxes.size();
+  X.ions = false;
+  for (const Box<T>& b : boxes) X.ions = X.ions || (b.ph.chem && b.ph.ions);
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&X.nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -251,7 +254,10 @@ void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
   // self-gravity: a box with a potential (such sims step alone, never in a batch)
   const bool grav = X.nb == 1 && X.h[0].phi != nullptr;
   for (int r = 0; r < 3; ++r) {
-    launch_k(X, st, KC_PRIM, DOM_CELLS, kb_prim<T>);
+    if (X.ions)
+      launch_k(X, st, KC_PRIM, DOM_CELLS, kb_prim<T, true>);
+    else
+      launch_k(X, st, KC_PRIM, DOM_CELLS, kb_prim<T, false>);
     launch_ks(X, st, KC_EFACE, DOM_PENCIL_X, euler_pencil_smem<T>(), kb_euler_pencil<T, 0>);
     launch_ks(X, st, KC_EFACE, DOM_PENCIL_Y, euler_pencil_smem<T>(), kb_euler_pencil<T, 1>);
     launch_ks(X, st, KC_EFACE, DOM_PENCIL_Z, euler_pencil_smem<T>(), kb_euler_pencil<T, 2>);
@@ -267,15 +273,30 @@ template <typename T>
 void launch_lag_stage(Exec<T>& X, cudaStream_t st) {
   for (int r = 0; r < 3; ++r) {
     if constexpr (lag_in_pencils<T>()) {
-      launch_k(X, st, KC_LFACE, DOM_PENCIL_X, kb_lag_pencil<T, 0>);
-      launch_k(X, st, KC_LFACE, DOM_PENCIL_Y, kb_lag_pencil<T, 1>);
-      launch_k(X, st, KC_LFACE, DOM_PENCIL_Z, kb_lag_pencil<T, 2>);
+      if (X.ions) {
+        launch_k(X, st, KC_LFACE, DOM_PENCIL_X, kb_lag_pencil<T, 0, true>);
+        launch_k(X, st, KC_LFACE, DOM_PENCIL_Y, kb_lag_pencil<T, 1, true>);
+        launch_k(X, st, KC_LFACE, DOM_PENCIL_Z, kb_lag_pencil<T, 2, true>);
+      } else {
+        launch_k(X, st, KC_LFACE, DOM_PENCIL_X, kb_lag_pencil<T, 0, false>);
+        launch_k(X, st, KC_LFACE, DOM_PENCIL_Y, kb_lag_pencil<T, 1, false>);
+        launch_k(X, st, KC_LFACE, DOM_PENCIL_Z, kb_lag_pencil<T, 2, false>);
+      }
     } else {
-      launch_k(X, st, KC_LFACE, DOM_FACE_X, kb_lag_face<T, 0>);
-      launch_k(X, st, KC_LFACE, DOM_FACE_Y, kb_lag_face<T, 1>);
-      launch_k(X, st, KC_LFACE, DOM_FACE_Z, kb_lag_face<T, 2>);
+      if (X.ions) {
+        launch_k(X, st, KC_LFACE, DOM_FACE_X, kb_lag_face<T, 0, true>);
+        launch_k(X, st, KC_LFACE, DOM_FACE_Y, kb_lag_face<T, 1, true>);
+        launch_k(X, st, KC_LFACE, DOM_FACE_Z, kb_lag_face<T, 2, true>);
+      } else {
+        launch_k(X, st, KC_LFACE, DOM_FACE_X, kb_lag_face<T, 0, false>);
+        launch_k(X, st, KC_LFACE, DOM_FACE_Y, kb_lag_face<T, 1, false>);
+        launch_k(X, st, KC_LFACE, DOM_FACE_Z, kb_lag_face<T, 2, false>);
+      }
     }
-    launch_k(X, st, KC_LUPD, DOM_CELLS, kb_lag_update<T>, r);
+    if (X.ions)
+      launch_k(X, st, KC_LUPD, DOM_CELLS, kb_lag_update<T, true>, r);
+    else
+      launch_k(X, st, KC_LUPD, DOM_CELLS, kb_lag_update<T, false>, r);
   }
 }
 
@@ -283,7 +304,10 @@ void launch_lag_stage(Exec<T>& X, cudaStream_t st) {
 // new state (cell_stages = do_reg = check = 0: only the CFL denominator)
 template <typename T>
 void launch_post(Exec<T>& X, cudaStream_t st, int cell_stages, int do_reg, int check) {
-  launch_k(X, st, KC_POST, DOM_CELLS, kb_post<T>, cell_stages, do_reg, check);
+  if (X.ions)
+    launch_k(X, st, KC_POST, DOM_CELLS, kb_post<T, true>, cell_stages, do_reg, check);
+  else
+    launch_k(X, st, KC_POST, DOM_CELLS, kb_post<T, false>, cell_stages, do_reg, check);
 }
 
 template <typename T>
@@ -396,6 +420,18 @@ cudaError_t load_full(mhd_sim* S, Box<T>& B, const double* const* d) {
 }
 
 template <typename T>
+cudaError_t store_ions(mhd_sim* S, Box<T>& B, double* d) {
+  k_store_ions<T><<<nblk(B.g.N, 256), 256, 0, S->stream>>>(B.g, B.s, d);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t load_ions(mhd_sim* S, Box<T>& B, const double* d) {
+  k_load_ions<T><<<nblk(B.g.N, 256), 256, 0, S->stream>>>(B.g, B.s, d);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t diag_partial(mhd_sim* S, Box<T>& B) {
   k_diag_partial<T><<<S->diag_blocks, DIAG_THREADS, 0, S->stream>>>(B.g, B.s, S->diag_part);
   return cudaGetLastError();
@@ -419,6 +455,8 @@ extern template cudaError_t set_faces<float>(mhd_sim*, Box<float>&, const double
 extern template cudaError_t store_full<float>(mhd_sim*, Box<float>&, double* const*);
 extern template cudaError_t load_full<float>(mhd_sim*, Box<float>&, const double* const*);
 extern template cudaError_t diag_partial<float>(mhd_sim*, Box<float>&);
+extern template cudaError_t store_ions<float>(mhd_sim*, Box<float>&, double*);
+extern template cudaError_t load_ions<float>(mhd_sim*, Box<float>&, const double*);
 #endif
 
 }  // namespace mhd_rt

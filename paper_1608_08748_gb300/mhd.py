@@ -16,7 +16,7 @@ from . import build as _build
 
 OPT = {"bc_x": 1, "bc_y": 2, "bc_z": 3, "chem": 4, "precision": 5, "regul_mode": 7,
        "chem_lshield": 8, "chem_bdop": 9, "chem_xnorm": 10, "chem_taud": 11, "graph": 14,
-       "heatcool": 15, "grav_g": 16}
+       "heatcool": 15, "grav_g": 16, "ions": 17}
 STATUS = {0: "MHD_OK", 1: "MHD_PENDING", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA",
           -4: "MHD_ENONPHYS", -5: "MHD_ETIMEOUT", -6: "MHD_ENOTFOUND", -7: "MHD_ECAPACITY"}
 F64, F32 = 0, 1
@@ -86,6 +86,8 @@ def lib():
         L.mhd_profile.argtypes = [vp, d, i, C.POINTER(d), C.POINTER(C.c_int64)]
         L.mhd_launches_per_step.argtypes = [vp]
         L.mhd_get_potential.argtypes = [vp, vp]
+        L.mhd_set_ions.argtypes = [vp, vp, i]
+        L.mhd_get_ions.argtypes = [vp, vp, i]
         L.mhd_batch_create.restype = vp
         L.mhd_batch_create.argtypes = [C.POINTER(vp), i]
         L.mhd_batch_destroy.argtypes = [vp]
@@ -233,6 +235,17 @@ class Sim:
     def stage(self, which, tau):
         _check(self.L.mhd_stage(self.h, int(which), float(tau)))
 
+    def set_ions(self, rho_hp):
+        """rho_H+ of every cell (float64; numpy or a CUDA tensor); after set_state, which zeroes it."""
+        p, on_dev, keep = _ptr(rho_hp, F64)
+        _check(self.L.mhd_set_ions(self.h, p, on_dev))
+        del keep
+
+    def get_ions(self):
+        out = np.empty(self.shape)
+        _check(self.L.mhd_get_ions(self.h, out.ctypes.data, 0))
+        return out
+
     def potential(self):
         """Sec. 2.10 gravitational potential of the current density (needs the grav_g option)."""
         out = np.empty(self.shape)
@@ -259,6 +272,8 @@ def from_ic(ic, **options):
     opts.update(options)
     s = Sim(nx, ny, nz, ic["gamma"], ic["dx"], **opts)
     s.set_state(ic["rho"], ic["mom"], ic["E"], ic["B"], ic.get("rho_h2"))
+    if ic.get("rho_hp") is not None:
+        s.set_ions(ic["rho_hp"])
     if "bface" in ic:
         s.set_face_B(*ic["bface"])
     return s

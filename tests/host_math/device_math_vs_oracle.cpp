@@ -19,6 +19,10 @@ osim* osim_create(int nx, int ny, int nz, double gamma, double dx);
 void osim_destroy(osim* s);
 void osim_chem_cell(const osim* s, double rho, double eint, double rh2, double tau, double out[8]);
 void osim_heatcool_cell(const osim* s, double rho, double eint, double rh2, double tau, double out[7]);
+void osim_chem_cell_ions(const osim* s, double rho, double eint, double rh2, double rhp, double tau,
+                         double out[15]);
+void osim_heatcool_cell_ions(const osim* s, double rho, double eint, double rh2, double rhp, double tau,
+                             double out[11]);
 int osim_set_option(osim* s, int key, double v);
 void o_ppm(const double q[5], int step4_as_written, double out[4]);
 void o_face_solve(const double wl[5], const double wr[5], double Bn, const double sl[30], const double sr[30],
@@ -208,7 +212,7 @@ int main() {
       const double tau = std::exp(10 * U01(g) - 12);
       double o[8];
       osim_chem_cell(s, rho, eint, rh2, tau, o);
-      const double a = chem_cell(ph, rho, eint, rh2, tau);
+      const double a = chem_cell<false>(ph, rho, eint, rh2, 0.0, tau).rh2;
       const double e = std::fabs(a - o[0]) / std::max(std::fabs(o[0]), 1e-12 * rho);
       worst = std::max(worst, e);
       if (e > 1e-12) ++bad;
@@ -225,7 +229,7 @@ int main() {
       const double tau = std::exp(10 * U01(g) - 12);
       double o[7];
       osim_heatcool_cell(s, rho, eint, rh2, tau, o);
-      const double a = heatcool_delta(ph, rho, eint, rh2, tau);
+      const double a = heatcool_delta<false>(ph, rho, eint, rh2, 0.0, tau);
       // relative to the gross exchange tau (Gamma_1 + Gamma_4 + Lambda_2 + Lambda_3) in code units:
       // the net change cancels near equilibrium
       const double gross = tau * (3.0856775814913673e18 / 1e5) * (o[2] + o[3] + o[4] + o[5]) / (1.6735575e-24 * 1e10);
@@ -233,8 +237,43 @@ int main() {
       worsth = std::max(worsth, e);
       if (e > 1e-12) ++badh;
     }
-    osim_destroy(s);
     report("heatcool", n, worsth, badh);
+    // 5c. with H+ and electrons (reactions 5-8): the new rho_H2 and rho_H+, and the heating/cooling
+    // change with Gamma_5, Lambda_6-8, over cold to hot, neutral to fully ionised cells
+    osim_set_option(s, 15, 1.0);
+    ph.ions = 1;
+    long badi = 0, badhi = 0;
+    double worsti = 0, worsthi = 0;
+    for (long it = 0; it < n; ++it) {
+      const double rho = std::exp(12 * U01(g) - 4);
+      const double f2 = U01(g) * (it % 3 ? 1.0 : 1e-6) * (it % 13 == 0 ? 0.0 : 1.0);
+      const double fp = (1.0 - f2) * U01(g) * (it % 5 ? 1.0 : 1e-6) * (it % 17 == 0 ? 0.0 : 1.0);
+      const double rh2 = rho * f2, rhp = rho * fp;
+      const double eint = rho * std::exp(16 * U01(g) - 8);
+      const double tau = std::exp(10 * U01(g) - 12);
+      double o[15];
+      osim_chem_cell_ions(s, rho, eint, rh2, rhp, tau, o);
+      const ChemOut a = chem_cell<true>(ph, rho, eint, rh2, rhp, tau);
+      // relative to the largest density the update adds or subtracts: the printed form n + tau (C -
+      // D n) / (1 + tau D) cancels where recombination removes nearly all of n_H+, leaving a rounding
+      // error of order eps n_H+(start) on both sides
+      const double e = std::max(std::fabs(a.rh2 - o[0]), std::fabs(a.rhp - o[1])) /
+                       std::max({std::fabs(o[0]), std::fabs(o[1]), rh2, rhp, 1e-12 * rho});
+      worsti = std::max(worsti, e);
+      if (e > 1e-12) ++badi;
+      double h[11];
+      osim_heatcool_cell_ions(s, rho, eint, rh2, rhp, tau, h);
+      const double d = heatcool_delta<true>(ph, rho, eint, rh2, rhp, tau);
+      double gross_rate = 0.0;
+      for (int k = 2; k <= 9; ++k) gross_rate += std::fabs(h[k]);
+      const double gross = tau * (3.0856775814913673e18 / 1e5) * gross_rate / (1.6735575e-24 * 1e10);
+      const double eh = std::fabs(d - h[0]) / std::max(std::max(std::fabs(h[0]), gross), 1e-300);
+      worsthi = std::max(worsthi, eh);
+      if (eh > 1e-12) ++badhi;
+    }
+    osim_destroy(s);
+    report("chemistry_ions", n, worsti, badi);
+    report("heatcool_ions", n, worsthi, badhi);
   }
   // 6. CFL denominator (FP64) against the oracle's
   {

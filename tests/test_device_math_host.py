@@ -6,8 +6,9 @@ inline-PTX integer-pipe helpers; this test replaces that block with portable C++
 definitions, compiles tests/host_math/device_math_vs_oracle.cpp against it and the oracle library,
 and checks: the FP64 parabolas equal the oracle's exactly (Sec. 2.1; -0 and +0 count as equal), the streamed ones equal
 the five-point ones bit for bit, the Riemann solve (Sec. 2.4, App. A) is within 1e-12 of the
-oracle's in FP64 and 1e-4 in FP32, the chemistry (Sec. 2.7, App. D) within 1e-12, the heating/cooling
-change (Sec. 2.8) within 1e-12 of the gross heating plus cooling and the CFL
+oracle's in FP64 and 1e-4 in FP32, the chemistry (Sec. 2.7, App. D; with and without reactions 5-8)
+within 1e-12, the heating/cooling change (Sec. 2.8; with and without Gamma_5 and Lambda_6-8) within
+1e-12 of the gross heating plus cooling and the CFL
 denominator (Sec. 2.3) within 1e-13.  The host build uses -ffp-contract=off like the oracle; the
 GPU build contracts to FMA, whose effect the GPU parity tests bound."""
 import os
@@ -47,7 +48,7 @@ inline bool sign_bit_b(float x) { return std::signbit(x); }
 '''
 
 BOUNDS = {"ppm_lean_equal": 0, "ppm_stream_bits": 0, "ppm_fp32": 0, "riemann_fp64": 0, "riemann_fp32": 0,
-          "chemistry": 0, "heatcool": 0, "cfl": 0}
+          "chemistry": 0, "heatcool": 0, "chemistry_ions": 0, "heatcool_ions": 0, "cfl": 0}
 
 
 def _cuda_include():

@@ -16,6 +16,7 @@ sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 import test_oracle_cfl_chem as T_cc  # noqa: E402
 import test_oracle_gravity as T_gr  # noqa: E402
 import test_oracle_heatcool as T_hc  # noqa: E402
+import test_oracle_ions as T_io  # noqa: E402
 import test_oracle_physics as T_ph  # noqa: E402
 import test_oracle_ppm as T_ppm  # noqa: E402
 import test_oracle_riemann as T_rs  # noqa: E402
@@ -49,8 +50,23 @@ MUTATIONS = [
     ("chem_photodissociation_dropped", "r.D = (r.k2 * nH + r.k3 * nH2) + r.k4;", "r.D = (r.k2 * nH + r.k3 * nH2);"),
     ("k1_temperature_power", "double s2 = sqrt(t2);", "double s2 = t2;"),
     ("regularisation_half_dropped", "double kin = 0.5 * m2 / r;", "double kin = m2 / r;"),
-    ("gamma_eff_weights_swapped", "return (5.0 * nH + 7.0 * nH2) / (3.0 * nH + 5.0 * nH2);",
-     "return (7.0 * nH + 5.0 * nH2) / (5.0 * nH + 3.0 * nH2);"),
+    ("gamma_eff_weights_swapped", "return (5.0 * n1 + 7.0 * nH2) / (3.0 * n1 + 5.0 * nH2);",
+     "return (7.0 * n1 + 5.0 * nH2) / (5.0 * n1 + 3.0 * nH2);"),
+    ("gamma_eff_electrons_dropped", "double n1 = (rho - rh2 - rhp) + 2.0 * rhp", "double n1 = (rho - rh2 - rhp) + 1.0 * rhp"),
+    ("temperature_electrons_dropped", "return p / ((((nH + nH2) + nHp) + ne) * KB_CGS);",
+     "return p / (((nH + nH2) + nHp) * KB_CGS);"),
+    ("k6_log_base", "double L = log(T * KB_EV)", "double L = log10(T * KB_EV)"),
+    ("k7_denominator_sign", "double Q = 1.0 - 0.38 * x", "double Q = 1.0 + 0.38 * x"),
+    ("k8_log_base", "- 4.4e-5 * log10(T))", "- 4.4e-5 * log(T))"),
+    ("ion_recombination_dropped", "r.D = r.k7 * ne + r.k8 * n;", "r.D = r.k8 * n;"),
+    ("ion_update_sign", "double nHpn = nHp + ts * (q.C - q.D * nHp) / (1.0 + ts * q.D);",
+     "double nHpn = nHp + ts * (q.C + q.D * nHp) / (1.0 + ts * q.D);"),
+    ("ion_clamp_ignores_h2", "if (nHpn > n - 2.0 * nH2n) nHpn = n - 2.0 * nH2n;", "if (nHpn > n) nHpn = n;"),
+    ("ion_rk_register_not_saved", "    memcpy(s->rhp0, s->rhp, bytes);\n", ""),
+    ("lambda7_psi_electrons", "sqrt(T) / ne;", "sqrt(T) * ne;"),
+    ("lambda8_power", "pow(T / 1e4, 0.8)", "pow(T / 1e4, 0.08)"),
+    ("gamma5_density", "h.G5 = 1.92e-28 * n;", "h.G5 = 1.92e-28 * nH;"),
+    ("lambda6_electrons_dropped", "h.L6 = 2.18e-11 * q.k6 * nH * ne;", "h.L6 = 2.18e-11 * q.k6 * nH;"),
     ("face_b_average_index", "s->b[d][c] = 0.5 * (Bc[d][srclo] + Bc[d][src]);", "s->b[d][c] = Bc[d][src];"),
     ("lambda2_high_T_constant", "3.9e-19 * exp(-6118.0 / T)", "3.9e-19 * exp(-6181.0 / T)"),
     ("lambda2_low_density_exponent", "(pow(nH2, 0.77) + 1.2 * pow(nH, 0.77))", "(pow(nH2, 0.77) + 1.2 * pow(nH, 0.7))"),
@@ -99,6 +115,22 @@ def pins(O):
                                    [(8, 10, 12), (5, 7, 9)]]
     yield "gravity_stage", lambda: T_gr.test_eulerian_stage_with_gravity_only(O)
     yield "gravity_fall", lambda: T_gr.test_gas_falls_towards_the_density_peak(O)
+    io = lambda **kw: O.Sim(4, 4, 4, 5.0 / 3.0, 2.0, chem=1, heatcool=1, ions=1, **kw)
+    yield "ions_gamma", lambda: [T_io.test_gamma_eff_is_the_equipartition_value(O, *a) for a in
+                                 [(1.0, 0.0, 1.0), (1.0, 0.4, 0.3)]]
+    yield "ions_temperature", lambda: T_io.test_temperature_counts_the_particles(O, 300.0, 2.0, 1.0, 0.5)
+    yield "ions_k6", lambda: T_io.test_k6_at_one_electron_volt_and_rising(O)
+    yield "ions_k6_activation", lambda: T_io.test_k6_activation_energy_is_the_ionisation_potential(O)
+    yield "ions_k7", lambda: T_io.test_k7_at_one_kelvin_and_falling_in_hot_gas(O)
+    yield "ions_k8", lambda: T_io.test_k8_constant_and_power_law(O)
+    yield "ions_terms", lambda: T_io.test_creation_and_destruction_terms(O)
+    yield "ions_energy", lambda: T_io.test_energy_per_event(io())
+    yield "ions_lambda8", lambda: T_io.test_lambda8_power_laws(io())
+    yield "ions_lambda7", lambda: T_io.test_lambda7_electron_scaling(O)
+    yield "ions_fixed_point", lambda: T_io.test_ion_equilibrium_is_a_fixed_point(O, io())
+    yield "ions_limits", lambda: T_io.test_ion_update_limits(io())
+    yield "ions_physical", lambda: T_io.test_species_stay_physical_and_nuclei_are_conserved(O, io())
+    yield "ions_lagrangian", lambda: T_io.test_lagrangian_stage_carries_an_exact_ion_fraction(O)
     st = T_rs.random_states(5, 7)
     yield "eigen", lambda: [T_rs.test_eigen_identities(O, s, 1e-11) for s in st]
     yield "linear_riemann", lambda: [T_rs.test_flat_riemann_matches_numpy_linear_solution(O, k) for k in range(3)]
