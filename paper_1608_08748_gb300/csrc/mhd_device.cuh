@@ -151,7 +151,7 @@ __device__ __forceinline__ Para<T> ppm_direct(T qm2, T qm1, T qc, T qp1, T qp2) 
   return P;
 }
 
-// ---- begin integer-pipe helpers ----
+// ---- begin inline-PTX helpers ----
 // Sign tests, absolute values, minima and comparisons of doubles on the integer pipes.  On sm_103
 // the FP64 pipe issues two instructions per clock per SM and the integer pipes 64, and the PPM
 // limiter is mostly such tests.  They work on the two 32-bit halves in inline PTX, so that the
@@ -219,10 +219,52 @@ __device__ __forceinline__ bool sign_bit_b(double x) {
 }
 __device__ __forceinline__ bool sign_bit_b(float x) { return signbit(x); }
 
-// ---- end integer-pipe helpers ----
+// Approximate reciprocal and reciprocal square root of a double (PTX rcp.approx.ftz.f64,
+// rsqrt.approx.ftz.f64): seeds for the Newton-Raphson steps below.  Subnormal arguments count as 0.
+__device__ __forceinline__ double rcp_seed(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ double rsqrt_seed(double x) {
+  double r;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+
+// ---- end inline-PTX helpers ----
 
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
+// FP64 reciprocal, quotient and square root in few FP64 instructions, by one third-order
+// Newton-Raphson step (the series of the inverse function) from the seeds above; a correctly
+// rounded FP64 division or square root takes about twice the FP64-pipe slots.
+//   1/x: with e = 1 - x r0, 1/x = r0 / (1 - e) = r0 (1 + e + e^2 + e^3 + ...); keeping 1 + e + e^2
+//        leaves a relative error of about e^3, below the double's rounding for the seed's error.
+//   1/sqrt(x): with e = 1 - x y0^2, 1/sqrt(x) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3 e^2 / 8 + ...).
+//   sqrt(x) = x (1/sqrt(x)).
+// Each is within 2 ulp of the correctly rounded value for finite normal arguments (x != 0); sqrt_nr
+// takes 0 and subnormal arguments through the library square root.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const double r = rcp_seed(x);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const double y = rsqrt_seed(x);
+  const double e = fma(-x, y * y, 1.0);
+  return fma(y, e * fma(0.375, e, 0.5), y);
+}
+__device__ __forceinline__ double sqrt_nr(double x) {
+  return x >= 2.2250738585072014e-308 ? x * rsqrt_nr(x) : sqrt(x);
+}
+// bulk-type forms: FP64 by the steps above; FP32 by the plain operations (the FP32 build already
+// takes the hardware-approximate division and square root)
+__device__ __forceinline__ double rcp_t(double x) { return rcp_nr(x); }
+__device__ __forceinline__ float rcp_t(float x) { return 1.0f / x; }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt_nr(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
 
 // Half the limited slope of Sec. 2.1 Step 1 for a cell with differences dn = q_0 - q_-1,
 // dp = q_1 - q_0 and s = q_1 - q_-1: the slope is min(|s|/2, 2|dp|, 2|dn|) with the sign of s where
@@ -384,7 +426,7 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
                                         const Para<T> pr[6], T tau_h, T qs[6]) {
   const T INV_SQRT2 = T(0.70710678118654752440);
   const T sl = wl[5], sr = wr[5];
-  const T iden = T(1) / (sl + sr);
+  const T iden = rcp_t(sl + sr);
   const T rho = (sl * wl[0] + sr * wr[0]) * iden;
   const T p = (sl * wl[1] + sr * wr[1]) * iden;
   const T gam = (sl * wl[2] + sr * wr[2]) * iden;
@@ -404,7 +446,7 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
   //   (c^2 - c_s^2)(c_f^2 - c^2) = c^2 b_perp^2,
   // so alpha_s (or alpha_f) is exactly 0 where B_perp = 0; dcs = c^2 - c_s^2, dfc = c_f^2 - c^2
   const T X = c2 - ca2;
-  const T sq = sqrt(X * X + bp2r * ((T(2) * c2 + T(2) * ca2) + bp2r));
+  const T sq = sqrt_t(X * X + bp2r * ((T(2) * c2 + T(2) * ca2) + bp2r));
   // the larger of the two differences from the sum, the other from their product
   T dcs, dfc;
   if constexpr (sizeof(T) == 8) {
@@ -412,7 +454,7 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
     const bool xpos = X >= T(0);
     T big = xpos ? T(0.5) * ((X + sq) - bp2r) : T(0.5) * ((bp2r - X) + sq);
     if (big < T(0)) big = T(0);
-    const T other = big > T(0) ? c2 * bp2r / big : T(0);
+    const T other = big >= T(2.2250738585072014e-308) ? (c2 * bp2r) * rcp_t(big) : big > T(0) ? c2 * bp2r / big : T(0);
     dcs = xpos ? big : other;
     dfc = xpos ? other : big;
   } else {
@@ -431,9 +473,9 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
   const T cs = (c * ca) * rcf;
   T af, as;
   if (sq > T(1e-12) * s) {
-    const T isq = T(1) / sq;
-    af = sqrt(dcs * isq);
-    as = sqrt(dfc * isq);
+    const T isq = rcp_t(sq);
+    af = sqrt_t(dcs * isq);
+    as = sqrt_t(dfc * isq);
   } else {
     af = INV_SQRT2;
     as = INV_SQRT2;
@@ -528,12 +570,12 @@ __device__ __forceinline__ double cfl_denominator(double rho, double mx, double 
                                                   double Bx, double By, double Bz, double gp) {
   const double irs = rsqrt(rho);
   const double irho = irs * irs;
-  const double sgp = sqrt(gp);
+  const double sgp = sqrt_nr(gp);
   const double B2 = Bx * Bx + By * By + Bz * Bz;
-  const double sB = sqrt(B2);
-  const double v = sqrt(mx * mx + my * my + mz * mz) * irho;
+  const double sB = sqrt_nr(B2);
+  const double v = sqrt_nr(mx * mx + my * my + mz * mz) * irho;
   const double Bm = fmax(fabs(Bx), fmax(fabs(By), fabs(Bz)));
-  const double fs = sqrt((gp + B2) + 2.0 * sgp * Bm);
+  const double fs = sqrt_nr((gp + B2) + 2.0 * sgp * Bm);
   return v + ((sB + sgp + Bm) + fs) * irs;
 }
 
@@ -614,14 +656,14 @@ __device__ __forceinline__ ChemOut chem_cell(const Phys& ph, double rho, double 
   const double nH = IONS ? rho - rh2 - rhp : rho - rh2, nH2 = 0.5 * rh2, n = rho;
   const double num = (2.0 * P0) * eint;
   const double den = (3.0 * (IONS ? nH + 2.0 * rhp : nH) + 5.0 * nH2) * ChemConst::KB;
-  const double r = 1.0 / (num * den);
+  const double r = rcp_nr(num * den);
   const double T = (num * num) * r, iT = (den * den) * r;
   // App. D rates
   const double t2 = T * 0.01;
   const double a2 = T > 7390.0 ? -2.93e4 * iT : -((6750.0 * iT) * (6750.0 * iT));
   const double a3 = T > 7291.0 ? -3.22e4 * iT : -(4060.0 * iT) - (7500.0 * iT) * (7500.0 * iT);
-  const double s2 = sqrt(t2);
-  const double k1p = 3e-17 * s2 / (((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2));
+  const double s2 = sqrt_nr(t2);
+  const double k1p = (3e-17 * s2) * rcp_nr(((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2));
   // exp of an argument below -746 is exactly 0 in double: skip the call in cold gas
   const double k2 = a2 < -746.0 ? 0.0 : (T > 7390.0 ? 6.11e-14 : 2.67e-15) * exp(a2);
   const double k3 = a3 < -746.0 ? 0.0 : (T > 7291.0 ? 5.22e-14 : 3.17e-15) * exp(a3);
@@ -632,12 +674,12 @@ __device__ __forceinline__ ChemOut chem_cell(const Phys& ph, double rho, double 
   const double u = 1.0 + x * ph.ibdop;
   const double isx = rsqrt(1.0 + x);
   const double sx = (1.0 + x) * isx;
-  const double fsh = 0.965 / (u * u) + (0.035 * isx) * exp(-8.5e-4 * sx);
+  const double fsh = 0.965 * rcp_nr(u * u) + (0.035 * isx) * exp(-8.5e-4 * sx);
   const double k4 = (3.3 * 1.7e-11) * fsh * fdust;
   const double C = k1p * n * nH;
   const double D = (k2 * nH + k3 * nH2) + k4;
   const double ts = tau * T0;
-  double nH2n = nH2 + ts * (C - D * nH2) / (1.0 + ts * D);
+  double nH2n = nH2 + (ts * (C - D * nH2)) * rcp_nr(1.0 + ts * D);
   if (nH2n < 0.0) nH2n = 0.0;
   if (nH2n > 0.5 * n) nH2n = 0.5 * n;
   ChemOut out;

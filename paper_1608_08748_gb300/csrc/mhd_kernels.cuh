@@ -390,7 +390,7 @@ __device__ __forceinline__ void lag_face(const Box<T>& B, idx_t t) {
   // v_l sqrt(rho_l) = m_l / sqrt(rho_l) and sqrt(rho) = rho / sqrt(rho): two 1/sqrt and a division
   T rl = B.s.rho[cl], rr = B.s.rho[cr];
   T isl = rsqrt_t(rl), isr = rsqrt_t(rr);
-  T vn = (B.s.m[D][cl] * isl + B.s.m[D][cr] * isr) / (rl * isl + rr * isr);
+  T vn = (B.s.m[D][cl] * isl + B.s.m[D][cr] * isr) * rcp_t(rl * isl + rr * isr);
   T y = fabs(vn) * tau_h;
   const T* q[7] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2};
   idx_t f = fidx(g, c[0], c[1], c[2]);
@@ -462,7 +462,7 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
       const idx_t cl = cell_at(f0 + k - 1), cr = cell_at(f0 + k);
       const T rl = B.s.rho[cl], rr = B.s.rho[cr];
       const T isl = rsqrt_t(rl), isr = rsqrt_t(rr);
-      vn[k] = (B.s.m[D][cl] * isl + B.s.m[D][cr] * isr) / (rl * isl + rr * isr);
+      vn[k] = (B.s.m[D][cl] * isl + B.s.m[D][cr] * isr) * rcp_t(rl * isl + rr * isr);
       const T y = abs_b(vn[k]) * tau_h;
       const T hy = T(0.5) * y;
       shy[k] = vn[k] >= T(0) ? neg_b(hy) : hy;

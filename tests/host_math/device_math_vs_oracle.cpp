@@ -1,6 +1,6 @@
 // The CUDA path's per-face and per-cell arithmetic (mhd_device.cuh) compiled for the host and
 // compared with the oracle's unit entry points on seeded random and adversarial inputs.  The test
-// that builds this file gives it a copy of the header in which the inline-PTX integer-pipe helpers
+// that builds this file gives it a copy of the header in which the inline-PTX helpers
 // are replaced by portable C++ with the same definitions (MHD_DEVICE_HOST_COPY).  Prints one line
 // per check: "<name> <cases> <worst relative difference> <cases beyond the bound>".
 #include <algorithm>
@@ -274,6 +274,24 @@ int main() {
     osim_destroy(s);
     report("chemistry_ions", n, worsti, badi);
     report("heatcool_ions", n, worsthi, badhi);
+  }
+  // 5d. the Newton-Raphson reciprocal, reciprocal square root and square root against the correctly
+  // rounded library values: within 2 ulp over the normal range
+  {
+    const long n = 1000000;
+    long bad = 0;
+    double worst = 0;
+    for (long it = 0; it < n; ++it) {
+      const double x = std::ldexp(1.0 + U01(g), (int)(2040 * U01(g)) - 1020) * (it % 2 ? 1.0 : -1.0);
+      const double ax = std::fabs(x);
+      const double e1 = std::fabs(rcp_nr(x) - 1.0 / x) / std::fabs(1.0 / x);
+      const double e2 = std::fabs(rsqrt_nr(ax) - 1.0 / std::sqrt(ax)) * std::sqrt(ax);
+      const double e3 = std::fabs(sqrt_nr(ax) - std::sqrt(ax)) / std::sqrt(ax);
+      const double e = std::max(e1, std::max(e2, e3)) / 2.220446049250313e-16;
+      worst = std::max(worst, e);
+      if (e > 2.0) ++bad;
+    }
+    report("newton_raphson_ulp", n, worst, bad);
   }
   // 6. CFL denominator (FP64) against the oracle's
   {

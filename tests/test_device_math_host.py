@@ -2,13 +2,14 @@
 
 The per-face and per-cell functions of mhd_device.cuh (PPM parabolas, the streamed parabolas, the
 Riemann solve, the chemistry of one cell, the CFL denominator) are plain C++ apart from a block of
-inline-PTX integer-pipe helpers; this test replaces that block with portable C++ of the same
-definitions, compiles tests/host_math/device_math_vs_oracle.cpp against it and the oracle library,
+inline-PTX helpers (integer-pipe tests, the reciprocal and reciprocal-square-root seeds of the
+Newton-Raphson forms); this test replaces that block with portable C++ of the same definitions, compiles tests/host_math/device_math_vs_oracle.cpp against it and the oracle library,
 and checks: the FP64 parabolas equal the oracle's exactly (Sec. 2.1; -0 and +0 count as equal), the streamed ones equal
 the five-point ones bit for bit, the Riemann solve (Sec. 2.4, App. A) is within 1e-12 of the
 oracle's in FP64 and 1e-4 in FP32, the chemistry (Sec. 2.7, App. D; with and without reactions 5-8)
 within 1e-12, the heating/cooling change (Sec. 2.8; with and without Gamma_5 and Lambda_6-8) within
-1e-12 of the gross heating plus cooling and the CFL
+1e-12 of the gross heating plus cooling, the Newton-Raphson reciprocal, reciprocal square root
+and square root within 2 ulp of the correctly rounded values, and the CFL
 denominator (Sec. 2.3) within 1e-13.  The host build uses -ffp-contract=off like the oracle; the
 GPU build contracts to FMA, whose effect the GPU parity tests bound."""
 import os
@@ -20,7 +21,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "paper_1608_08748_gb300", "csrc", "mhd_device.cuh")
 HARNESS = os.path.join(ROOT, "tests", "host_math", "device_math_vs_oracle.cpp")
-BEGIN, END = "// ---- begin integer-pipe helpers ----", "// ---- end integer-pipe helpers ----"
+BEGIN, END = "// ---- begin inline-PTX helpers ----", "// ---- end inline-PTX helpers ----"
 
 # portable C++ with the definitions of the inline-PTX helpers (sign, magnitude and ordering of the
 # bit patterns of doubles; the float overloads are the plain operations)
@@ -45,10 +46,17 @@ inline bool same_sign(double a, double b) {
 inline bool same_sign(float a, float b) { return a * b > 0.f; }
 inline bool sign_bit_b(double x) { return bits_(x) < 0; }
 inline bool sign_bit_b(float x) { return std::signbit(x); }
+// approximate seeds: the correctly rounded value with its low 30 mantissa bits cleared (a relative
+// error below 2^-22, like the hardware approximations'); subnormal arguments flush to zero
+inline double seed_(double v) { return from_bits_(bits_(v) & ~((1LL << 30) - 1)); }
+inline double ftz_(double x) { return std::fabs(x) < 2.2250738585072014e-308 ? std::copysign(0.0, x) : x; }
+inline double rcp_seed(double x) { return seed_(1.0 / ftz_(x)); }
+inline double rsqrt_seed(double x) { return seed_(1.0 / std::sqrt(ftz_(x))); }
 '''
 
 BOUNDS = {"ppm_lean_equal": 0, "ppm_stream_bits": 0, "ppm_fp32": 0, "riemann_fp64": 0, "riemann_fp32": 0,
-          "chemistry": 0, "heatcool": 0, "chemistry_ions": 0, "heatcool_ions": 0, "cfl": 0}
+          "chemistry": 0, "heatcool": 0, "chemistry_ions": 0, "heatcool_ions": 0, "cfl": 0,
+          "newton_raphson_ulp": 0}
 
 
 def _cuda_include():
