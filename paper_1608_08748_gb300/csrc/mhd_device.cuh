@@ -308,7 +308,12 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
       qL = qLp;
       qR = qRp;
     } else if (gt_nn(num_s, T(0.05) * abs_b(den))) {
-      const T eta = num / den;
+      // eta by the Newton-Raphson reciprocal in FP64 (den is nonzero here)
+      T eta;
+      if constexpr (sizeof(T) == 8)
+        eta = num * rcp_nr(den);
+      else
+        eta = num / den;
       T hb = T(20) * (eta - T(0.05));
       hb = hb < T(1) ? hb : T(1);
       if (hb > T(0)) {
