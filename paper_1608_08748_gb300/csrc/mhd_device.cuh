@@ -658,9 +658,15 @@ __device__ __forceinline__ ChemOut chem_cell(const Phys& ph, double rho, double 
                                              double rhp, double tau) {
   const double P0 = ChemConst::MH * ChemConst::KMS * ChemConst::KMS;  // code pressure, erg cm^-3
   const double T0 = ChemConst::PC / ChemConst::KMS;                  // code time, s
-  const double nH = IONS ? rho - rh2 - rhp : rho - rh2, nH2 = 0.5 * rh2, n = rho;
+  // the ion terms are added to the H/H2 expressions with explicit FMAs, so that a box without ions
+  // gets the same bits from either instance (rhp = 0 then adds exactly nothing)
+  double nH = rho - rh2;
+  if (IONS) nH = nH - rhp;
+  const double nH2 = 0.5 * rh2, n = rho;
   const double num = (2.0 * P0) * eint;
-  const double den = (3.0 * (IONS ? nH + 2.0 * rhp : nH) + 5.0 * nH2) * ChemConst::KB;
+  double den3 = fma(3.0, nH, 5.0 * nH2);  // 3 n_1 + 5 n_H2 with n_1 = n_H + n_H+ + n_e
+  if (IONS) den3 = fma(6.0, rhp, den3);
+  const double den = den3 * ChemConst::KB;
   const double r = rcp_nr(num * den);
   const double T = (num * num) * r, iT = (den * den) * r;
   // App. D rates
@@ -725,8 +731,12 @@ __device__ __forceinline__ double heatcool_delta(const Phys& ph, double rho, dou
   const double P0 = ChemConst::MH * ChemConst::KMS * ChemConst::KMS;  // erg cm^-3
   const double T0 = ChemConst::PC / ChemConst::KMS;                  // s
   const double KB_EV = 8.617333262e-5;                               // eV / K
-  const double nH = IONS ? rho - rh2 - rhp : rho - rh2, nH2 = 0.5 * rh2, n = rho;
-  const double T = ((2.0 * P0) * eint) / ((3.0 * (IONS ? nH + 2.0 * rhp : nH) + 5.0 * nH2) * ChemConst::KB);
+  double nH = rho - rh2;
+  if (IONS) nH = nH - rhp;
+  const double nH2 = 0.5 * rh2, n = rho;
+  double den3 = fma(3.0, nH, 5.0 * nH2);
+  if (IONS) den3 = fma(6.0, rhp, den3);
+  const double T = ((2.0 * P0) * eint) / (den3 * ChemConst::KB);
   const double x = log10(T * 1e-4);
   // k1' and k4 (App. D, as in chem_cell)
   const double t2 = T * 0.01, s2 = sqrt(t2);

@@ -80,3 +80,35 @@ def test_batch_of_one_matches_the_oracle(M, oracle_mod):
     b.sync()
     o = oracle_mod.run(ic, steps=5)
     compare(g.get_state(), o.get_state())
+
+
+def make_chem(M, precision, k):
+    """Boxes with H/H2 chemistry: with the H+ network (k = 0), with heating/cooling (k = 1), plain (k = 2)."""
+    ic = dict(I.turbulence(8, mach=2.0 + k, beta=0.5, seed=50 + k, shape=SHAPES[k], T_K=3000.0))
+    ic["rho_h2"] = 0.05 * ic["rho"]
+    opts = dict(ic["options"])
+    if k == 0:
+        ic["rho_hp"] = 0.01 * ic["rho"]
+        opts.update(ions=1, heatcool=1)
+    elif k == 1:
+        opts.update(heatcool=1)
+    ic["options"] = opts
+    return M.from_ic(ic, precision=precision)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_with_ions_equals_solo_bitwise(M, precision):
+    # a batch with one H+ box runs the kernels with the ion code for every box; the other boxes must
+    # still evolve exactly as alone (where the kernels without the ion code run)
+    solo = [make_chem(M, precision, k) for k in range(3)]
+    mixed = [make_chem(M, precision, k) for k in range(3)]
+    batch = M.Batch(mixed)
+    for _ in range(6):
+        for s in solo:
+            s.step(0.4, sync=False)
+        batch.step(0.4)
+    batch.sync()
+    for s, m in zip(solo, mixed):
+        s.sync()
+        assert_same(s.get_state(), m.get_state())
+        assert np.array_equal(s.get_ions(), m.get_ions())
