@@ -96,6 +96,12 @@ struct Exec {
   int nsm = 152;
   Profiler* prof = nullptr;
   bool ions = false;      // some box has H+ (reactions 5-8): the kernels with the ion code
+  // The three directional sweeps of a stage are independent (each reads the cells and writes its
+  // own face arrays): the y and z sweeps run on two side streams forked from and joined to the
+  // launching stream, so that each sweep's tail overlaps the others' work.  In a captured step the
+  // fork and join become graph edges.
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork_ev = nullptr, join_ev[2] = {nullptr, nullptr};
 };
 
 template <typename T>
@@ -196,6 +202,16 @@ cudaError_t exec_init(Exec<T>& X, const std::vector<Box<T>>& boxes) {
   X.nb = (int)boxes.size();
   X.ions = false;
   for (const Box<T>& b : boxes) X.ions = X.ions || (b.ph.chem && b.ph.ions);
+  if (!X.side[0]) {
+    for (int k = 0; k < 2; ++k) {
+      cudaError_t es = cudaStreamCreateWithFlags(&X.side[k], cudaStreamNonBlocking);
+      if (es != cudaSuccess) return es;
+      es = cudaEventCreateWithFlags(&X.join_ev[k], cudaEventDisableTiming);
+      if (es != cudaSuccess) return es;
+    }
+    cudaError_t es = cudaEventCreateWithFlags(&X.fork_ev, cudaEventDisableTiming);
+    if (es != cudaSuccess) return es;
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&X.nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -221,6 +237,14 @@ void exec_free(Exec<T>& X) {
   X.d = nullptr;
   X.nb = 0;
   X.h.clear();
+  for (int k = 0; k < 2; ++k) {
+    if (X.side[k]) cudaStreamDestroy(X.side[k]);
+    if (X.join_ev[k]) cudaEventDestroy(X.join_ev[k]);
+    X.side[k] = nullptr;
+    X.join_ev[k] = nullptr;
+  }
+  if (X.fork_ev) cudaEventDestroy(X.fork_ev);
+  X.fork_ev = nullptr;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -249,6 +273,26 @@ void launch_small(Exec<T>& X, cudaStream_t st, int which, double cfl = 0, double
   if (which == 3) kb_zero_dmax<T><<<g, 128, 0, st>>>(X.d, X.nb);
 }
 
+// the x, y, z sweeps sw(dir, stream): forked onto the side streams, or in order on st while the
+// per-class profiler runs (its events bracket launches on st)
+template <typename T, typename F>
+void launch_sweeps(Exec<T>& X, cudaStream_t st, F sw) {
+  if (!X.side[0] || (X.prof && X.prof->on)) {
+    for (int d = 0; d < 3; ++d) sw(d, st);
+    return;
+  }
+  cudaEventRecord(X.fork_ev, st);
+  cudaStreamWaitEvent(X.side[0], X.fork_ev, 0);
+  cudaStreamWaitEvent(X.side[1], X.fork_ev, 0);
+  sw(0, st);
+  sw(1, X.side[0]);
+  sw(2, X.side[1]);
+  for (int k = 0; k < 2; ++k) {
+    cudaEventRecord(X.join_ev[k], X.side[k]);
+    cudaStreamWaitEvent(st, X.join_ev[k], 0);
+  }
+}
+
 template <typename T>
 void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
   // self-gravity: a box with a potential (such sims step alone, never in a batch)
@@ -258,9 +302,11 @@ void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
       launch_k(X, st, KC_PRIM, DOM_CELLS, kb_prim<T, true>);
     else
       launch_k(X, st, KC_PRIM, DOM_CELLS, kb_prim<T, false>);
-    launch_ks(X, st, KC_EFACE, DOM_PENCIL_X, euler_pencil_smem<T>(), kb_euler_pencil<T, 0>);
-    launch_ks(X, st, KC_EFACE, DOM_PENCIL_Y, euler_pencil_smem<T>(), kb_euler_pencil<T, 1>);
-    launch_ks(X, st, KC_EFACE, DOM_PENCIL_Z, euler_pencil_smem<T>(), kb_euler_pencil<T, 2>);
+    launch_sweeps(X, st, [&](int d, cudaStream_t s) {
+      if (d == 0) launch_ks(X, s, KC_EFACE, DOM_PENCIL_X, euler_pencil_smem<T>(), kb_euler_pencil<T, 0>);
+      if (d == 1) launch_ks(X, s, KC_EFACE, DOM_PENCIL_Y, euler_pencil_smem<T>(), kb_euler_pencil<T, 1>);
+      if (d == 2) launch_ks(X, s, KC_EFACE, DOM_PENCIL_Z, euler_pencil_smem<T>(), kb_euler_pencil<T, 2>);
+    });
     launch_k(X, st, KC_EDGES, DOM_LATTICE, kb_edges<T>);
     if (grav)
       launch_k(X, st, KC_EUPD, DOM_CELLS, kb_euler_update<T, true>, r);
@@ -272,27 +318,31 @@ void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
 template <typename T>
 void launch_lag_stage(Exec<T>& X, cudaStream_t st) {
   for (int r = 0; r < 3; ++r) {
-    if constexpr (lag_in_pencils<T>()) {
-      if (X.ions) {
-        launch_k(X, st, KC_LFACE, DOM_PENCIL_X, kb_lag_pencil<T, 0, true>);
-        launch_k(X, st, KC_LFACE, DOM_PENCIL_Y, kb_lag_pencil<T, 1, true>);
-        launch_k(X, st, KC_LFACE, DOM_PENCIL_Z, kb_lag_pencil<T, 2, true>);
+    launch_sweeps(X, st, [&](int d, cudaStream_t s) {
+      if constexpr (lag_in_pencils<T>()) {
+        const int dom = DOM_PENCIL_X + d;
+        if (X.ions) {
+          if (d == 0) launch_k(X, s, KC_LFACE, dom, kb_lag_pencil<T, 0, true>);
+          if (d == 1) launch_k(X, s, KC_LFACE, dom, kb_lag_pencil<T, 1, true>);
+          if (d == 2) launch_k(X, s, KC_LFACE, dom, kb_lag_pencil<T, 2, true>);
+        } else {
+          if (d == 0) launch_k(X, s, KC_LFACE, dom, kb_lag_pencil<T, 0, false>);
+          if (d == 1) launch_k(X, s, KC_LFACE, dom, kb_lag_pencil<T, 1, false>);
+          if (d == 2) launch_k(X, s, KC_LFACE, dom, kb_lag_pencil<T, 2, false>);
+        }
       } else {
-        launch_k(X, st, KC_LFACE, DOM_PENCIL_X, kb_lag_pencil<T, 0, false>);
-        launch_k(X, st, KC_LFACE, DOM_PENCIL_Y, kb_lag_pencil<T, 1, false>);
-        launch_k(X, st, KC_LFACE, DOM_PENCIL_Z, kb_lag_pencil<T, 2, false>);
+        const int dom = DOM_FACE_X + d;
+        if (X.ions) {
+          if (d == 0) launch_k(X, s, KC_LFACE, dom, kb_lag_face<T, 0, true>);
+          if (d == 1) launch_k(X, s, KC_LFACE, dom, kb_lag_face<T, 1, true>);
+          if (d == 2) launch_k(X, s, KC_LFACE, dom, kb_lag_face<T, 2, true>);
+        } else {
+          if (d == 0) launch_k(X, s, KC_LFACE, dom, kb_lag_face<T, 0, false>);
+          if (d == 1) launch_k(X, s, KC_LFACE, dom, kb_lag_face<T, 1, false>);
+          if (d == 2) launch_k(X, s, KC_LFACE, dom, kb_lag_face<T, 2, false>);
+        }
       }
-    } else {
-      if (X.ions) {
-        launch_k(X, st, KC_LFACE, DOM_FACE_X, kb_lag_face<T, 0, true>);
-        launch_k(X, st, KC_LFACE, DOM_FACE_Y, kb_lag_face<T, 1, true>);
-        launch_k(X, st, KC_LFACE, DOM_FACE_Z, kb_lag_face<T, 2, true>);
-      } else {
-        launch_k(X, st, KC_LFACE, DOM_FACE_X, kb_lag_face<T, 0, false>);
-        launch_k(X, st, KC_LFACE, DOM_FACE_Y, kb_lag_face<T, 1, false>);
-        launch_k(X, st, KC_LFACE, DOM_FACE_Z, kb_lag_face<T, 2, false>);
-      }
-    }
+    });
     if (X.ions)
       launch_k(X, st, KC_LUPD, DOM_CELLS, kb_lag_update<T, true>, r);
     else
