@@ -453,16 +453,27 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
   // E + shy (d + sgn q6 w) with E = q^R of the left cell (v_n >= 0, sgn = -1) or q^L of the right
   // cell (sgn = +1), shy = sgn y / 2 and w = 1 - 2y/3 (the two forms of Sec. 2.4)
   T vn[PENCIL], shy[PENCIL], w[PENCIL];
+  // v_n = (v_l sqrt(rho_l) + v_r sqrt(rho_r)) / (sqrt(rho_l) + sqrt(rho_r)) from the per-cell
+  // m / sqrt(rho) and rho / sqrt(rho) = sqrt(rho), each formed once and carried to the next face
+  T al, bl;
+  {
+    const idx_t c0 = cell_at(f0 - 1);
+    const T r0 = B.s.rho[c0], is0 = rsqrt_t(r0);
+    al = B.s.m[D][c0] * is0;
+    bl = r0 * is0;
+  }
 #pragma unroll
   for (int k = 0; k < PENCIL; ++k) {
     vn[k] = T(0);
     shy[k] = T(0);
     w[k] = T(1);
     if (k < nfp) {
-      const idx_t cl = cell_at(f0 + k - 1), cr = cell_at(f0 + k);
-      const T rl = B.s.rho[cl], rr = B.s.rho[cr];
-      const T isl = rsqrt_t(rl), isr = rsqrt_t(rr);
-      vn[k] = (B.s.m[D][cl] * isl + B.s.m[D][cr] * isr) * rcp_t(rl * isl + rr * isr);
+      const idx_t cr = cell_at(f0 + k);
+      const T rr = B.s.rho[cr], isr = rsqrt_t(rr);
+      const T ar = B.s.m[D][cr] * isr, br = rr * isr;
+      vn[k] = (al + ar) * rcp_t(bl + br);
+      al = ar;
+      bl = br;
       const T y = abs_b(vn[k]) * tau_h;
       const T hy = T(0.5) * y;
       shy[k] = vn[k] >= T(0) ? neg_b(hy) : hy;
