@@ -588,7 +588,7 @@ __device__ __forceinline__ double cfl_denominator(double rho, double mx, double 
 template <typename T>
 __device__ __forceinline__ T gamma_eff(T rho, T rh2) {
   T nH = rho - rh2, nH2 = T(0.5) * rh2;
-  return (T(5) * nH + T(7) * nH2) / (T(3) * nH + T(5) * nH2);
+  return (T(5) * nH + T(7) * nH2) * rcp_t(T(3) * nH + T(5) * nH2);
 }
 
 // ... and with H+ and electrons: the monatomic particles n_1 = n_H + n_H+ + n_e replace n_H, with
@@ -596,7 +596,7 @@ __device__ __forceinline__ T gamma_eff(T rho, T rh2) {
 template <typename T>
 __device__ __forceinline__ T gamma_eff(T rho, T rh2, T rhp) {
   T n1 = (rho - rh2 - rhp) + T(2) * rhp, nH2 = T(0.5) * rh2;
-  return (T(5) * n1 + T(7) * nH2) / (T(3) * n1 + T(5) * nH2);
+  return (T(5) * n1 + T(7) * nH2) * rcp_t(T(3) * n1 + T(5) * nH2);
 }
 
 // ------------------------------------------------------------------------------------------------

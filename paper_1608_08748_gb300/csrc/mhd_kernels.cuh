@@ -103,11 +103,12 @@ __device__ __forceinline__ void prim_cell(const Box<T>& B, idx_t c) {
   // gamma_eff in the bulk type: the FP32-bulk path's fluxes are FP32
   T gmt = !B.ph.chem ? (T)B.ph.gamma
           : (IONS && B.ph.ions) ? gamma_eff(rho, B.s.rh2[c], B.s.rhp[c]) : gamma_eff(rho, B.s.rh2[c]);
+  const T irho = rcp_t(rho);  // one reciprocal for the three velocities
 #pragma unroll
-  for (int d = 0; d < 3; ++d) B.w.v[d][c] = B.s.m[d][c] / rho;
+  for (int d = 0; d < 3; ++d) B.w.v[d][c] = B.s.m[d][c] * irho;
   B.w.p[c] = (gmt - T(1)) * B.s.eint[c];
   B.w.g[c] = gmt;
-  B.w.sr[c] = sqrt(rho);
+  B.w.sr[c] = sqrt_t(rho);
 }
 
 template <typename T, bool IONS>
@@ -289,19 +290,23 @@ __global__ void __launch_bounds__(512) kb_edges(const Box<T>* __restrict__ boxes
   }
 }
 
-// SSP-RK3 combination of Sec. 2.2 for one value: a Q^n + b Q + g tau R.  The first substage has
-// a = 0 and stores Q^n (the stage's start value, the Q it reads) in the RK register instead of
-// reading it; later substages read it.
+// SSP-RK3 combination of Sec. 2.2 for one value: a Q^n + b Q + g tau R, with g tau R = gth S for a
+// flux-difference sum S (R = S / h, gth = g tau / h once per thread).  The first substage has
+// a = 0, b = g = 1: it stores Q^n (the stage's start value, the Q it reads) in the RK register and
+// returns Q + gth S; later substages read the register.  (The FP64 update kernels are bound by the
+// FP64 pipe, so the constants are folded.)
 template <typename T>
-__device__ __forceinline__ T rk_combine(T* qn, T q, T a, T b, T g, T tauR, int r) {
-  T q0;
+__device__ __forceinline__ T rk_combine(T* qn, T q, T a, T b, T gthS, int r) {
   if (r == 0) {
     *qn = q;
-    q0 = q;
-  } else {
-    q0 = *qn;
+    return q + gthS;
   }
-  return (a * q0 + b * q) + g * tauR;
+  return (a * *qn + b * q) + gthS;
+}
+// g tau / h of substage r
+template <typename T>
+__device__ __forceinline__ T rk_gth(const Box<T>& B, int r) {
+  return (T)(RK3_G(r) * B.sc->tau * B.ph.ih);
 }
 
 // Eulerian update of one cell: finite-volume R of m, rho E, rho eps (Sec. 2.4 + A12), Flux-CT of
@@ -311,12 +316,11 @@ __device__ __forceinline__ void euler_update_cell(const Box<T>& B, idx_t c, int 
   const Geom& g = B.g;
   int q[3];
   decode(c, g.n[0], g.n[1], q);
-  const T a = (T)RK3_A(r), bb = (T)RK3_B(r), gg = (T)RK3_G(r);
-  const T tau = (T)B.sc->tau;
-  const T ih = (T)B.ph.ih;
+  const T a = (T)RK3_A(r), bb = (T)RK3_B(r), gth = rk_gth(B, r);
   idx_t f0 = fidx(g, q[0], q[1], q[2]);
   idx_t fup[3] = {fidx(g, q[0] + 1, q[1], q[2]), fidx(g, q[0], q[1] + 1, q[2]), fidx(g, q[0], q[1], q[2] + 1)};
-  T acc[5] = {T(0), T(0), T(0), T(0), T(0)};  // m_x, m_y, m_z, rho E, -h div V
+  // -0 + x is x for every x, so the first addition to each sum folds away
+  T acc[5] = {T(-0.0), T(-0.0), T(-0.0), T(-0.0), T(-0.0)};  // m_x, m_y, m_z, rho E, -h div V
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
@@ -327,10 +331,10 @@ __device__ __forceinline__ void euler_update_cell(const Box<T>& B, idx_t c, int 
     acc[3] = acc[3] + (o.f[3][f0] - o.f[3][fup[d]]);
     acc[4] = acc[4] + (o.f[4][f0] - o.f[4][fup[d]]);
   }
-  T Rv[5];
+  T Rv[5];  // h R: the flux-difference sums, and -(gamma - 1) rho eps h div V
 #pragma unroll
-  for (int v = 0; v < 4; ++v) Rv[v] = acc[v] * ih;
-  Rv[4] = ((B.w.g[c] - T(1)) * B.s.eint[c]) * (acc[4] * ih);  // -(gamma - 1) rho eps div V
+  for (int v = 0; v < 4; ++v) Rv[v] = acc[v];
+  Rv[4] = ((B.w.g[c] - T(1)) * B.s.eint[c]) * acc[4];
   if (GRAV) {
     // self-gravity (Sec. 2): -rho grad Phi and -rho v . grad Phi, central differences of the
     // potential of the step (periodic box); a separate instance, so that the update without
@@ -340,7 +344,7 @@ __device__ __forceinline__ void euler_update_cell(const Box<T>& B, idx_t c, int 
     const T rho = B.s.rho[c];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const T gd = -(B.phi[upc[d]] - B.phi[dn[d]]) * (T(0.5) * ih);
+      const T gd = -(B.phi[upc[d]] - B.phi[dn[d]]) * T(0.5);  // h (-d Phi / dx_d)
       Rv[d] = Rv[d] + rho * gd;
       Rv[3] = Rv[3] + B.s.m[d][c] * gd;
     }
@@ -348,14 +352,13 @@ __device__ __forceinline__ void euler_update_cell(const Box<T>& B, idx_t c, int 
   T* qq[5] = {B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint};
   T* q0[5] = {B.s0.m[0], B.s0.m[1], B.s0.m[2], B.s0.E, B.s0.eint};
 #pragma unroll
-  for (int v = 0; v < 5; ++v) qq[v][c] = rk_combine(q0[v] + c, qq[v][c], a, bb, gg, tau * Rv[v], r);
+  for (int v = 0; v < 5; ++v) qq[v][c] = rk_combine(q0[v] + c, qq[v][c], a, bb, gth * Rv[v], r);
   // Flux-CT: d b_d / dt = -(curl E)_d on the face i_d - 1/2 of this cell
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
     T curl = (B.e[d1][fup[d2]] - B.e[d1][f0]) - (B.e[d2][fup[d1]] - B.e[d2][f0]);
-    T Rb = curl * ih;
-    B.s.b[d][c] = rk_combine(B.s0.b[d] + c, B.s.b[d][c], a, bb, gg, tau * Rb, r);
+    B.s.b[d][c] = rk_combine(B.s0.b[d] + c, B.s.b[d][c], a, bb, gth * curl, r);
   }
 }
 
@@ -522,9 +525,7 @@ __device__ __forceinline__ void lag_update_cell(const Box<T>& B, idx_t c, int r)
   const Geom& g = B.g;
   int q[3];
   decode(c, g.n[0], g.n[1], q);
-  const T a = (T)RK3_A(r), bb = (T)RK3_B(r), gg = (T)RK3_G(r);
-  const T tau = (T)B.sc->tau;
-  const T ih = (T)B.ph.ih;
+  const T a = (T)RK3_A(r), bb = (T)RK3_B(r), gth = rk_gth(B, r);
   idx_t f0 = fidx(g, q[0], q[1], q[2]);
   idx_t fup[3] = {fidx(g, q[0] + 1, q[1], q[2]), fidx(g, q[0], q[1] + 1, q[2]), fidx(g, q[0], q[1], q[2] + 1)};
   T* qq[8] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2, B.s.rhp};
@@ -533,11 +534,10 @@ __device__ __forceinline__ void lag_update_cell(const Box<T>& B, idx_t c, int r)
 #pragma unroll
   for (int v = 0; v < (IONS ? 8 : 7); ++v) {
     if (v >= nv) break;
-    T acc = T(0);
+    T acc = T(-0.0);  // -0 + x is x: the first addition folds away
 #pragma unroll
     for (int d = 0; d < 3; ++d) acc = acc + (B.fo[d].f[v][f0] - B.fo[d].f[v][fup[d]]);
-    T R = acc * ih;
-    qq[v][c] = rk_combine(q0[v] + c, qq[v][c], a, bb, gg, tau * R, r);
+    qq[v][c] = rk_combine(q0[v] + c, qq[v][c], a, bb, gth * acc, r);
   }
 }
 
