@@ -219,6 +219,23 @@ __device__ __forceinline__ bool sign_bit_b(double x) {
 }
 __device__ __forceinline__ bool sign_bit_b(float x) { return signbit(x); }
 
+// x 2^-K (K = 1, 2) on the integer pipe: the exponent field lowered by K.  Equal to the FP64
+// product wherever that is a normal double, a zero, an infinity or a NaN; a product below the
+// normal range (|x| < 2^(K-1021)) is taken as the zero of the sign of x.
+template <int K>
+__device__ __forceinline__ double scale_down_b(double x) {
+  double r;
+  asm("{\n\t.reg .b32 lo, hi, e, s, t, l;\n\t.reg .pred p, q;\n\tmov.b64 {lo, hi}, %1;\n\t"
+      "bfe.u32 e, hi, 20, 11;\n\tsetp.gt.u32 p, e, %2;\n\tsetp.eq.u32 q, e, 2047;\n\t"
+      "and.b32 s, hi, 0x80000000;\n\tsub.u32 t, hi, %3;\n\tselp.b32 t, t, s, p;\n\t"
+      "selp.b32 l, lo, 0, p;\n\tselp.b32 t, hi, t, q;\n\tselp.b32 l, lo, l, q;\n\t"
+      "mov.b64 %0, {l, t};\n\t}"
+      : "=d"(r) : "d"(x), "n"(K), "n"(K << 20));
+  return r;
+}
+template <int K>
+__device__ __forceinline__ float scale_down_b(float x) { return x * (1.0f / (float)(1 << K)); }
+
 // Approximate reciprocal and reciprocal square root of a double (PTX rcp.approx.ftz.f64,
 // rsqrt.approx.ftz.f64): seeds for the Newton-Raphson steps below.  Subnormal arguments count as 0.
 __device__ __forceinline__ double rcp_seed(double x) {
@@ -272,7 +289,7 @@ __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
 template <typename T>
 __device__ __forceinline__ T half_slope(T s, T dn, T dp) {
   if (!same_sign(dn, dp)) return T(0);
-  T m = min_nn(min_nn(T(0.25) * abs_b(s), abs_b(dp)), abs_b(dn));
+  T m = min_nn(min_nn(scale_down_b<2>(abs_b(s)), abs_b(dp)), abs_b(dn));
   return with_sign_b(m, s);
 }
 
@@ -346,8 +363,8 @@ __device__ __forceinline__ Para<T> ppm_lean(T qm2, T qm1, T qc, T qp1, T qp2) {
   const T sm = qc - qm2, s0 = qp1 - qm1, sp = qp2 - qc;
   const T hm = half_slope(sm, d0, d1), h0 = half_slope(s0, d1, d2), hp = half_slope(sp, d2, d3);
   // Step 1: edge values (dm0 - dmm) / 6 = (h0 - hm) / 3
-  const T qL = T(0.5) * (qm1 + qc) - (h0 - hm) * THIRD;
-  const T qR = T(0.5) * (qc + qp1) - (hp - h0) * THIRD;
+  const T qL = scale_down_b<1>(qm1 + qc) - (h0 - hm) * THIRD;
+  const T qR = scale_down_b<1>(qc + qp1) - (hp - h0) * THIRD;
   // second differences D+ = q_{i+2} - 2 q_{i+1} + q_i, D- = q_i - 2 q_{i-1} + q_{i-2}
   const T Dp = (qp2 - T(2) * qp1) + qc;
   const T Dm = (qc - T(2) * qm1) + qm2;
@@ -374,7 +391,7 @@ struct PPMStream {
     const T hm = half_slope(qc - qa, d0, d1);
     s0 = qd - qb;
     h0 = half_slope(s0, d1, d2);
-    eL = T(0.5) * (qb + qc) - (h0 - hm) * THIRD;
+    eL = scale_down_b<1>(qb + qc) - (h0 - hm) * THIRD;
     Cm = (qc - T(2) * qb) + qa;
     C0 = (qd - T(2) * qc) + qb;
     qm = qb;
@@ -388,7 +405,7 @@ struct PPMStream {
     const T s1 = qn - q0;
     const T h1 = half_slope(s1, dp, d2);
     const T C1 = (qn - T(2) * qp) + q0;
-    const T eR = T(0.5) * (q0 + qp) - (h1 - h0) * THIRD;
+    const T eR = scale_down_b<1>(q0 + qp) - (h1 - h0) * THIRD;
     Para<T> P = ppm_limit(eL, eR, q0, h0, C1, Cm, s0, qp, qm);
     qm = q0;
     q0 = qp;
@@ -521,7 +538,7 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
   // R s_+ + (S R) s_- is R (s_+ - s_-) on v_n, v_t1, v_t2 and R (s_+ + s_-) on B_t1, B_t2, P.
   auto magnetosonic_pair = [&](const T L[6], const T R[6], T speed) {
     const T y = speed * tau_h;
-    const T hy = T(0.5) * y, w = T(1) - TWO_THIRDS * y;
+    const T hy = scale_down_b<1>(y), w = T(1) - TWO_THIRDS * y;
     T pa = T(0), pb = T(0), ma = T(0), mb = T(0);
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
@@ -544,7 +561,7 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
   // Alfven pair: the v_t rows are shared, the B_t rows change sign
   auto alfven_pair = [&]() {
     const T y = ca * tau_h;
-    const T hy = T(0.5) * y, w = T(1) - TWO_THIRDS * y;
+    const T hy = scale_down_b<1>(y), w = T(1) - TWO_THIRDS * y;
     T qp[5], qm[5];
 #pragma unroll
     for (int m = 1; m < 5; ++m) {
