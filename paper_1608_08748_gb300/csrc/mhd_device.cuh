@@ -299,15 +299,17 @@ __device__ __forceinline__ T half_slope(T s, T dn, T dp) {
 // bound.
 template <typename T>
 __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm, T s0, T qp1, T qm1) {
+  // 6 q_c once per parabola (FP64); 3 q_c = (6 q_c) / 2 exactly
+  const T six_qc = T(6) * qc;
   // Step 2: monotonicity
   {
     const T dq = qR - qL;
-    const T q6 = T(6) * (qc - T(0.5) * (qL + qR));
+    const T q6 = six_qc - T(3) * (qL + qR);
     const bool ext = !same_sign(qL - qc, qc - qR);
     const T a = dq * q6, b = dq * dq;
     const bool up = gt_nn(a, b), dn = !up && gt_nn(neg_b(a), b);
     // the two overshoot fixes are exclusive: one candidate 3 qc - 2 q from the opposite edge
-    const T cand = T(3) * qc - T(2) * (up ? qR : qL);
+    const T cand = scale_down_b<1>(six_qc) - T(2) * (up ? qR : qL);
     const T qLm = ext ? qc : (up ? cand : qL);
     const T qRm = ext ? qc : (dn ? cand : qR);
     qL = qLm;
@@ -319,12 +321,14 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
     const T num = Dm - Dp, den = T(3) * s0;  // eta = num / den, den != 0 here
     const T num_s = sign_bit_b(den) ? neg_b(num) : num;
     const T qLp = qc - T(0.5) * h0, qRp = qc + T(0.5) * h0;
-    if (sizeof(T) == 8 && gt_nn(num_s, T(0.1) * abs_b(den))) {
+    // eta > 1/10 as num_s / 2 > |den| / 20 (halving is exact), so that one product serves both tests
+    const T ad20 = T(0.05) * abs_b(den);
+    if (sizeof(T) == 8 && gt_nn(scale_down_b<1>(num_s), ad20)) {
       // eta > 1/10: hbar = 1, the flattened values themselves (no FP64 division; in FP32 the
       // division is cheaper than the branch)
       qL = qLp;
       qR = qRp;
-    } else if (gt_nn(num_s, T(0.05) * abs_b(den))) {
+    } else if (gt_nn(num_s, ad20)) {
       // eta by the Newton-Raphson reciprocal in FP64 (den is nonzero here)
       T eta;
       if constexpr (sizeof(T) == 8)
@@ -344,7 +348,7 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
   P.L = qL;
   P.R = qR;
   P.d = qR - qL;
-  P.q6 = T(6) * (qc - T(0.5) * (qL + qR));
+  P.q6 = six_qc - T(3) * (qL + qR);
   return P;
 }
 
@@ -513,7 +517,7 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
   }
   const T sg = Bn >= T(0) ? T(1) : T(-1);
   const T sqr = rho * rs, sc = sqr * c, sr2 = sqr * INV_SQRT2;
-  const T i2c2 = T(0.5) * (rc * rc), i2sc = T(0.5) * (rs * rc), i2rc2 = i2c2 * irho;
+  const T i2c2 = scale_down_b<1>(rc * rc), i2sc = scale_down_b<1>(rs * rc), i2rc2 = i2c2 * irho;
   const T isr2 = rs * INV_SQRT2;
 
   // App. A rows of the +c_f and +c_s waves; the -c waves negate the v_n, v_t1, v_t2 entries

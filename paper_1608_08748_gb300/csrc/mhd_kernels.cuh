@@ -478,7 +478,7 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
       al = ar;
       bl = br;
       const T y = abs_b(vn[k]) * tau_h;
-      const T hy = T(0.5) * y;
+      const T hy = scale_down_b<1>(y);
       shy[k] = vn[k] >= T(0) ? neg_b(hy) : hy;
       w[k] = T(1) - TWO_THIRDS * y;
     }

@@ -64,15 +64,16 @@ int main() {
       o_ppm(q, 0, o);
       const Para<double> P = ppm_lean(q[0], q[1], q[2], q[3], q[4]);
       const double d[4] = {P.L, P.R, P.d, P.q6};
-      // IEEE equality (-0 and +0 are the same value; the bit helpers may differ there), except in the
-      // Step 4 blend, whose eta comes from the Newton-Raphson reciprocal: there within 1e-15 of the
-      // largest |q| of the stencil
+      // within 3e-15 of the largest |q| of the stencil: q6 is formed as 6 q_c - 3 (q_L + q_R), two
+      // roundings of values up to 6 max|q| on each side (at most 4 ulp of 6 max|q|, 2.7e-15), and the
+      // Step 4 blend's eta comes from the Newton-Raphson reciprocal; q_L, q_R and Delta q outside the
+      // blend are the oracle's bits
       double sc = 0;
       for (int i = 0; i < 5; ++i) sc = std::max(sc, std::fabs(q[i]));
       double e = 0;
       for (int k = 0; k < 4; ++k) e = std::max(e, std::fabs(d[k] - o[k]) / (sc + 1e-300));
       worst = std::max(worst, e);
-      if (e > 1e-15) ++bad;
+      if (e > 3e-15) ++bad;
     }
     report("ppm_lean_close", n, worst, bad);
   }
