@@ -219,6 +219,16 @@ __device__ __forceinline__ bool sign_bit_b(double x) {
 }
 __device__ __forceinline__ bool sign_bit_b(float x) { return signbit(x); }
 
+// Ordered key of a double: the signed 64-bit order of the keys is the order of the values, with
+// -0 below +0 (the magnitude bits of a negative value flipped).  Comparisons of keys run on the
+// integer pipe.
+__device__ __forceinline__ long long okey(double x) {
+  long long k;
+  asm("{\n\t.reg .s64 m;\n\tmov.b64 %0, %1;\n\tshr.s64 m, %0, 63;\n\t"
+      "and.b64 m, m, 0x7fffffffffffffff;\n\txor.b64 %0, %0, m;\n\t}" : "=l"(k) : "d"(x));
+  return k;
+}
+
 // x 2^-K (K = 1, 2) on the integer pipe: the exponent field lowered by K.  Equal to the FP64
 // product wherever that is a normal double, a zero, an infinity or a NaN; a product below the
 // normal range (|x| < 2^(K-1021)) is taken as the zero of the sign of x.
@@ -305,9 +315,24 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
   {
     const T dq = qR - qL;
     const T q6 = six_qc - T(3) * (qL + qR);
-    const bool ext = !same_sign(qL - qc, qc - qR);
-    const T a = dq * q6, b = dq * dq;
-    const bool up = gt_nn(a, b), dn = !up && gt_nn(neg_b(a), b);
+    bool ext, up, dn;
+    if constexpr (sizeof(T) == 8) {
+      // the tests as orderings of the values on the integer pipe: (q_L - q_c)(q_c - q_R) > 0 is q_c
+      // strictly between q_L and q_R; dq q6 > dq^2 is q6 beyond dq on the side of its sign, and
+      // -dq q6 > dq^2 is q6 beyond -dq on the other side (exact comparisons instead of rounded
+      // products: the fixes are continuous at the ties, q_L = 3 q_c - 2 q_R there)
+      const long long kL = okey(qL), kc = okey(qc), kR = okey(qR);
+      ext = !((kL > kc && kc > kR) || (kL < kc && kc < kR));
+      const long long kd = okey(dq), k6 = okey(q6), kmd = okey(neg_b(dq));
+      const bool dpos = kd > 0, dneg = kd < -1;  // dq > 0, dq < 0 (keys of +0 and -0: 0 and -1)
+      up = (dpos && k6 > kd) || (dneg && k6 < kd);
+      dn = (dpos && k6 < kmd) || (dneg && k6 > kmd);
+    } else {
+      ext = !same_sign(qL - qc, qc - qR);
+      const T a = dq * q6, b = dq * dq;
+      up = gt_nn(a, b);
+      dn = !up && gt_nn(neg_b(a), b);
+    }
     // the two overshoot fixes are exclusive: one candidate 3 qc - 2 q from the opposite edge
     const T cand = scale_down_b<1>(six_qc) - T(2) * (up ? qR : qL);
     const T qLm = ext ? qc : (up ? cand : qL);

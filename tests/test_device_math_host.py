@@ -52,6 +52,7 @@ inline bool sign_bit_b(float x) { return std::signbit(x); }
 inline double seed_(double v) { return from_bits_(bits_(v) & ~((1LL << 30) - 1)); }
 inline double ftz_(double x) { return std::fabs(x) < 2.2250738585072014e-308 ? std::copysign(0.0, x) : x; }
 inline double rcp_seed(double x) { return seed_(1.0 / ftz_(x)); }
+inline long long okey(double x) { long long k = bits_(x); return k ^ ((k >> 63) & MAG_); }
 template <int K> inline double scale_down_b(double x) {
   const double r = x * (1.0 / (1 << K));
   return std::fabs(r) < 2.2250738585072014e-308 ? std::copysign(0.0, x) : r;
