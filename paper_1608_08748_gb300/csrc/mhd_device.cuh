@@ -343,11 +343,14 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
   // Step 4: discontinuity detector
   const T mn = min_nn(abs_b(qp1), abs_b(qm1));
   if (gt_nn(abs_b(s0), T(0.01) * mn) && !same_sign(Dp, Dm)) {
-    const T num = Dm - Dp, den = T(3) * s0;  // eta = num / den, den != 0 here
-    const T num_s = sign_bit_b(den) ? neg_b(num) : num;
+    // eta = num / den with den = 3 s0 != 0 here; num_s = num sgn(den)
+    const T num = Dm - Dp;
+    const T num_s = sign_bit_b(s0) ? neg_b(num) : num;
     const T qLp = qc - T(0.5) * h0, qRp = qc + T(0.5) * h0;
-    // eta > 1/10 as num_s / 2 > |den| / 20 (halving is exact), so that one product serves both tests
-    const T ad20 = T(0.05) * abs_b(den);
+    // eta > 1/20 as num_s > |den| / 20 = 0.15 |s0| and eta > 1/10 as num_s / 2 > 0.15 |s0| (halving is
+    // exact): one product serves both tests (at the two thresholds hbar is continuous, so their
+    // rounding cannot move the result)
+    const T ad20 = T(0.15) * abs_b(s0);
     if (sizeof(T) == 8 && gt_nn(scale_down_b<1>(num_s), ad20)) {
       // eta > 1/10: hbar = 1, the flattened values themselves (no FP64 division; in FP32 the
       // division is cheaper than the branch)
@@ -357,9 +360,9 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
       // eta by the Newton-Raphson reciprocal in FP64 (den is nonzero here)
       T eta;
       if constexpr (sizeof(T) == 8)
-        eta = num * rcp_nr(den);
+        eta = num * rcp_nr(T(3) * s0);
       else
-        eta = num / den;
+        eta = num / (T(3) * s0);
       T hb = T(20) * (eta - T(0.05));
       hb = hb < T(1) ? hb : T(1);
       if (hb > T(0)) {
@@ -502,10 +505,11 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
   T dcs, dfc;
   if constexpr (sizeof(T) == 8) {
     // one FP64 division for both signs of X, so a warp with both signs does not take two
-    const bool xpos = X >= T(0);
+    const bool xpos = !sign_bit_b(X);  // at X = 0 either form holds
     T big = xpos ? T(0.5) * ((X + sq) - bp2r) : T(0.5) * ((bp2r - X) + sq);
-    if (big < T(0)) big = T(0);
-    const T other = big >= T(2.2250738585072014e-308) ? (c2 * bp2r) * rcp_t(big) : big > T(0) ? c2 * bp2r / big : T(0);
+    big = sign_bit_b(big) ? T(0) : big;
+    const T other = !gt_nn(T(2.2250738585072014e-308), big) ? (c2 * bp2r) * rcp_t(big)
+                    : gt_nn(big, T(0)) ? c2 * bp2r / big : T(0);
     dcs = xpos ? big : other;
     dfc = xpos ? other : big;
   } else {
@@ -523,7 +527,7 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
   const T c = c2 * rc, cf = cf2 * rcf, ca = abs_b(Bn) * rs;
   const T cs = (c * ca) * rcf;
   T af, as;
-  if (sq > T(1e-12) * s) {
+  if (gt_nn(sq, T(1e-12) * s)) {
     const T isq = rcp_t(sq);
     af = sqrt_t(dcs * isq);
     as = sqrt_t(dfc * isq);
@@ -532,7 +536,7 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
     as = INV_SQRT2;
   }
   T by, bz;
-  if (bp2 > T(1e-24) * rho * s) {
+  if (gt_nn(bp2, T(1e-24) * rho * s)) {
     const T ibp = rsqrt_t(bp2);
     by = Bt1 * ibp;
     bz = Bt2 * ibp;
@@ -540,7 +544,7 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
     by = INV_SQRT2;
     bz = INV_SQRT2;
   }
-  const T sg = Bn >= T(0) ? T(1) : T(-1);
+  const T sg = (sign_bit_b(Bn) && gt_nn(abs_b(Bn), T(0))) ? T(-1) : T(1);  // sign(0) = +1
   const T sqr = rho * rs, sc = sqr * c, sr2 = sqr * INV_SQRT2;
   const T i2c2 = scale_down_b<1>(rc * rc), i2sc = scale_down_b<1>(rs * rc), i2rc2 = i2c2 * irho;
   const T isr2 = rs * INV_SQRT2;

@@ -479,7 +479,7 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
       bl = br;
       const T y = abs_b(vn[k]) * tau_h;
       const T hy = scale_down_b<1>(y);
-      shy[k] = vn[k] >= T(0) ? neg_b(hy) : hy;
+      shy[k] = sign_bit_b(vn[k]) ? hy : neg_b(hy);  // v_n = -0 has y = 0
       w[k] = T(1) - TWO_THIRDS * y;
     }
   }
@@ -496,7 +496,7 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
     for (int k = 0; k < PENCIL; ++k) {
       if (k < nfp) {
         const Para<T> Pr = S.next(a[cell_at(f0 + k + 2)]);  // cell f0 + k
-        const bool left = vn[k] >= T(0);
+        const bool left = !sign_bit_b(vn[k]);  // v_n = -0: a zero flux either way
         const T E = left ? Pl.R : Pr.L;
         const T d = left ? Pl.d : Pr.d;
         const T q6 = left ? neg_b(Pl.q6) : Pr.q6;
