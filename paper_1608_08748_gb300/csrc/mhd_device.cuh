@@ -481,11 +481,12 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
   const T INV_SQRT2 = T(0.70710678118654752440);
   const T sl = wl[5], sr = wr[5];
   const T iden = rcp_t(sl + sr);
-  const T rho = (sl * wl[0] + sr * wr[0]) * iden;
-  const T p = (sl * wl[1] + sr * wr[1]) * iden;
-  const T gam = (sl * wl[2] + sr * wr[2]) * iden;
-  const T Bt1 = (sl * wr[3] + sr * wl[3]) * iden;  // crossed weights for B
-  const T Bt2 = (sl * wr[4] + sr * wl[4]) * iden;
+  const T al = sl * iden, ar = sr * iden;  // the normalised weights
+  const T rho = al * wl[0] + ar * wr[0];
+  const T p = al * wl[1] + ar * wr[1];
+  const T gam = al * wl[2] + ar * wr[2];
+  const T Bt1 = al * wr[3] + ar * wl[3];  // crossed weights for B
+  const T Bt2 = al * wr[4] + ar * wl[4];
 
   const T rs = rsqrt_t(rho);  // 1 / sqrt(rho)
   const T irho = rs * rs;
@@ -506,7 +507,8 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
   if constexpr (sizeof(T) == 8) {
     // one FP64 division for both signs of X, so a warp with both signs does not take two
     const bool xpos = !sign_bit_b(X);  // at X = 0 either form holds
-    T big = xpos ? T(0.5) * ((X + sq) - bp2r) : T(0.5) * ((bp2r - X) + sq);
+    // (|X| + sq - bp2r) / 2 for X >= 0, (|X| + sq + bp2r) / 2 for X < 0
+    T big = scale_down_b<1>((abs_b(X) + sq) - (xpos ? bp2r : neg_b(bp2r)));
     big = sign_bit_b(big) ? T(0) : big;
     const T other = !gt_nn(T(2.2250738585072014e-308), big) ? (c2 * bp2r) * rcp_t(big)
                     : gt_nn(big, T(0)) ? c2 * bp2r / big : T(0);
