@@ -2,11 +2,15 @@
 // arXiv:1608.08748 (Kulikov, Chernykh & Protasov).  Templated on the bulk type T (double for the
 // FP64 path, float for the FP32-bulk path); the CFL reduction and the chemistry are FP64 always.
 //
-// The formulas follow the paper section by section.  The PPM limiter gives the plain evaluation's
-// values bit for bit (its tests run on the integer pipes); the Riemann solver forms its speeds and
-// eigenvector rows with fewer divisions and square roots, and the FP64 build lets the compiler
-// contract a*b+c into one FMA, so the FP64 path agrees with a plain evaluation to a few ulp per
-// operation (about 1e-15 relative L1 after 50 steps of the 128^3 turbulence box).
+// The formulas follow the paper section by section.  On GB300 the FP64 pipe is the bound of the FP64
+// path, so the work that need not be FP64 arithmetic leaves it: the limiter's sign tests, minima,
+// orderings and power-of-two scalings run on the integer pipes (inline PTX on the halves of the
+// doubles), quotients and roots take one Newton-Raphson step from the hardware seeds, and the
+// Riemann solver forms its speeds and eigenvector rows with few divisions and square roots.  The
+// PPM keeps the plain evaluation's edge values bit for bit outside the Step 4 blend (q6 is formed as
+// 6 q_c - 3 (q_L + q_R)); the FP64 build contracts a*b+c into one FMA.  The FP64 path agrees with a
+// plain evaluation to a few ulp per operation (about 1e-15 relative L1 after 50 steps of the 128^3
+// turbulence box).
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
