@@ -39,6 +39,22 @@ int set_error(int code, const std::string& msg) { return fail(code, msg); }
 
 namespace {
 
+// the helpers of the FP64 path on an array of doubles (mhd_selftest_helpers)
+__global__ void k_selftest_helpers(const double* __restrict__ x, int n, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i], a = fabs(v);
+  double* o = out + 8 * (size_t)i;
+  o[0] = abs_b(v);
+  o[1] = neg_b(v);
+  o[2] = scale_down_b<1>(v);
+  o[3] = scale_down_b<2>(v);
+  o[4] = __longlong_as_double(okey(v));
+  o[5] = rcp_nr(v);
+  o[6] = rsqrt_nr(a);
+  o[7] = sqrt_nr(a);
+}
+
 size_t pool_size(const Geom& g, int precision, int chem) {
   (void)chem;
   size_t es = precision ? sizeof(float) : sizeof(double);
@@ -629,6 +645,15 @@ int mhd_get_potential(mhd_sim* S, double* out) {
   if ((rc = ensure_exec(S)) != MHD_OK) return rc;
   if ((rc = grav_solve(S)) != MHD_OK) return rc;
   return grav_copy(S, out);
+}
+
+int mhd_selftest_helpers(const double* x, int n, double* out) {
+  if (n < 0 || (n > 0 && (!x || !out))) return fail(MHD_EINVAL, "mhd_selftest_helpers: bad argument");
+  if (n == 0) return MHD_OK;
+  k_selftest_helpers<<<(n + 255) / 256, 256>>>(x, n, out);
+  CK(cudaGetLastError());
+  CK(cudaDeviceSynchronize());
+  return MHD_OK;
 }
 
 int mhd_launches_per_step(mhd_sim* S) {

@@ -87,6 +87,7 @@ def lib():
         L.mhd_launches_per_step.argtypes = [vp]
         L.mhd_get_potential.argtypes = [vp, vp]
         L.mhd_set_ions.argtypes = [vp, vp, i]
+        L.mhd_selftest_helpers.argtypes = [vp, i, vp]
         L.mhd_get_ions.argtypes = [vp, vp, i]
         L.mhd_batch_create.restype = vp
         L.mhd_batch_create.argtypes = [C.POINTER(vp), i]
@@ -263,6 +264,16 @@ class Sim:
 
 def bytes_needed(nx, ny, nz, precision=0, chem=1):
     return lib().mhd_bytes_needed(nx, ny, nz, precision, chem)
+
+
+def selftest_helpers(x):
+    """Device self-test of the FP64 arithmetic helpers (mhd_selftest_helpers): an (n, 8) float64
+    array of |x|, -x, x/2, x/4, the ordered key of x (its bits), 1/x, 1/sqrt|x|, sqrt|x|."""
+    import torch
+    xd = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64).ravel()).cuda()
+    out = torch.empty((xd.numel(), 8), dtype=torch.float64, device=xd.device)
+    _check(lib().mhd_selftest_helpers(xd.data_ptr(), xd.numel(), out.data_ptr()))
+    return out.cpu().numpy()
 
 
 def from_ic(ic, **options):
