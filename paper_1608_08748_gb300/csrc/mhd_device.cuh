@@ -195,6 +195,14 @@ __device__ __forceinline__ double min_nn(double a, double b) {
   return r;
 }
 __device__ __forceinline__ float min_nn(float a, float b) { return a < b ? a : b; }
+// the larger of a, b >= 0
+__device__ __forceinline__ double max_nn(double a, double b) {
+  double r;
+  asm("{\n\t.reg .s64 ia, ib;\n\t.reg .pred p;\n\tmov.b64 ia, %1;\n\tmov.b64 ib, %2;\n\t"
+      "setp.gt.s64 p, ia, ib;\n\tselp.b64 %0, %1, %2, p;\n\t}" : "=d"(r) : "d"(a), "d"(b));
+  return r;
+}
+__device__ __forceinline__ float max_nn(float a, float b) { return a > b ? a : b; }
 // a > b for b >= 0
 __device__ __forceinline__ bool gt_nn(double a, double b) {
   unsigned r;
@@ -635,7 +643,7 @@ __device__ __forceinline__ double cfl_denominator(double rho, double mx, double 
   const double B2 = Bx * Bx + By * By + Bz * Bz;
   const double sB = sqrt_nr(B2);
   const double v = sqrt_nr(mx * mx + my * my + mz * mz) * irho;
-  const double Bm = fmax(fabs(Bx), fmax(fabs(By), fabs(Bz)));
+  const double Bm = max_nn(abs_b(Bx), max_nn(abs_b(By), abs_b(Bz)));
   const double fs = sqrt_nr((gp + B2) + 2.0 * sgp * Bm);
   return v + ((sB + sgp + Bm) + fs) * irs;
 }
@@ -727,13 +735,15 @@ __device__ __forceinline__ ChemOut chem_cell(const Phys& ph, double rho, double 
   const double T = (num * num) * r, iT = (den * den) * r;
   // App. D rates
   const double t2 = T * 0.01;
-  const double a2 = T > 7390.0 ? -2.93e4 * iT : -((6750.0 * iT) * (6750.0 * iT));
-  const double a3 = T > 7291.0 ? -3.22e4 * iT : -(4060.0 * iT) - (7500.0 * iT) * (7500.0 * iT);
+  // the branch tests and clamps compare on the integer pipe (T >= 0; a2, a3 < 0)
+  const bool hot2 = gt_nn(T, 7390.0), hot3 = gt_nn(T, 7291.0);
+  const double a2 = hot2 ? -2.93e4 * iT : -((6750.0 * iT) * (6750.0 * iT));
+  const double a3 = hot3 ? -3.22e4 * iT : -(4060.0 * iT) - (7500.0 * iT) * (7500.0 * iT);
   const double s2 = sqrt_nr(t2);
   const double k1p = (3e-17 * s2) * rcp_nr(((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2));
   // exp of an argument below -746 is exactly 0 in double: skip the call in cold gas
-  const double k2 = a2 < -746.0 ? 0.0 : (T > 7390.0 ? 6.11e-14 : 2.67e-15) * exp(a2);
-  const double k3 = a3 < -746.0 ? 0.0 : (T > 7291.0 ? 5.22e-14 : 3.17e-15) * exp(a3);
+  const double k2 = gt_nn(neg_b(a2), 746.0) ? 0.0 : (hot2 ? 6.11e-14 : 2.67e-15) * exp(a2);
+  const double k3 = gt_nn(neg_b(a3), 746.0) ? 0.0 : (hot3 ? 5.22e-14 : 3.17e-15) * exp(a3);
   const double Ls = (ph.lshield > 0.0 ? ph.lshield : ph.dx) * ChemConst::PC;
   const double NH = nH * Ls, NH2 = nH2 * Ls;
   const double fdust = exp(-(ph.taud * (NH + NH2)));
@@ -747,8 +757,9 @@ __device__ __forceinline__ ChemOut chem_cell(const Phys& ph, double rho, double 
   const double D = (k2 * nH + k3 * nH2) + k4;
   const double ts = tau * T0;
   double nH2n = nH2 + (ts * (C - D * nH2)) * rcp_nr(1.0 + ts * D);
-  if (nH2n < 0.0) nH2n = 0.0;
-  if (nH2n > 0.5 * n) nH2n = 0.5 * n;
+  if (sign_bit_b(nH2n)) nH2n = 0.0;
+  const double half_n = scale_down_b<1>(n);
+  if (gt_nn(nH2n, half_n)) nH2n = half_n;
   ChemOut out;
   out.rh2 = 2.0 * nH2n;
   out.rhp = rhp;

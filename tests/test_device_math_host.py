@@ -37,6 +37,8 @@ inline float neg_b(float x) { return -x; }
 inline double with_sign_b(double m, double s) { return from_bits_(bits_(m) | (bits_(s) & SIGN_)); }
 inline float with_sign_b(float m, float s) { return std::copysign(m, s); }
 inline double min_nn(double a, double b) { return bits_(a) < bits_(b) ? a : b; }
+inline double max_nn(double a, double b) { return bits_(a) > bits_(b) ? a : b; }
+inline float max_nn(float a, float b) { return a > b ? a : b; }
 inline float min_nn(float a, float b) { return a < b ? a : b; }
 inline bool gt_nn(double a, double b) { return bits_(a) > bits_(b); }
 inline bool gt_nn(float a, float b) { return a > b; }
