@@ -409,9 +409,16 @@ __device__ __forceinline__ Para<T> ppm_lean(T qm2, T qm1, T qc, T qp1, T qp2) {
   // Step 1: edge values (dm0 - dmm) / 6 = (h0 - hm) / 3
   const T qL = scale_down_b<1>(qm1 + qc) - (h0 - hm) * THIRD;
   const T qR = scale_down_b<1>(qc + qp1) - (hp - h0) * THIRD;
-  // second differences D+ = q_{i+2} - 2 q_{i+1} + q_i, D- = q_i - 2 q_{i-1} + q_{i-2}
-  const T Dp = (qp2 - T(2) * qp1) + qc;
-  const T Dm = (qc - T(2) * qm1) + qm2;
+  // second differences D+ = q_{i+2} - 2 q_{i+1} + q_i, D- = q_i - 2 q_{i-1} + q_{i-2}: in FP64 as
+  // differences of the first differences (one instruction each, as the stream forms them)
+  T Dp, Dm;
+  if constexpr (sizeof(T) == 8) {
+    Dp = d3 - d2;
+    Dm = d1 - d0;
+  } else {
+    Dp = (qp2 - T(2) * qp1) + qc;
+    Dm = (qc - T(2) * qm1) + qm2;
+  }
   return ppm_limit(qL, qR, qc, h0, Dp, Dm, s0, qp1, qm1);
 }
 
@@ -436,8 +443,8 @@ struct PPMStream {
     s0 = qd - qb;
     h0 = half_slope(s0, d1, d2);
     eL = scale_down_b<1>(qb + qc) - (h0 - hm) * THIRD;
-    Cm = (qc - T(2) * qb) + qa;
-    C0 = (qd - T(2) * qc) + qb;
+    Cm = d1 - d0;
+    C0 = d2 - d1;
     qm = qb;
     q0 = qc;
     qp = qd;
@@ -448,7 +455,7 @@ struct PPMStream {
     const T d2 = qn - qp;
     const T s1 = qn - q0;
     const T h1 = half_slope(s1, dp, d2);
-    const T C1 = (qn - T(2) * qp) + q0;
+    const T C1 = d2 - dp;
     const T eR = scale_down_b<1>(q0 + qp) - (h1 - h0) * THIRD;
     Para<T> P = ppm_limit(eL, eR, q0, h0, C1, Cm, s0, qp, qm);
     qm = q0;
