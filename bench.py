@@ -42,7 +42,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FLOPS_PER_EULER_FACE = 577
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one x-direction Eulerian face launch
 # at 128^3, from one ncu capture of this kernel (set to None whenever the kernel changes)
-EULER_FACE_TRAFFIC_BYTES = None
+EULER_FACE_TRAFFIC_BYTES = 358.3e6
 
 
 def reduce_max(x, dist=None, device="cpu"):
