@@ -45,3 +45,36 @@ def test_bytes_needed_is_host_only(libmhd):
     small, big = f(16, 16, 16, 0, 1), f(32, 32, 32, 0, 1)
     assert 7.0 < big / small < 8.5
     assert f(64, 64, 64, 1, 1) < f(64, 64, 64, 0, 1)
+
+
+def test_argument_errors_are_reported_without_a_device(libmhd):
+    """Bad arguments are rejected on the host, before any CUDA call: the calls return MHD_EINVAL (or
+    NULL) and mhd_last_error names the call."""
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    libmhd.mhd_last_error.restype = ctypes.c_char_p
+    err = lambda: libmhd.mhd_last_error().decode()
+    EINVAL = -1
+
+    libmhd.mhd_create.restype = vp
+    libmhd.mhd_create.argtypes = [i, i, i, d, d]
+    for args in [(0, 4, 4, 1.4, 1.0), (4, 4, 4, 1.0, 1.0), (4, 4, 4, 1.4, 0.0), (2048, 2048, 1024, 1.4, 1.0)]:
+        assert libmhd.mhd_create(*args) is None
+        assert "mhd_create" in err()
+
+    libmhd.mhd_set_option.argtypes = [vp, i, d]
+    assert libmhd.mhd_set_option(None, 4, 1.0) == EINVAL and "mhd_set_option" in err()
+    libmhd.mhd_step.argtypes = [vp, d, vp]
+    assert libmhd.mhd_step(None, 0.4, None) == EINVAL and "mhd_step" in err()
+    libmhd.mhd_set_ions.argtypes = [vp, vp, i]
+    assert libmhd.mhd_set_ions(None, None, 0) == EINVAL and "mhd_set_ions" in err()
+    libmhd.mhd_get_ions.argtypes = [vp, vp, i]
+    assert libmhd.mhd_get_ions(None, None, 0) == EINVAL and "mhd_get_ions" in err()
+    libmhd.mhd_batch_create.restype = vp
+    libmhd.mhd_batch_create.argtypes = [vp, i]
+    assert libmhd.mhd_batch_create(None, 0) is None and "mhd_batch_create" in err()
+    libmhd.mhd_server_set_policy.argtypes = [vp, i]
+    assert libmhd.mhd_server_set_policy(None, 0) == EINVAL and "mhd_server_set_policy" in err()
+    libmhd.mhd_selftest_helpers.argtypes = [vp, i, vp]
+    assert libmhd.mhd_selftest_helpers(None, 5, None) == EINVAL and "mhd_selftest_helpers" in err()
+    assert libmhd.mhd_selftest_helpers(None, -1, None) == EINVAL
+    assert libmhd.mhd_selftest_helpers(None, 0, None) == 0  # nothing to do, no launch
