@@ -275,9 +275,25 @@ int main() {
       worsthi = std::max(worsthi, eh);
       if (eh > 1e-12) ++badhi;
     }
+    // 5d. the instances with the ion code, on a box without ions (rho_H+ = 0), give the bits of the
+    // instances without it (a batch that mixes such boxes runs the former for all of them)
+    ph.ions = 0;
+    long badsame = 0;
+    for (long it = 0; it < n / 10; ++it) {
+      const double rho = std::exp(12 * U01(g) - 4);
+      const double rh2 = rho * U01(g) * (it % 3 ? 1.0 : 1e-6);
+      const double eint = rho * std::exp(16 * U01(g) - 8);
+      const double tau = std::exp(10 * U01(g) - 12);
+      const ChemOut a1 = chem_cell<true>(ph, rho, eint, rh2, 0.0, tau);
+      const ChemOut a0 = chem_cell<false>(ph, rho, eint, rh2, 0.0, tau);
+      const double h1 = heatcool_delta<true>(ph, rho, eint, rh2, 0.0, tau);
+      const double h0 = heatcool_delta<false>(ph, rho, eint, rh2, 0.0, tau);
+      if (std::memcmp(&a1.rh2, &a0.rh2, 8) != 0 || std::memcmp(&h1, &h0, 8) != 0) ++badsame;
+    }
     osim_destroy(s);
     report("chemistry_ions", n, worsti, badi);
     report("heatcool_ions", n, worsthi, badhi);
+    report("ion_instances_without_ions_same_bits", n / 10, 0.0, badsame);
   }
   // 5d. the Newton-Raphson reciprocal, reciprocal square root and square root against the correctly
   // rounded library values: within 2 ulp over the normal range

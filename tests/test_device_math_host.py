@@ -64,7 +64,7 @@ inline double rsqrt_seed(double x) { return seed_(1.0 / std::sqrt(ftz_(x))); }
 '''
 
 BOUNDS = {"ppm_lean_close": 0, "ppm_stream_bits": 0, "ppm_fp32": 0, "riemann_fp64": 0, "riemann_fp32": 0,
-          "chemistry": 0, "heatcool": 0, "chemistry_ions": 0, "heatcool_ions": 0, "cfl": 0,
+          "chemistry": 0, "heatcool": 0, "chemistry_ions": 0, "heatcool_ions": 0, "ion_instances_without_ions_same_bits": 0, "cfl": 0,
           "newton_raphson_ulp": 0}
 
 

@@ -208,3 +208,23 @@ def test_lagrangian_stage_carries_an_exact_ion_fraction(oracle_mod):
     rho = s.get_state()["rho"]
     assert np.array_equal(s.get_ions(), 0.25 * rho)
     assert np.array_equal(s.get_state()["rho_h2"], 0.125 * rho)
+
+
+def test_full_steps_with_ions_conserve_mass_and_keep_species_physical(oracle_mod):
+    # periodic box, ions and heating/cooling on: the step conserves sum rho (the chemistry moves
+    # nuclei between species only), every species stays within [0, n], and rho_H2 + rho_H+ <= rho
+    ic = dict(I.turbulence(10, seed=5, mach=2.0, T_K=8000.0))
+    ic["rho_h2"] = 0.05 * ic["rho"]
+    s = oracle_mod.Sim(10, 10, 10, 5.0 / 3.0, ic["dx"], chem=1, ions=1, heatcool=1)
+    s.set_state(ic["rho"], ic["mom"], ic["E"], ic["B"], ic["rho_h2"])
+    s.set_ions(0.01 * ic["rho"])
+    m0 = s.diag()["rho"]
+    hp0 = s.get_ions().sum()
+    for _ in range(3):
+        s.step(0.4)
+    st = s.get_state()
+    assert s.diag()["rho"] == pytest.approx(m0, rel=1e-13, abs=0)
+    hp = s.get_ions()
+    assert (hp >= 0).all() and (st["rho_h2"] >= 0).all()
+    assert (st["rho_h2"] + hp <= st["rho"] * (1 + 1e-12)).all()
+    assert hp.sum() != pytest.approx(hp0, rel=1e-6)  # the network acted
