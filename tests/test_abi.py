@@ -78,3 +78,12 @@ def test_argument_errors_are_reported_without_a_device(libmhd):
     assert libmhd.mhd_selftest_helpers(None, 5, None) == EINVAL and "mhd_selftest_helpers" in err()
     assert libmhd.mhd_selftest_helpers(None, -1, None) == EINVAL
     assert libmhd.mhd_selftest_helpers(None, 0, None) == 0  # nothing to do, no launch
+
+
+def test_binding_option_keys_match_the_header():
+    src = open(os.path.join(ROOT, "include", "mhd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    enum = re.search(r"enum mhd_option\s*\{(.*?)\};", src, flags=re.S).group(1)
+    header = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"MHD_OPT_([A-Z0-9_]+)\s*=\s*(\d+)", enum)}
+    from paper_1608_08748_gb300 import mhd
+    assert mhd.OPT == header
