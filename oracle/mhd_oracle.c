@@ -168,6 +168,29 @@ static double slope_m(double qm, double q0, double qp) {
   return 0.0;
 }
 
+/* Step 4 discontinuity detector for cell i from q[0..4] = q_{i-2}..q_{i+2}: the criterion eta
+   with D the undivided second difference (A2), zeroed by the two conditions (A3), and the weight
+   hbar = max(min(20 (eta - 0.05), 1), 0) of the flattened edge values.  eta_out may be NULL. */
+static double step4_weight(const double q[5], double* eta_out) {
+  double Dp = q[4] - 2.0 * q[3] + q[2];
+  double Dm = q[2] - 2.0 * q[1] + q[0];
+  double dq2 = q[3] - q[1];
+  double ap = fabs(q[3]), am = fabs(q[1]);
+  double mn = ap < am ? ap : am;
+  double sum = ap + am;
+  mn = mn < sum ? mn : sum;
+  double eta;
+  if (fabs(dq2) - 0.01 * mn <= 0.0 || Dp * Dm > 0.0)
+    eta = 0.0;
+  else
+    eta = -(Dp - Dm) / (3.0 * dq2);
+  double hb = 20.0 * (eta - 0.05);
+  hb = hb < 1.0 ? hb : 1.0;
+  hb = hb > 0.0 ? hb : 0.0;
+  if (eta_out) *eta_out = eta;
+  return hb;
+}
+
 /* Steps 1-5 for cell i from q[0..4] = q_{i-2}..q_{i+2} */
 static para ppm_cell(const double q[5], int step4_as_written) {
   const double qc = q[2];
@@ -190,23 +213,9 @@ static para ppm_cell(const double q[5], int step4_as_written) {
   }
   /* Step 3 recomputes Delta q and q6; Step 4 only needs q^L, q^R, so they are recomputed in
      Step 5 below. */
-  /* Step 4: discontinuity detector eta and weight hbar (A2, A3, A4) */
+  /* Step 4: flattened edge values q -+ delta_m q / 4, weighted by hbar (A2, A3, A4) */
   double qLp = qc - 0.25 * dm0, qRp = qc + 0.25 * dm0;
-  double Dp = q[4] - 2.0 * q[3] + q[2];
-  double Dm = q[2] - 2.0 * q[1] + q[0];
-  double dq2 = q[3] - q[1];
-  double ap = fabs(q[3]), am = fabs(q[1]);
-  double mn = ap < am ? ap : am;
-  double sum = ap + am;
-  mn = mn < sum ? mn : sum;
-  double eta;
-  if (fabs(dq2) - 0.01 * mn <= 0.0 || Dp * Dm > 0.0)
-    eta = 0.0;
-  else
-    eta = -(Dp - Dm) / (3.0 * dq2);
-  double hb = 20.0 * (eta - 0.05);
-  hb = hb < 1.0 ? hb : 1.0;
-  hb = hb > 0.0 ? hb : 0.0;
+  double hb = step4_weight(q, NULL);
   if (step4_as_written) {
     qL = (1.0 - hb) * qLp + hb * qL;
     qR = (1.0 - hb) * qRp + hb * qR;
@@ -1350,6 +1359,13 @@ void o_ppm(const double q[5], int step4_as_written, double out[4]) {
   out[1] = P.R;
   out[2] = P.d;
   out[3] = P.q6;
+}
+
+/* Step 4 detector of one cell: q[0..4] = q_{i-2}..q_{i+2} -> out = (eta, hbar) */
+void o_step4(const double q[5], double out[2]) {
+  double eta = 0.0;
+  out[1] = step4_weight(q, &eta);
+  out[0] = eta;
 }
 
 /* domain-of-dependence average of a parabola P = (q^L, q^R, Delta q, q^(6)) over the fraction y

@@ -71,6 +71,7 @@ def lib():
         L.osim_nsteps.argtypes = [vp]
         L.osim_diag.argtypes = [vp, _dp]
         L.o_ppm.argtypes = [_dp, i, _dp]
+        L.o_step4.argtypes = [_dp, _dp]
         L.o_avg.restype = d
         L.o_avg.argtypes = [_dp, d, i]
         L.o_eigen.argtypes = [_dp, _dp, _dp, _dp, _dp]
@@ -238,6 +239,13 @@ def ppm(q5, step4_as_written=False):
     out = np.zeros(4)
     lib().o_ppm(_f64(q5), int(step4_as_written), out)
     return out  # qL, qR, dq, q6
+
+
+def step4(q5):
+    """Step 4 detector of one cell from q_{i-2}..q_{i+2}: (eta, hbar)."""
+    out = np.zeros(2)
+    lib().o_step4(_f64(q5), out)
+    return out
 
 
 def avg(P, y, right_end):

@@ -20,10 +20,27 @@ import test_oracle_ions as T_io  # noqa: E402
 import test_oracle_physics as T_ph  # noqa: E402
 import test_oracle_ppm as T_ppm  # noqa: E402
 import test_oracle_riemann as T_rs  # noqa: E402
+import test_oracle_step4 as T_s4  # noqa: E402
 
 # (name, text in mhd_oracle.c, replacement)
 MUTATIONS = [
     ("ppm_delta_sign", "P.d = qR - qL;", "P.d = qL - qR;"),
+    ("step4_eta_normalisation_two", "eta = -(Dp - Dm) / (3.0 * dq2);", "eta = -(Dp - Dm) / (2.0 * dq2);"),
+    ("step4_eta_normalisation_six", "eta = -(Dp - Dm) / (3.0 * dq2);", "eta = -(Dp - Dm) / (6.0 * dq2);"),
+    ("step4_eta_sign", "eta = -(Dp - Dm) / (3.0 * dq2);", "eta = (Dp - Dm) / (3.0 * dq2);"),
+    ("step4_small_jump_gate_tenth", "if (fabs(dq2) - 0.01 * mn <= 0.0 || Dp * Dm > 0.0)",
+     "if (fabs(dq2) - 0.1 * mn <= 0.0 || Dp * Dm > 0.0)"),
+    ("step4_small_jump_gate_dropped", "if (fabs(dq2) - 0.01 * mn <= 0.0 || Dp * Dm > 0.0)", "if (Dp * Dm > 0.0)"),
+    ("step4_inflection_gate_reversed", "if (fabs(dq2) - 0.01 * mn <= 0.0 || Dp * Dm > 0.0)",
+     "if (fabs(dq2) - 0.01 * mn <= 0.0 || Dp * Dm < 0.0)"),
+    ("step4_inflection_gate_dropped", "if (fabs(dq2) - 0.01 * mn <= 0.0 || Dp * Dm > 0.0)",
+     "if (fabs(dq2) - 0.01 * mn <= 0.0)"),
+    ("step4_ramp_slope", "double hb = 20.0 * (eta - 0.05);", "double hb = 10.0 * (eta - 0.05);"),
+    ("step4_ramp_threshold", "double hb = 20.0 * (eta - 0.05);", "double hb = 20.0 * (eta - 0.1);"),
+    ("step4_flattened_quarter", "double qLp = qc - 0.25 * dm0, qRp = qc + 0.25 * dm0;",
+     "double qLp = qc - 0.5 * dm0, qRp = qc + 0.5 * dm0;"),
+    ("step4_weights_as_printed", "    qL = hb * qLp + (1.0 - hb) * qL;\n    qR = hb * qRp + (1.0 - hb) * qR;",
+     "    qL = (1.0 - hb) * qLp + hb * qL;\n    qR = (1.0 - hb) * qRp + hb * qR;"),
     ("slope_factor_dropped", "b = 2.0 * fabs(dp)", "b = fabs(dp)"),
     ("edge_value_sixth_sign", "qR = 0.5 * (q[2] + q[3]) - (dmp - dm0) * SIXTH;",
      "qR = 0.5 * (q[2] + q[3]) + (dmp - dm0) * SIXTH;"),
@@ -50,6 +67,9 @@ MUTATIONS = [
     ("chem_photodissociation_dropped", "r.D = (r.k2 * nH + r.k3 * nH2) + r.k4;", "r.D = (r.k2 * nH + r.k3 * nH2);"),
     ("k1_temperature_power", "double s2 = sqrt(t2);", "double s2 = t2;"),
     ("regularisation_half_dropped", "double kin = 0.5 * m2 / r;", "double kin = m2 / r;"),
+    ("regularisation_max_reversed", "if (s->regul_mode != 0 || e > s->eint[c]) s->eint[c] = e;",
+     "if (s->regul_mode != 0 || e < s->eint[c]) s->eint[c] = e;"),
+    ("regularisation_max_dropped", "if (s->regul_mode != 0 || e > s->eint[c]) s->eint[c] = e;", "s->eint[c] = e;"),
     ("gamma_eff_weights_swapped", "return (5.0 * n1 + 7.0 * nH2) / (3.0 * n1 + 5.0 * nH2);",
      "return (7.0 * n1 + 5.0 * nH2) / (5.0 * n1 + 3.0 * nH2);"),
     ("gamma_eff_electrons_dropped", "double n1 = (rho - rh2 - rhp) + 2.0 * rhp", "double n1 = (rho - rh2 - rhp) + 1.0 * rhp"),
@@ -131,6 +151,13 @@ def pins(O):
     yield "ions_limits", lambda: T_io.test_ion_update_limits(io())
     yield "ions_physical", lambda: T_io.test_species_stay_physical_and_nuclei_are_conserved(O, io())
     yield "ions_lagrangian", lambda: T_io.test_lagrangian_stage_carries_an_exact_ion_fraction(O)
+    yield "step4_cubic", lambda: [T_s4.test_eta_and_weight_closed_form_on_a_cubic(O, a) for a in T_s4.A_VALUES]
+    yield "step4_parabola", lambda: [T_s4.test_parabola_edges_follow_the_weight(O, a) for a in T_s4.A_VALUES]
+    yield "step4_inflection", lambda: [T_s4.test_no_inflection_zeroes_eta(O, b, act) for b, act in
+                                       [(2.9, True), (3.1, False), (-3.1, False)]]
+    yield "step4_small_jumps", lambda: [T_s4.test_small_jumps_zero_eta(O, 1.0, f, act) for f, act in
+                                        [(0.98, True), (1.02, False)]]
+    yield "step4_sine", lambda: T_s4.test_sampled_sine_closed_form(O)
     st = T_rs.random_states(5, 7)
     yield "eigen", lambda: [T_rs.test_eigen_identities(O, s, 1e-11) for s in st]
     yield "linear_riemann", lambda: [T_rs.test_flat_riemann_matches_numpy_linear_solution(O, k) for k in range(3)]
@@ -151,6 +178,7 @@ def pins(O):
     yield "ot_symmetry", lambda: T_ph.test_orszag_tang_point_symmetry(O)
     yield "oblique_waves", lambda: [T_ph.test_oblique_linear_wave_converges(O, k) for k in ["fast", "alfven"]]
     yield "regularisation", lambda: T_ph.test_regularisation_restores_the_energy_closure(O)
+    yield "regularisation_entropy", lambda: T_ph.test_regularisation_never_lowers_the_entropy(O)
     yield "faces_from_cells", lambda: T_ph.test_faces_from_linear_cell_field_are_midpoint_values(O)
 
 

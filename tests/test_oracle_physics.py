@@ -351,3 +351,42 @@ def test_faces_from_linear_cell_field_are_midpoint_values(oracle_mod):
     assert np.allclose(bf[0][:, :, 1:], (1.0 + 0.3 * xf)[None, None, :], rtol=0, atol=1e-14)
     assert np.allclose(bf[1][:, 1:, :], (2.0 - 0.7 * xf)[None, :, None], rtol=0, atol=1e-14)
     assert np.allclose(bf[2][1:, :, :], (0.5 + 1.1 * xf)[:, None, None], rtol=0, atol=1e-14)
+
+
+def _regularise_once(oracle_mod, factor, mode):
+    """Stage 4 alone on a chemistry-free turbulence box whose stored rho eps is factor x (rho E -
+    rho v^2/2 - B^2/2) per cell; returns (rho, e = the closure value, rho eps before, after)."""
+    ic = I.turbulence(8, mach=2.0, seed=19, shape=(6, 7, 8))
+    s = oracle_mod.run(ic, chem=0, regul_mode=mode)
+    full = s.get_full()
+    st = s.get_state()
+    kin = 0.5 * (st["mom"] ** 2).sum(0) / st["rho"]
+    mag = 0.5 * (st["B"] ** 2).sum(0)
+    e = st["E"] - kin - mag
+    eint = factor * e
+    s.set_full(eint, full["bface"])
+    s.stage(4, 1.0)
+    return st["rho"], e, eint, s.get_full()["eint"], s
+
+
+def test_regularisation_never_lowers_the_entropy(oracle_mod):
+    """Sec. 2.9: the correction of the thermal energy "guarantees non-decreasing of entropy".  At
+    fixed rho (the stage changes neither rho nor gamma) the specific entropy ln(p / rho^gamma),
+    p = (gamma - 1) rho eps, rises or falls with rho eps, so in the entropy branch (thermal fraction
+    >= 1e-3 everywhere here) rho eps may be raised to the closure value rho E - rho v^2/2 - B^2/2
+    but never lowered to it: cells whose rho eps lies above the closure keep it, cells below take
+    the closure value.  The unconditional overwrite (mode 1) lowers the entropy of the first kind
+    of cell, which is why it is not the default."""
+    gam = 5.0 / 3.0
+    rng = np.random.default_rng(3)
+    factor = np.where(rng.random((6, 7, 8)) < 0.5, 0.6, 1.4)
+    rho, e, before, after, s = _regularise_once(oracle_mod, factor, 0)
+    entropy = lambda eint: np.log((gam - 1.0) * eint / rho ** gam)
+    assert (entropy(after) >= entropy(before)).all()
+    up = factor < 1.0
+    assert np.allclose(after[up], e[up], rtol=1e-13, atol=0)
+    assert np.array_equal(after[~up], before[~up])
+    assert s.diag()["vel_branch"] == 0
+    rho, e, before, after1, _ = _regularise_once(oracle_mod, factor, 1)
+    assert np.allclose(after1, e, rtol=1e-13, atol=0)  # overwrite everywhere
+    assert (entropy(after1)[~up] < entropy(before)[~up]).all()
