@@ -431,10 +431,12 @@ int grav_solve(mhd_sim* S);
 int grav_copy(mhd_sim* S, double* out);
 void grav_free(mhd_sim* S);
 
-// per-sim (non-batched) helpers: state transfer and diagnostics
+// per-sim (non-batched) helpers: state transfer and diagnostics.  They take the sim's geometry
+// (S->g), not the box descriptor's copy: that copy is refreshed only when the executor is rebuilt,
+// so after a boundary option changes it still holds the old boundaries until the next step.
 template <typename T, typename In>
 cudaError_t load_state(mhd_sim* S, Box<T>& B, const In* const* p) {
-  const Geom& g = B.g;
+  const Geom& g = S->g;
   k_load_cells<T, In><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s, p[0], p[1], p[2], p[3], p[4], p[8]);
   k_faces_from_cells<T, In><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s, p[5], p[6], p[7]);
   k_derive_eint<T><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s);
@@ -443,7 +445,7 @@ cudaError_t load_state(mhd_sim* S, Box<T>& B, const In* const* p) {
 
 template <typename T, typename Out>
 cudaError_t store_state(mhd_sim* S, Box<T>& B, Out* const* p) {
-  const Geom& g = B.g;
+  const Geom& g = S->g;
   k_store_state<T, Out><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s, p[0], p[1], p[2], p[3], p[4], p[5],
                                                                 p[6], p[7], p[8]);
   return cudaGetLastError();
@@ -451,7 +453,7 @@ cudaError_t store_state(mhd_sim* S, Box<T>& B, Out* const* p) {
 
 template <typename T>
 cudaError_t set_faces(mhd_sim* S, Box<T>& B, const double* const* b) {
-  const Geom& g = B.g;
+  const Geom& g = S->g;
   k_faces_copy<T><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s, b[0], b[1], b[2]);
   k_derive_eint<T><<<nblk(g.N, 256), 256, 0, S->stream>>>(g, B.s);
   return cudaGetLastError();
@@ -459,31 +461,31 @@ cudaError_t set_faces(mhd_sim* S, Box<T>& B, const double* const* b) {
 
 template <typename T>
 cudaError_t store_full(mhd_sim* S, Box<T>& B, double* const* d) {
-  k_store_full<T><<<nblk(B.g.N, 256), 256, 0, S->stream>>>(B.g, B.s, d[0], d[1], d[2], d[3]);
+  k_store_full<T><<<nblk(S->g.N, 256), 256, 0, S->stream>>>(S->g, B.s, d[0], d[1], d[2], d[3]);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t load_full(mhd_sim* S, Box<T>& B, const double* const* d) {
-  k_load_full<T><<<nblk(B.g.N, 256), 256, 0, S->stream>>>(B.g, B.s, d[0], d[1], d[2], d[3]);
+  k_load_full<T><<<nblk(S->g.N, 256), 256, 0, S->stream>>>(S->g, B.s, d[0], d[1], d[2], d[3]);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t store_ions(mhd_sim* S, Box<T>& B, double* d) {
-  k_store_ions<T><<<nblk(B.g.N, 256), 256, 0, S->stream>>>(B.g, B.s, d);
+  k_store_ions<T><<<nblk(S->g.N, 256), 256, 0, S->stream>>>(S->g, B.s, d);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t load_ions(mhd_sim* S, Box<T>& B, const double* d) {
-  k_load_ions<T><<<nblk(B.g.N, 256), 256, 0, S->stream>>>(B.g, B.s, d);
+  k_load_ions<T><<<nblk(S->g.N, 256), 256, 0, S->stream>>>(S->g, B.s, d);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t diag_partial(mhd_sim* S, Box<T>& B) {
-  k_diag_partial<T><<<S->diag_blocks, DIAG_THREADS, 0, S->stream>>>(B.g, B.s, S->diag_part);
+  k_diag_partial<T><<<S->diag_blocks, DIAG_THREADS, 0, S->stream>>>(S->g, B.s, S->diag_part);
   return cudaGetLastError();
 }
 

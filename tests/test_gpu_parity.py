@@ -136,3 +136,27 @@ def test_turbulence_128_config2_full(M, oracle_mod):
     dg = g.diagnostics()
     assert dg["steps"] == 50 and dg["t"] == pytest.approx(o.t, rel=1e-13, abs=0)
     print("config 2 rel L1:", {k: f"{v:.1e}" for k, v in errs.items()})
+
+
+@pytest.mark.parametrize("mode,shape,mach,tube_t", [(1, (16, 12, 20), 5.0, 0.02), (2, (12, 14, 10), 2.0, None)])
+def test_regularisation_modes(M, oracle_mod, mode, shape, mach, tube_t):
+    """The other two readings of Sec. 2.9 (option regul_mode): 1 overwrites rho eps wherever the
+    thermal fraction is >= 1e-3, 2 takes the sentence's branch order (speed correction there).
+    Each against the oracle in the same mode: 8 turbulence steps with chemistry (and for mode 1 a
+    Brio-Wu tube), with the count of velocity-branch cells equal on both sides.  Mode 2 rescales
+    every velocity to the energy left over after rho eps and B^2/2; where the gas is at rest that
+    velocity is rounding noise and its new direction is the noise's, so the tube, which starts at
+    rest, is not a parity case for it."""
+    ic = I.turbulence(8, mach=mach, seed=7, shape=shape)
+    ic["options"] = dict(ic["options"], regul_mode=mode)
+    g, o = run_pair(M, oracle_mod, ic, steps=8)
+    compare(g.get_state(), o.get_state())
+    assert g.diagnostics()["vel_branch"] == o.diag()["vel_branch"]
+    if mode == 2:
+        assert o.diag()["vel_branch"] > 0  # the branch the test is about was taken
+    if tube_t is not None:
+        tube = I.brio_wu(128, 4, 4)
+        tube["options"] = dict(tube["options"], regul_mode=mode)
+        g, o = run_pair(M, oracle_mod, tube, t_end=tube_t)
+        compare(g.get_state(), o.get_state())
+        assert g.diagnostics()["vel_branch"] == o.diag()["vel_branch"]
