@@ -31,8 +31,17 @@ CFL = 0.4
 N_GRID = 128
 WORKLOAD = "mhd_turbulence_h2chem_128^3_fp64"
 METRIC = "Mcell-updates/s"
-# FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (max SM clock)
+# FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (max SM clock); the
+# FMA-chain peak measured in the run (mhd_probe_fma_peak) is reported beside it
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 peak: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# algorithmic HBM bytes of one cell-update of the unfused substage model (129 field accesses with
+# chemistry: each of the six RK substages reads its inputs and the RK register and writes its
+# outputs once; the post pass reads the face fields), FP64 and FP32 bulk
+BYTES_PER_CELL_UPDATE = {8: 1032, 4: 516}
+# the copy bandwidth used when the measured peaks are not available
+HBM_FALLBACK_GBS = 6800.0
 # algorithmic FP64 flops of one Eulerian face, counted from the kernel source with an FMA as two
 # flops and a division, square root or reciprocal square root as one (compares and selects not
 # counted): the parabolas of the six primitives of one new cell, streamed along the pencil (6 x 32:
@@ -43,6 +52,34 @@ FLOPS_PER_EULER_FACE = 577
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one x-direction Eulerian face launch
 # at 128^3, from one ncu capture of this kernel (set to None whenever the kernel changes)
 EULER_FACE_TRAFFIC_BYTES = 358.3e6
+# FP32 bulk: FP32 flops of one Eulerian face (fadd + fmul + 2 ffma executed, from one ncu capture
+# of kb_euler_pencil<float>, divided by the faces of the launch) and the DRAM bytes of one 256^3
+# launch; None until captured for the current kernel
+FP32_FLOPS_PER_EULER_FACE = None
+EULER_FACE_TRAFFIC_BYTES_FP32 = None
+
+
+def hbm_peak():
+    """(GB/s, source) of the HBM roofline: the measured copy bandwidth of the GB300s when
+    the measured-peaks file is present, else the fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        if v > 0:
+            return v, "measured (STREAM-style copy)"
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def hbm_roofline(bytes_per_update, cells, ms_per_step):
+    """Whole-step HBM roofline: algorithmic bytes of one step over its time, against the peak."""
+    peak, src = hbm_peak()
+    achieved = bytes_per_update * cells / (ms_per_step * 1e-3) / 1e9
+    return {"bound": "hbm", "scope": "whole step (algorithmic bytes / step time)",
+            "bytes_per_cell_update": bytes_per_update, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_source": src}
 
 
 def reduce_max(x, dist=None, device="cpu"):
@@ -109,19 +146,21 @@ def summarize_clocks(lines, gpu_index):
             "samples": len(sm)}
 
 
-def oracle_rate(n, steps, warm=1):
-    """Oracle Mcell-updates/s on an n^3 box of the same turbulence set-up; returns (rate, cores)."""
+def oracle_rate(n, steps, warm=1, threads=None):
+    """Oracle Mcell-updates/s on an n^3 box of the same turbulence set-up (all host cores, or
+    `threads` OpenMP threads); returns (rate, cores, seconds)."""
     from oracle import oracle as O
     from paper_1608_08748_gb300 import inputs as I
     ic = I.turbulence(n, mach=5.0, beta=1.0, seed=1)
-    s = O.run(ic)
+    opts = {} if threads is None else {"threads": threads}
+    s = O.run(ic, **opts)
     for _ in range(warm):
         s.step(CFL)
     t0 = time.perf_counter()
     for _ in range(steps):
         s.step(CFL)
     dt = time.perf_counter() - t0
-    cores = os.cpu_count()
+    cores = os.cpu_count() if threads is None else threads
     return n ** 3 * steps / dt / 1e6, cores, dt
 
 
@@ -188,9 +227,11 @@ def timed_steps(torch, sim, steps, warm):
     return e0.elapsed_time(e1)
 
 
-def fp32_leg(M, I, torch, n=256, steps=10, warm=3, err_steps=5):
-    """Config 3: the same turbulence set-up at n^3 with the FP32-bulk path; per-field error against
-    the FP64 GPU path (which matches the FP64 oracle to 1e-15 at 128^3) after err_steps steps."""
+def fp32_leg(M, I, torch, n=256, steps=10, warm=3, err_steps=100):
+    """Config 3: the same turbulence set-up at n^3 with the FP32-bulk path.  Per-field error
+    against the FP64 GPU path from the same initial state after err_steps steps (the FP64 path
+    matches the FP64 oracle element by element; the oracle itself is checked against the FP32 path
+    at 64^3 over the same 100 steps in the GPU tests)."""
     ic = I.turbulence(n, mach=5.0, beta=1.0, seed=1)
     s32 = M.from_ic(ic, precision=1)
     ms = timed_steps(torch, s32, steps, warm)
@@ -204,11 +245,30 @@ def fp32_leg(M, I, torch, n=256, steps=10, warm=3, err_steps=5):
     a.sync()
     b.sync()
     err = rel_l1_fields(a.get_state(), b.get_state())
+    t32, t64 = a.diagnostics()["t"], b.diagnostics()["t"]
     del a, b
+    ms_step = ms / steps
+    kernels = {k: v["ms_total"] / 2 for k, v in prof.items()}
+    dominant = max((k for k in kernels if k != "small"), key=lambda k: kernels[k])
+    roof = None
+    if FP32_FLOPS_PER_EULER_FACE:
+        faces = (n + 1) * n * n
+        launch_s = prof["euler_face"]["ms_total"] / prof["euler_face"]["launches"] * 1e-3
+        measured = M.probe_fma_peak(fp64=False)
+        achieved = FP32_FLOPS_PER_EULER_FACE * faces / launch_s / 1e12
+        roof = {"bound": "alu", "kernel": "kb_euler_pencil (FP32)", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": EULER_FACE_TRAFFIC_BYTES_FP32, "flops_per_face": FP32_FLOPS_PER_EULER_FACE,
+                "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 flop x 2.07 GHz",
+                "peak_measured": measured, "frac_of_measured": achieved / measured,
+                "share_of_step": kernels["euler_face"] / sum(kernels.values())}
     return {"workload": f"mhd_turbulence_h2chem_{n}^3_fp32bulk", "value": n ** 3 * steps / (ms * 1e-3) / 1e6,
-            "unit": METRIC, "ms_per_step": ms / steps, "steps": steps, "warmup": warm,
-            "rel_l1_vs_fp64": err, "error_steps": err_steps,
-            "kernels": {k: v["ms_total"] / 2 for k, v in prof.items()}}
+            "unit": METRIC, "ms_per_step": ms_step, "steps": steps, "warmup": warm,
+            "roofline_hbm": hbm_roofline(BYTES_PER_CELL_UPDATE[4], n ** 3, ms_step),
+            "roofline": roof, "dominant_kernel": dominant,
+            "rel_l1_vs_fp64_100steps": err, "error_steps": err_steps,
+            "t_after_error_steps": {"fp32": t32, "fp64": t64},
+            "kernels": kernels}
 
 
 def heatcool_leg(M, I, torch, n=128, steps=10, warm=3):
@@ -297,11 +357,13 @@ def batched_leg(M, I, torch, steps=20, warm=3):
             "kernels": {k: v["ms_total"] / 2 for k, v in prof.items()}}
 
 
-def serving_leg(M, I, torch, duration=10.0, big=False, policy="fifo"):
+def serving_leg(M, I, torch, duration=10.0, big=True, policy="fifo"):
     """Config 5: Poisson arrivals (20 requests/s, seed 5) of turbulence runs, cubic n in
-    {32..192} (and 512 with probability 0.005 when big), 20-200 steps, FP32 bulk, submitted in real
+    {32..192} and 512 with probability 0.005 (when big), 20-200 steps, FP32 bulk, submitted in real
     time to the continuous-batching server.  Velocity fields: one cached solenoidal field per size,
-    shifted periodically per request."""
+    shifted periodically per request.  Besides p50/p99 time-to-result it reports the service time
+    (admission to result) and the queueing delay (submission to admission) per size class, and the
+    admission log's summary."""
     arr = [r for r in I.serving_arrivals(big_prob=0.005 if big else 0.0) if r["t"] < duration]
     base = {}
     for n in sorted({r["n"] for r in arr}):
@@ -319,10 +381,11 @@ def serving_leg(M, I, torch, duration=10.0, big=False, policy="fifo"):
         while time.perf_counter() - t0 < r["t"]:
             time.sleep(0.001)
         ids.append((srv.submit(ic, nsteps=r["steps"], precision=1), r))
-    srv.drain(1800)
+    srv.drain(3600)
     wall = time.perf_counter() - t0
     lat, work, first, last = [], 0, None, None
     failed = {}
+    classes = {}
     for rid, r in ids:
         rc, res = srv.poll(rid)
         if rc != 0:
@@ -333,15 +396,30 @@ def serving_leg(M, I, torch, duration=10.0, big=False, policy="fifo"):
         work += res["cells"] * res["steps_done"]
         first = res["t_submit"] if first is None else min(first, res["t_submit"])
         last = res["t_done"] if last is None else max(last, res["t_done"])
+        n = r["n"]
+        cls = "512" if n == 512 else ("32-64" if n <= 64 else ("72-128" if n <= 128 else "136-192"))
+        c = classes.setdefault(cls, {"service_s": [], "queue_s": [], "rate": []})
+        svc = res["t_done"] - res["t_admit"]
+        c["service_s"].append(svc)
+        c["queue_s"].append(res["t_admit"] - res["t_submit"])
+        c["rate"].append(res["cells"] * res["steps_done"] / max(svc, 1e-9) / 1e6)
     st = srv.stats()
     srv.close()
     lat = np.array(lat)
+    table = {k: {"requests": len(v["service_s"]), "service_p50_s": float(np.median(v["service_s"])),
+                 "service_p99_s": float(np.percentile(v["service_s"], 99)),
+                 "queue_p50_s": float(np.median(v["queue_s"])),
+                 "per_request_mcell_updates_s_p50": float(np.median(v["rate"]))}
+             for k, v in sorted(classes.items())}
     return {"workload": "serving_poisson_20rps_fp32bulk", "requests": len(ids), "completed": len(lat),
-            "stream_s": duration, "big_512": bool(big), "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "value": work / (last - first) / 1e6,
-            "unit": METRIC, "wall_s": wall, "hbm_budget_bytes": budget, "peak_bytes": st["peak_bytes"],
-            "peak_active": st["peak_active"], "scheduler_iterations": st["iterations"], "failed": failed,
-            "policy": policy}
+            "stream_s": duration, "big_512": bool(big), "requests_512": sum(1 for _, r in ids if r["n"] == 512),
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "value": work / (last - first) / 1e6, "unit": METRIC, "wall_s": wall,
+            "by_size": table,
+            "admission": {"hbm_budget_bytes": budget, "peak_bytes": st["peak_bytes"],
+                          "peak_active": st["peak_active"], "scheduler_iterations": st["iterations"],
+                          "max_active": 64},
+            "failed": failed, "policy": policy}
 
 
 def run_leg(args):
@@ -353,7 +431,7 @@ def run_leg(args):
     from paper_1608_08748_gb300 import inputs as I
     fn = {"fp32": fp32_leg, "batched": batched_leg, "serving": serving_leg, "heatcool": heatcool_leg,
           "gravity": gravity_leg, "ions": ions_leg}[args.leg]
-    kw = {"policy": args.serve_policy, "big": args.serving_big} if args.leg == "serving" else {}
+    kw = {"policy": args.serve_policy, "big": not args.no_serving_big} if args.leg == "serving" else {}
     print(json.dumps({args.leg: fn(M, I, torch, **kw)}), flush=True)
 
 
@@ -446,9 +524,13 @@ def run_ours(args):
         faces_per_launch = (N_GRID + 1) * N_GRID * N_GRID
         avg_launch_s = kernels["euler_face"]["ms_total"] / kernels["euler_face"]["launches"] * 1e-3
         achieved = FLOPS_PER_EULER_FACE * faces_per_launch / avg_launch_s / 1e12
+        measured = M.probe_fma_peak(fp64=True)
         roofline = {"bound": "alu", "kernel": "kb_euler_pencil (FP64)", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "traffic": EULER_FACE_TRAFFIC_BYTES, "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
+                    "traffic": EULER_FACE_TRAFFIC_BYTES,
+                    "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                    "peak_measured": measured, "frac_of_measured": achieved / measured,
+                    "peak_measured_source": "FP64 FMA chains timed here (mhd_probe_fma_peak)"}
 
     if rank != 0:
         return
@@ -457,15 +539,18 @@ def run_ours(args):
     if world == 1 and not args.no_extras:
         extras["fp32_bulk"] = fp32_leg(M, I, torch)
         extras["batched"] = batched_leg(M, I, torch)
-        extras["serving"] = serving_leg(M, I, torch, big=args.serving_big, policy=args.serve_policy)
+        extras["serving"] = serving_leg(M, I, torch, big=not args.no_serving_big, policy=args.serve_policy)
         extras["heatcool"] = heatcool_leg(M, I, torch)
         extras["gravity"] = gravity_leg(M, I, torch)
         extras["ions"] = ions_leg(M, I, torch)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, secs = oracle_rate(48, 8)
+        rate1, _, secs1 = oracle_rate(32, 4, threads=1)
         cpu = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle",
-               "sample": f"48^3 box of the same turbulence set-up, 8 steps ({secs:.1f} s)"}
+               "sample": f"48^3 box of the same turbulence set-up, 8 steps ({secs:.1f} s)",
+               "one_core": {"value": rate1, "unit": METRIC, "cores": 1,
+                            "sample": f"32^3 box of the same set-up, 4 steps ({secs1:.1f} s)"}}
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -477,6 +562,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline,
+        "roofline_hbm": hbm_roofline(BYTES_PER_CELL_UPDATE[8], cells, ms / args.steps),
         "cpu_baseline": cpu,
         "kernels": kernels,
     }
@@ -498,8 +584,8 @@ def main():
                     help="run one secondary leg alone (for profiling)")
     ap.add_argument("--serve-policy", choices=["fifo", "smallest_work"], default="fifo",
                     help="admission order of the serving leg")
-    ap.add_argument("--serving-big", action="store_true",
-                    help="include the 512^3 request class (probability 0.005) in the serving leg")
+    ap.add_argument("--no-serving-big", action="store_true",
+                    help="leave the 512^3 request class (probability 0.005) out of the serving leg")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

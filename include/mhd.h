@@ -294,14 +294,24 @@ int mhd_server_stats(mhd_server* srv, int64_t* iterations, int64_t* peak_bytes, 
    MHD_NOALLOC_MAX_CELLS / 256 * 9 doubles (1.125 MiB) that every GPU which loads the library holds
    until the process exits; nx*ny*nz above MHD_NOALLOC_MAX_CELLS returns MHD_EINVAL.  The first
    call on a device looks up that array's device address (cudaGetSymbolAddress), so make the first
-   call on each device before any stream capture.  Every call shares the array: calls that may
-   overlap on the GPU (different streams, or different host threads) race and must be serialised
-   by the caller. */
+   call on each device before any stream capture.  The address belongs to the device's current
+   context: after that context is replaced (cudaDeviceReset, or a context of the caller's own) the
+   next call looks it up again, so that call too belongs before any capture.  Every call shares
+   the array: calls that may overlap on the GPU (different streams, or different host threads)
+   race and must be serialised by the caller. */
 #define MHD_NOALLOC_MAX_CELLS 4194304LL
 int mhd_diagnostics_noalloc(const double* rho, const double* mx, const double* my,
                             const double* mz, const double* E, const double* bx, const double* by,
                             const double* bz, int nx, int ny, int nz, int bc_x, int bc_y,
                             int bc_z, double* out, void* stream);
+
+/* Measured FMA peak of the current GPU in TFLOP/s (an FMA counted as two flops): a grid of eight
+   blocks of 256 threads per SM, each thread running eight independent chains of `iters` dependent
+   FMAs in FP64 (fp64 = 1) or FP32 (fp64 = 0), the best of three launches timed with CUDA events
+   after one warm-up.  The roofline denominator of the kernels bound by an arithmetic pipe (the
+   paper has no counterpart: this is measurement support).  Synchronises the device; allocates and
+   frees one small output array.  MHD_EINVAL for fp64 not in {0, 1}, iters < 1 or a null tflops. */
+int mhd_probe_fma_peak(int fp64, int iters, double* tflops);
 
 /* Bytes of device memory one sim of this size uses (precision 0 FP64 / 1 FP32, chem 0/1). */
 size_t mhd_bytes_needed(int nx, int ny, int nz, int precision, int chem);

@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmhd.so")
-SOURCES = ["mhd.cu", "mhd_noalloc.cu", "mhd_server.cu", "mhd_gravity.cu"]
+SOURCES = ["mhd.cu", "mhd_noalloc.cu", "mhd_server.cu", "mhd_gravity.cu", "mhd_probe.cu"]
 # FP32-bulk launchers: compiled separately with contraction on
 SOURCES_F32 = ["mhd_f32.cu"]
 HEADERS = ["mhd_device.cuh", "mhd_kernels.cuh", "mhd_runtime.cuh"]

@@ -9,6 +9,7 @@
 //     synchronise) that application's caching allocator.
 // For them this file keeps the block partials of the reduction in a fixed file-scope device array,
 // so the call below only launches two kernels.
+#include <cuda.h>  // types of the two driver entry points fetched at run time (no libcuda link)
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -33,7 +34,40 @@ static __device__ __align__(256) double g_partials[NA_MAX_BLOCKS * 9];
 
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_mutex;
+// Per device: the address of g_partials and the id of the context it was looked up in.  A device
+// reset destroys that context and loads the module again at another address, so the address is
+// only reused while the same context (by its process-unique id) is current.
 double* g_ptr[NA_MAX_DEVICES] = {nullptr};
+unsigned long long g_ctx_id[NA_MAX_DEVICES] = {0};
+
+// cuCtxGetCurrent and cuCtxGetId, fetched from the driver through the runtime, so that the library
+// does not link libcuda itself (it still loads on a machine without a driver)
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+ctx_get_current_fn g_ctx_get_current = nullptr;
+ctx_get_id_fn g_ctx_get_id = nullptr;
+
+// id of the current context (0 if none is current or the driver does not tell)
+unsigned long long current_context_id() {
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+      cudaGetLastError();
+      return 0;
+    }
+    g_ctx_get_current = (ctx_get_current_fn)f1;
+    g_ctx_get_id = (ctx_get_id_fn)f2;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 
 __device__ __forceinline__ long long na_up(int i, int j, int k, int d, const int n[3], const int bc[3]) {
@@ -106,20 +140,23 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_final(const double* part, int
   if (threadIdx.x < 9) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// Device address of g_partials on the current device, looked up once per device.  In host code
-// the name g_partials is only a host-side stand-in, never a device address.
+// Device address of g_partials on the current device, looked up once per device (and again after
+// the device's context was replaced, as by cudaDeviceReset).  In host code the name g_partials is
+// only a host-side stand-in, never a device address.
 int scratch_for_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return mhd_rt::set_error(MHD_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= NA_MAX_DEVICES) return mhd_rt::set_error(MHD_EINVAL, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_ptr[dev]) {
+  const unsigned long long id = current_context_id();
+  if (!g_ptr[dev] || id == 0 || id != g_ctx_id[dev]) {
     double* p = nullptr;
-    e = cudaGetSymbolAddress((void**)&p, g_partials);
+    e = cudaGetSymbolAddress((void**)&p, g_partials);  // creates the context if none is current yet
     if (e != cudaSuccess || p == nullptr)
       return mhd_rt::set_error(MHD_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     g_ptr[dev] = p;
+    g_ctx_id[dev] = current_context_id();
   }
   *out = g_ptr[dev];
   return MHD_OK;

@@ -88,6 +88,7 @@ def lib():
         L.mhd_get_potential.argtypes = [vp, vp]
         L.mhd_set_ions.argtypes = [vp, vp, i]
         L.mhd_selftest_helpers.argtypes = [vp, i, vp]
+        L.mhd_probe_fma_peak.argtypes = [i, i, C.POINTER(d)]
         L.mhd_get_ions.argtypes = [vp, vp, i]
         L.mhd_batch_create.restype = vp
         L.mhd_batch_create.argtypes = [C.POINTER(vp), i]
@@ -274,6 +275,15 @@ def selftest_helpers(x):
     out = torch.empty((xd.numel(), 8), dtype=torch.float64, device=xd.device)
     _check(lib().mhd_selftest_helpers(xd.data_ptr(), xd.numel(), out.data_ptr()))
     return out.cpu().numpy()
+
+
+def probe_fma_peak(fp64=True, iters=None):
+    """Measured FMA peak of the current GPU in TFLOP/s (mhd_probe_fma_peak), FP64 or FP32."""
+    if iters is None:
+        iters = 20000 if fp64 else 400000
+    out = C.c_double(0.0)
+    _check(lib().mhd_probe_fma_peak(int(bool(fp64)), int(iters), C.byref(out)))
+    return out.value
 
 
 def from_ic(ic, **options):

@@ -6,12 +6,15 @@ simulation allocated, on two calls in a row.
 This file is collected last on purpose, so a run that stops at the first failure has already run
 every other test."""
 import ctypes as C
+import os
+import sys
 
 import numpy as np
 import pytest
 
 from paper_1608_08748_gb300 import inputs as I
 
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
 
@@ -66,6 +69,42 @@ def test_noalloc_diagnostics_match_allocating_entry_point():
         for q, k in enumerate(keys):
             scale = max(abs(want[k]), abs(want["rho"]) * 1e-12, 1e-300)
             assert abs(got[q] - want[k]) <= TOL * scale, (call, k, got[q], want[k])
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 0, 1)], ids=["periodic", "outflow_xz"])
+def test_noalloc_diagnostics_match_the_oracle(oracle_mod, bc):
+    """The same nine values against the oracle's diagnostics of the same state (sums to 1e-12 of
+    the sum of |terms|; max |div b| h, here of order the field's variation, to 1e-12 of max |b|),
+    right after the load and after three steps, with periodic and with outflow upper faces."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1608_08748_gb300 import build as B
+    B.build()
+    import paper_1608_08748_gb300 as M
+    import test_gpu_diagnostics as TD
+
+    shape = (14, 17, 20)
+    ic = TD.divergent_turbulence(shape)
+    ic["options"] = dict(ic["options"], bc_x=bc[0], bc_y=bc[1], bc_z=bc[2])
+    sim = M.from_ic(ic)
+    o = oracle_mod.run(ic)
+    fn = _noalloc_fn(M)
+    out = torch.empty(9, dtype=torch.float64, device="cuda")
+    keys = ["rho", "mx", "my", "mz", "E", "bx", "by", "bz", "max_div_b_h"]
+    for call in range(2):
+        st, faces = _device_state(M, torch, sim, shape)
+        out.fill_(float("nan"))
+        args = [st["rho"].data_ptr(), st["mom"][0].data_ptr(), st["mom"][1].data_ptr(),
+                st["mom"][2].data_ptr(), st["E"].data_ptr()] + [f.data_ptr() for f in faces]
+        rc = fn(*args, shape[2], shape[1], shape[0], bc[0], bc[1], bc[2], out.data_ptr(), None)
+        assert rc == 0, M.lib().mhd_last_error()
+        torch.cuda.synchronize()
+        got = dict(zip(keys, out.cpu().numpy().tolist()))
+        TD.check(got, o.diag(), o, 1e-12)
+        for _ in range(3):
+            sim.step(0.4)
+            o.step(0.4)
 
 
 def test_noalloc_rejects_sizes_beyond_its_fixed_scratch():
