@@ -46,7 +46,8 @@ enum mhd_status {
                             the state is left as the failing step produced it */
   MHD_ETIMEOUT = -5,     /* a bounded wait gave up */
   MHD_ENOTFOUND = -6,    /* serving: unknown request id */
-  MHD_ECAPACITY = -7     /* serving: request can never fit the memory budget */
+  MHD_ECAPACITY = -7,    /* serving: request can never fit the memory budget */
+  MHD_ECANCELED = -8     /* serving: the request was cancelled (mhd_cancel) */
 };
 
 enum mhd_option {
@@ -93,7 +94,9 @@ enum mhd_dtype { MHD_F64 = 0, MHD_F32 = 1 };
 
 /* Field set for set/get.  All pointers host or all device (on_device), dtype MHD_F64 or MHD_F32.
    mom and B are three arrays each (x, y, z); B is cell-centred.  rho_h2 may be NULL (then zero on
-   input, skipped on output). */
+   input, skipped on output).  Host arrays that are page-locked (cudaMallocHost, cudaHostAlloc,
+   cudaHostRegister of the whole array) are read and written in place by the load and store
+   kernels (over NVLink-C2C on GB300); pageable ones go through a device staging copy. */
 typedef struct mhd_fields {
   void* rho;
   void* mom[3];
@@ -148,8 +151,12 @@ int mhd_set_ions(mhd_sim* s, const double* rho_hp, int on_device);
 int mhd_get_ions(mhd_sim* s, double* rho_hp, int on_device);
 
 /* One full step with tau = CFL-limited (Sec. 2.3).  dt_taken may be NULL: then the call only
-   enqueues work and does not synchronise (errors of the step surface at the next synchronising
-   call).  With dt_taken != NULL it waits for the step and reports MHD_ENONPHYS. */
+   enqueues work and does not synchronise.  Every step copies its error flags to a host-mapped word
+   when it finishes, so such a call first returns MHD_ENONPHYS (or MHD_EINVAL for tau <= 0) if a
+   step that has finished on the device by then flagged a non-physical state; a flagged step still
+   in flight surfaces at a later mhd_step or at the next synchronising call (mhd_sync,
+   mhd_diagnostics, mhd_step with dt_taken).  With dt_taken != NULL it waits for the step and
+   reports MHD_ENONPHYS. */
 int mhd_step(mhd_sim* s, double cfl, double* dt_taken);
 /* Steps until t_end (the last step truncated to t_end) or max_steps. */
 int mhd_advance(mhd_sim* s, double cfl, double t_end, int max_steps, int* steps_done);
@@ -213,6 +220,13 @@ void mhd_batch_destroy(mhd_batch* b);
 int mhd_batch_step(mhd_batch* b, double cfl);
 /* Wait for the batch's work; MHD_ENONPHYS if any member flagged a non-physical state. */
 int mhd_batch_sync(mhd_batch* b);
+/* Non-blocking: MHD_PENDING while the batch's work is still queued or running, else as
+   mhd_batch_sync. */
+int mhd_batch_query(mhd_batch* b);
+/* Issue the batch's work on a stream of the device's highest (high = 1) or lowest (0, the
+   default) priority: where batches of both kinds are in flight, the block scheduler starts the
+   high-priority batch's blocks first as SMs free up. */
+int mhd_batch_set_priority(mhd_batch* b, int high);
 /* Autotune the launch shape (threads per tile, grid size) of every kernel class on this batch by
    timing `reps` full steps per candidate; the members' states are restored afterwards, so tuning
    changes no results.  best_ms (may be NULL) receives the tuned per-step time. */
@@ -228,12 +242,14 @@ int mhd_batch_profile(mhd_batch* b, double cfl, int steps, double* out_ms, int64
 /* ---- Serving: continuous batching of simulation requests -------------------------------------
    A server owns a scheduler thread.  Requests (a grid, an initial state and a number of steps)
    wait in arrival order; a request is admitted when its device memory (mhd_bytes_needed) fits in
-   the remaining HBM budget and fewer than max_active are running.  Every scheduler iteration
-   advances all admitted requests of one precision by one step in one batched launch per kernel
-   class (their work overlaps on the device); a request that has taken its steps is copied back to
+   the remaining HBM budget and fewer than max_active are running.  The admitted requests of one
+   precision and size lane (mhd_server_set_bulk_cells) advance together, one step per batched launch
+   per kernel class (their work overlaps on the device), each lane on a stream of its own priority
+   and as soon as its previous step has finished; a request that has taken its steps is copied back to
    host memory and its device memory released, which admits waiting requests.  A request's result
-   is the same as running it alone (bit for bit).  mhd_submit, mhd_poll and mhd_fetch are
-   thread-safe. */
+   is the same as running it alone (bit for bit).  A request whose device memory cannot be had when
+   it is admitted (mhd_create fails) ends with that error (MHD_ENOMEM for a failed allocation) and
+   gives its budget back; the server carries on.  Every server call is thread-safe. */
 typedef struct mhd_server mhd_server;
 
 typedef struct mhd_request {
@@ -273,6 +289,24 @@ int mhd_fetch(mhd_server* srv, int64_t id, mhd_fields* out);
 /* Wait (up to timeout_s seconds) until every submitted request has finished: MHD_OK or
    MHD_ETIMEOUT. */
 int mhd_server_drain(mhd_server* srv, double timeout_s);
+/* Cancel a request.  A waiting request leaves the queue at once; a running one is retired at the
+   end of the scheduler's current batched step (its device memory released, no result kept).  Its
+   status becomes MHD_ECANCELED (mhd_poll, mhd_fetch).  Returns MHD_OK, MHD_ENOTFOUND for an
+   unknown id, or MHD_EINVAL if the request has already finished. */
+int mhd_cancel(mhd_server* srv, int64_t id);
+/* Pause (paused = 1) or resume (0) admission: while paused no waiting request is admitted;
+   running requests keep stepping.  For maintenance and draining. */
+int mhd_server_pause(mhd_server* srv, int paused);
+/* Requests of at least `cells` cells (default 16,777,216, i.e. 256^3) form the bulk lane: they are
+   batched apart from the smaller ones and step on a low-priority stream, while the smaller ones
+   step on a high-priority stream, each group as soon as its previous step has finished.  A large
+   box then shares the GPU with the small requests instead of setting the pace of their steps.
+   Applies to requests admitted afterwards.  MHD_EINVAL for cells < 1. */
+int mhd_server_set_bulk_cells(mhd_server* srv, int64_t cells);
+/* Change the HBM budget.  Waiting requests that can no longer ever fit fail with MHD_ECAPACITY;
+   running requests are not disturbed, and a budget below what they use only holds back further
+   admissions until they finish.  MHD_EINVAL for a zero budget. */
+int mhd_server_set_budget(mhd_server* srv, size_t hbm_budget_bytes);
 /* Server clock now (same clock as the result times). */
 double mhd_server_clock(mhd_server* srv);
 /* Scheduler statistics: iterations (batched steps), peak bytes admitted, peak active requests. */

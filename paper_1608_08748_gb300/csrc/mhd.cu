@@ -18,9 +18,11 @@ using namespace mhd_rt;
 namespace {
 
 thread_local std::string g_err;
+thread_local int g_err_code = MHD_OK;
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
+  g_err_code = code;
   return code;
 }
 
@@ -35,6 +37,8 @@ int fail(int code, const std::string& msg) {
 namespace mhd_rt {
 // record the message mhd_last_error() returns on this thread; returns code
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
+// the code of the last failure recorded on this thread (for calls that return a pointer)
+int last_error_code() { return g_err_code; }
 }  // namespace mhd_rt
 
 namespace {
@@ -93,6 +97,7 @@ void carve(mhd_sim* S, Box<T>& B) {
     for (int v = 0; v < 8; ++v) B.fo[d].f[v] = take(NF);
   for (int d = 0; d < 3; ++d) B.e[d] = take(NF);
   B.phi = nullptr;
+  B.hflags = S->hflags_dev;
   B.g = S->g;
   B.ph = S->ph;
   B.sc = S->sc;
@@ -216,6 +221,20 @@ int refresh_cfl(mhd_sim* S) {
 
 size_t dtype_size(int dt) { return dt == MHD_F32 ? 4 : 8; }
 
+// The device address of a host buffer that kernels can read and write in place: page-locked
+// memory (cudaMallocHost, cudaHostAlloc) or memory registered with cudaHostRegister; nullptr for
+// pageable memory.  On GB300 the GPU reaches such memory over NVLink-C2C, so the load and store
+// kernels take it directly instead of a copy through the staging buffer.
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return a.devicePointer;
+}
+
 int reset_scalars(mhd_sim* S) {
   CK(cudaMemsetAsync(S->sc, 0, sizeof(Scalars), S->stream));
   S->params_dirty = true;
@@ -294,10 +313,17 @@ mhd_sim* mhd_create(int nx, int ny, int nz, double gamma, double dx) {
   S->diag_out = S->diag_part + (size_t)S->diag_blocks * 9;
   if ((e = cudaMallocHost(&S->diag_host, 16 * sizeof(double))) != cudaSuccess) return bail("cudaMallocHost(diag)", e);
   if ((e = cudaMalloc(&S->staging, (size_t)S->g.N * 10 * 8)) != cudaSuccess) return bail("cudaMalloc(staging)", e);
+  if ((e = cudaHostAlloc((void**)&S->hflags_host, sizeof(int), cudaHostAllocMapped)) != cudaSuccess)
+    return bail("cudaHostAlloc(flags)", e);
+  *(volatile int*)S->hflags_host = 0;
+  if ((e = cudaHostGetDevicePointer((void**)&S->hflags_dev, S->hflags_host, 0)) != cudaSuccess)
+    return bail("cudaHostGetDevicePointer(flags)", e);
   if (alloc_pool(S) != MHD_OK) {
     std::string msg = g_err;
+    const int code = g_err_code;
     mhd_destroy(S);
     g_err = msg;
+    g_err_code = code;
     return nullptr;
   }
   if (reset_scalars(S) != MHD_OK || cudaStreamSynchronize(S->stream) != cudaSuccess) {
@@ -320,6 +346,7 @@ void mhd_destroy(mhd_sim* S) {
   if (S->sc_host) cudaFreeHost(S->sc_host);
   if (S->diag_part) cudaFree(S->diag_part);
   if (S->diag_host) cudaFreeHost(S->diag_host);
+  if (S->hflags_host) cudaFreeHost(S->hflags_host);
   if (S->own_stream && S->stream) cudaStreamDestroy(S->stream);
   delete S;
 }
@@ -413,6 +440,8 @@ int mhd_set_state(mhd_sim* S, const mhd_fields* in) {
     }
     if (in->on_device) {
       dev[q] = src[q];
+    } else if (const void* m = mapped_host(src[q])) {
+      dev[q] = m;  // page-locked: the load kernels read it in place
     } else {
       void* dst = S->staging + (size_t)q * S->g.N * 8;
       CK(cudaMemcpyAsync(dst, src[q], bytes, cudaMemcpyHostToDevice, S->stream));
@@ -432,6 +461,7 @@ int mhd_set_state(mhd_sim* S, const mhd_fields* in) {
   if ((rc = reset_scalars(S)) != MHD_OK) return rc;
   if ((rc = refresh_cfl(S)) != MHD_OK) return rc;
   CK(cudaStreamSynchronize(S->stream));
+  *(volatile int*)S->hflags_host = 0;  // the steps before this load are finished
   S->has_state = true;
   return MHD_OK;
 }
@@ -465,11 +495,19 @@ int mhd_get_state(mhd_sim* S, mhd_fields* out) {
     if (!dst[q]) return fail(MHD_EINVAL, "mhd_get_state: rho, mom[3], E and B[3] are required");
   const size_t es = dtype_size(out->dtype), bytes = (size_t)S->g.N * es;
   void* dev[9];
+  bool in_place[9];
   for (int q = 0; q < 9; ++q) {
-    if (!dst[q])
+    in_place[q] = false;
+    if (!dst[q]) {
       dev[q] = nullptr;
-    else
-      dev[q] = out->on_device ? dst[q] : (void*)(S->staging + (size_t)q * S->g.N * 8);
+    } else if (out->on_device) {
+      dev[q] = dst[q];
+    } else if (const void* m = mapped_host(dst[q])) {
+      dev[q] = const_cast<void*>(m);  // page-locked: the store kernel writes it in place
+      in_place[q] = true;
+    } else {
+      dev[q] = (void*)(S->staging + (size_t)q * S->g.N * 8);
+    }
   }
   if (out->dtype == MHD_F64) {
     double* p[9];
@@ -482,7 +520,7 @@ int mhd_get_state(mhd_sim* S, mhd_fields* out) {
   }
   if (!out->on_device)
     for (int q = 0; q < 9; ++q)
-      if (dst[q]) CK(cudaMemcpyAsync(dst[q], dev[q], bytes, cudaMemcpyDeviceToHost, S->stream));
+      if (dst[q] && !in_place[q]) CK(cudaMemcpyAsync(dst[q], dev[q], bytes, cudaMemcpyDeviceToHost, S->stream));
   CK(cudaStreamSynchronize(S->stream));
   return MHD_OK;
 }
@@ -558,6 +596,12 @@ int mhd_step(mhd_sim* S, double cfl, double* dt_taken) {
     S->last_cfl = cfl;
     S->last_tend = 0.0;
     S->params_dirty = false;
+  }
+  if (!dt_taken) {
+    // an earlier step flagged by the device and finished by now (no synchronisation here)
+    const int hf = *(volatile int*)S->hflags_host;
+    if (hf & 1) return fail(MHD_ENONPHYS, "non-physical state after an earlier step (rho, rho eps <= 0 or non-finite)");
+    if (hf & 2) return fail(MHD_EINVAL, "tau <= 0 in an earlier step");
   }
   if ((rc = enqueue_step(S)) != MHD_OK) return rc;
   if (dt_taken) {
@@ -973,6 +1017,26 @@ int mhd_batch_sync(mhd_batch* b) {
     if (S->sc_host->flags & 1) bad = 1;
   }
   if (bad) return fail(MHD_ENONPHYS, "non-physical state in a batch member");
+  return MHD_OK;
+}
+
+int mhd_batch_query(mhd_batch* b) {
+  if (!b) return fail(MHD_EINVAL, "mhd_batch_query: null batch");
+  cudaError_t e = cudaStreamQuery(b->stream);
+  if (e == cudaErrorNotReady) return MHD_PENDING;
+  CK(e);
+  return mhd_batch_sync(b);
+}
+
+int mhd_batch_set_priority(mhd_batch* b, int high) {
+  if (!b || (high != 0 && high != 1)) return fail(MHD_EINVAL, "mhd_batch_set_priority: high must be 0 or 1");
+  int least = 0, greatest = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  cudaStream_t st = nullptr;
+  CK(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, high ? greatest : least));
+  CK(cudaStreamSynchronize(b->stream));
+  cudaStreamDestroy(b->stream);
+  b->stream = st;
   return MHD_OK;
 }
 

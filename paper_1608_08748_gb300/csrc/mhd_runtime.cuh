@@ -402,6 +402,8 @@ struct mhd_sim {
   char* staging = nullptr;  // 10 * N * 8 bytes for host transfers / dtype conversion
   Scalars* sc = nullptr;
   Scalars* sc_host = nullptr;  // pinned mirror
+  int* hflags_host = nullptr;  // host-mapped error flags of the last finished step
+  int* hflags_dev = nullptr;   // its device address
   double* diag_part = nullptr;
   double* diag_out = nullptr;
   double* diag_host = nullptr;  // pinned, 9 doubles

@@ -1,7 +1,8 @@
 // mhd_server.cu -- continuous-batching server of simulation requests (include/mhd.h, "Serving").
-// Host code only: a scheduler thread admits requests by HBM budget, advances every admitted
-// request of a (precision, CFL) group by one step per iteration with one batched launch per kernel
-// class (mhd_batch_*), retires finished requests to host memory and frees their device memory.
+// Host code only: a scheduler thread admits requests by HBM budget, advances the admitted
+// requests of each (lane, precision, CFL) group one step at a time with one batched launch per
+// kernel class (mhd_batch_*), the groups independently on streams of their lane's priority, and
+// retires finished requests to host memory and frees their device memory.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -22,6 +23,7 @@
 
 namespace mhd_rt {
 int set_error(int code, const std::string& msg);  // mhd.cu
+int last_error_code();                            // mhd.cu
 }
 
 namespace {
@@ -35,17 +37,33 @@ struct Req {
   bool has_h2 = false;
   size_t bytes = 0;
   ReqState st = WAITING;
+  bool cancel = false;  // running: retire at the end of the current batched step
   mhd_sim* sim = nullptr;
   mhd_result res{};
   std::vector<double> out[9];  // final state (float64, B cell-centred)
 };
 
-using GroupKey = std::pair<int, double>;  // (precision, cfl)
+// (lane, precision, cfl).  Lane 0 holds the requests below the bulk size and runs at high
+// stream priority; lane 1 the bulk requests at low priority, so that a large box's long steps do
+// not hold the small ones back: each group steps on its own stream as soon as its previous step
+// has finished, and the block scheduler starts the high-priority blocks first as SMs free up.
+struct GroupKey {
+  int lane;
+  int precision;
+  double cfl;
+  bool operator<(const GroupKey& o) const {
+    if (lane != o.lane) return lane < o.lane;
+    if (precision != o.precision) return precision < o.precision;
+    return cfl < o.cfl;
+  }
+};
 
 struct Group {
-  std::vector<Req*> active;
+  std::vector<Req*> active;   // the members of the batch (of the step in flight, if any)
+  std::vector<Req*> joining;  // admitted while a step was in flight: join at the next launch
   mhd_batch* batch = nullptr;
   bool dirty = true;
+  bool inflight = false;  // a batched step is queued or running on the batch's stream
 };
 
 }  // namespace
@@ -65,6 +83,8 @@ struct mhd_server {
   int64_t next_id = 0;
   int64_t unfinished = 0;
   bool stop = false;
+  bool paused = false;
+  int64_t bulk_cells = 1ll << 24;  // requests with at least this many cells run in the bulk lane
   std::thread th;
   std::chrono::steady_clock::time_point t0;
   std::atomic<int64_t> iterations{0};
@@ -84,7 +104,10 @@ size_t dsize(int dtype) { return dtype == MHD_F32 ? 4 : 8; }
 int start_request(mhd_server* S, Req* q) {
   const mhd_request& r = q->r;
   mhd_sim* sim = mhd_create(r.nx, r.ny, r.nz, r.gamma, r.dx);
-  if (!sim) return MHD_ENOMEM;
+  if (!sim) {
+    const int code = mhd_rt::last_error_code();
+    return code < 0 ? code : MHD_ENOMEM;
+  }
   int rc = MHD_OK;
   if (r.precision) rc = mhd_set_option(sim, MHD_OPT_PRECISION, 1.0);
   if (rc == MHD_OK) rc = mhd_set_option(sim, MHD_OPT_CHEM, r.chem ? 1.0 : 0.0);
@@ -141,7 +164,9 @@ void scheduler(mhd_server* S) {
     {
       std::unique_lock<std::mutex> lk(S->mu);
       if (S->stop) break;
-      if (S->policy == MHD_SERVE_FIFO) {
+      if (S->paused) {
+        // admission held: nothing leaves the queue
+      } else if (S->policy == MHD_SERVE_FIFO) {
         // strict arrival order: the head waits until it fits
         while (!S->waiting.empty()) {
           Req* q = S->reqs[S->waiting.front()].get();
@@ -177,7 +202,7 @@ void scheduler(mhd_server* S) {
         }
       }
       if (admit.empty() && S->nactive == 0) {
-        S->cv.wait(lk, [&] { return S->stop || !S->waiting.empty(); });
+        S->cv.wait(lk, [&] { return S->stop || (!S->paused && !S->waiting.empty()); });
         continue;
       }
       if ((int64_t)S->used > S->peak_bytes) S->peak_bytes = (int64_t)S->used;
@@ -196,13 +221,78 @@ void scheduler(mhd_server* S) {
         S->cv_done.notify_all();
         continue;
       }
-      Group& G = S->groups[GroupKey(q->r.precision, q->r.cfl)];
-      G.active.push_back(q);
-      G.dirty = true;
+      const int64_t cells = (int64_t)q->r.nx * q->r.ny * q->r.nz;
+      Group& G = S->groups[GroupKey{cells >= S->bulk_cells ? 1 : 0, q->r.precision, q->r.cfl}];
+      G.joining.push_back(q);
     }
-    // one batched step of every group
+    // every group whose previous step has finished: take its results, then queue its next step
+    bool progressed = !admit.empty();
     for (auto it = S->groups.begin(); it != S->groups.end();) {
       Group& G = it->second;
+      if (G.inflight) {
+        const int qrc = mhd_batch_query(G.batch);
+        if (qrc == MHD_PENDING) {
+          ++it;
+          continue;
+        }
+        G.inflight = false;
+        progressed = true;
+        std::vector<Req*> keep, done;
+        std::vector<int> qrcs;
+        for (Req* q : G.active) {
+          int r1 = qrc;
+          if (qrc == MHD_ENONPHYS) {  // find the members that flagged it
+            mhd_diag dg{};
+            r1 = (mhd_diagnostics(q->sim, &dg) == MHD_OK && !(dg.error_flags & 1)) ? MHD_OK : MHD_ENONPHYS;
+          }
+          qrcs.push_back(r1);
+        }
+        {
+          std::lock_guard<std::mutex> lk(S->mu);
+          for (size_t k = 0; k < G.active.size(); ++k) {
+            Req* q = G.active[k];
+            if (qrcs[k] == MHD_OK) q->res.steps_done += 1;
+            if (q->cancel) {
+              q->res.status = MHD_ECANCELED;
+              done.push_back(q);
+            } else if (qrcs[k] != MHD_OK || q->res.steps_done >= q->r.nsteps) {
+              if (qrcs[k] != MHD_OK) q->res.status = qrcs[k];
+              done.push_back(q);
+            } else {
+              keep.push_back(q);
+            }
+          }
+        }
+        if (!done.empty()) {
+          if (G.batch) mhd_batch_destroy(G.batch);
+          G.batch = nullptr;
+          G.dirty = true;
+          for (Req* q : done) {
+            int frc = MHD_OK;
+            if (q->res.status == MHD_ECANCELED) {  // no result is kept: release the device memory
+              mhd_destroy(q->sim);
+              q->sim = nullptr;
+            } else {
+              frc = finish_request(S, q);
+            }
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (q->res.status == MHD_PENDING) q->res.status = frc;
+            else if (q->res.status == MHD_OK && frc != MHD_OK) q->res.status = frc;
+            q->res.t_done = now_s(S);
+            q->st = q->res.status == MHD_OK ? DONE : FAILED;
+            S->used -= q->bytes;
+            S->nactive -= 1;
+            S->unfinished -= 1;
+          }
+          S->cv_done.notify_all();
+        }
+        G.active.swap(keep);
+      }
+      if (!G.joining.empty()) {  // no step in flight here: the admitted requests join now
+        G.active.insert(G.active.end(), G.joining.begin(), G.joining.end());
+        G.joining.clear();
+        G.dirty = true;
+      }
       if (G.active.empty()) {
         if (G.batch) mhd_batch_destroy(G.batch);
         it = S->groups.erase(it);
@@ -215,62 +305,49 @@ void scheduler(mhd_server* S) {
         for (Req* q : G.active) sims.push_back(q->sim);
         G.batch = mhd_batch_create(sims.data(), (int)sims.size());
         rc = G.batch ? MHD_OK : MHD_ECUDA;
+        if (rc == MHD_OK) rc = mhd_batch_set_priority(G.batch, it->first.lane == 0 ? 1 : 0);
         G.dirty = false;
       }
-      if (rc == MHD_OK) rc = mhd_batch_step(G.batch, it->first.second);
-      if (rc == MHD_OK) rc = mhd_batch_sync(G.batch);
-      std::vector<Req*> keep, done;
-      std::vector<int> qrcs;
-      for (Req* q : G.active) {
-        int qrc = rc;
-        if (rc == MHD_ENONPHYS) {  // find the members that flagged it
-          mhd_diag dg{};
-          qrc = (mhd_diagnostics(q->sim, &dg) == MHD_OK && !(dg.error_flags & 1)) ? MHD_OK : MHD_ENONPHYS;
-        }
-        qrcs.push_back(qrc);
-      }
-      {
+      if (rc == MHD_OK) rc = mhd_batch_step(G.batch, it->first.cfl);
+      if (rc == MHD_OK) {
+        G.inflight = true;
+        S->iterations += 1;
+      } else {
+        // the group cannot step: its requests end with the error
         std::lock_guard<std::mutex> lk(S->mu);
-        for (size_t k = 0; k < G.active.size(); ++k) {
-          Req* q = G.active[k];
-          if (qrcs[k] == MHD_OK) q->res.steps_done += 1;
-          if (qrcs[k] != MHD_OK || q->res.steps_done >= q->r.nsteps) {
-            if (qrcs[k] != MHD_OK) q->res.status = qrcs[k];
-            done.push_back(q);
-          } else {
-            keep.push_back(q);
-          }
-        }
-      }
-      if (!done.empty()) {
-        if (G.batch) mhd_batch_destroy(G.batch);
-        G.batch = nullptr;
-        G.dirty = true;
-        for (Req* q : done) {
-          int frc = finish_request(S, q);
-          std::lock_guard<std::mutex> lk(S->mu);
-          if (q->res.status == MHD_PENDING) q->res.status = frc;
-          else if (q->res.status == MHD_OK && frc != MHD_OK) q->res.status = frc;
+        for (Req* q : G.active) {
+          if (q->sim) mhd_destroy(q->sim);
+          q->sim = nullptr;
+          q->res.status = rc;
           q->res.t_done = now_s(S);
-          q->st = q->res.status == MHD_OK ? DONE : FAILED;
+          q->st = FAILED;
           S->used -= q->bytes;
           S->nactive -= 1;
           S->unfinished -= 1;
         }
         S->cv_done.notify_all();
+        G.active.clear();
+        if (G.batch) mhd_batch_destroy(G.batch);
+        G.batch = nullptr;
+        it = S->groups.erase(it);
+        continue;
       }
-      G.active.swap(keep);
       ++it;
     }
-    S->iterations += 1;
+    if (!progressed) {
+      // nothing finished: wait a little for the device (or for a submission or a stop)
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait_for(lk, std::chrono::microseconds(200), [&] { return S->stop; });
+    }
   }
   for (auto& kv : S->groups) {
     if (kv.second.batch) mhd_batch_destroy(kv.second.batch);
-    for (Req* q : kv.second.active)
-      if (q->sim) {
-        mhd_destroy(q->sim);
-        q->sim = nullptr;
-      }
+    for (auto* list : {&kv.second.active, &kv.second.joining})
+      for (Req* q : *list)
+        if (q->sim) {
+          mhd_destroy(q->sim);
+          q->sim = nullptr;
+        }
   }
   S->groups.clear();
 }
@@ -391,6 +468,72 @@ int mhd_fetch(mhd_server* S, int64_t id, mhd_fields* out) {
       std::memcpy(dst[k], q->out[k].data(), N * sizeof(double));
     }
   }
+  return MHD_OK;
+}
+
+int mhd_cancel(mhd_server* S, int64_t id) {
+  if (!S) return mhd_rt::set_error(MHD_EINVAL, "mhd_cancel: null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return mhd_rt::set_error(MHD_ENOTFOUND, "mhd_cancel: unknown request id");
+  Req* q = it->second.get();
+  if (q->st == WAITING) {
+    for (auto w = S->waiting.begin(); w != S->waiting.end(); ++w)
+      if (*w == id) {
+        S->waiting.erase(w);
+        break;
+      }
+    q->st = FAILED;
+    q->res.status = MHD_ECANCELED;
+    q->res.t_done = now_s(S);
+    S->unfinished -= 1;
+    S->cv_done.notify_all();
+    return MHD_OK;
+  }
+  if (q->st == RUNNING) {
+    q->cancel = true;
+    return MHD_OK;
+  }
+  return mhd_rt::set_error(MHD_EINVAL, "mhd_cancel: the request has already finished");
+}
+
+int mhd_server_pause(mhd_server* S, int paused) {
+  if (!S || (paused != 0 && paused != 1)) return mhd_rt::set_error(MHD_EINVAL, "mhd_server_pause: paused must be 0 or 1");
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->paused = paused != 0;
+  }
+  S->cv.notify_all();
+  return MHD_OK;
+}
+
+int mhd_server_set_budget(mhd_server* S, size_t hbm_budget_bytes) {
+  if (!S || hbm_budget_bytes == 0) return mhd_rt::set_error(MHD_EINVAL, "mhd_server_set_budget: need a budget > 0");
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->budget = hbm_budget_bytes;
+    for (auto w = S->waiting.begin(); w != S->waiting.end();) {
+      Req* q = S->reqs[*w].get();
+      if (q->bytes > S->budget) {
+        q->st = FAILED;
+        q->res.status = MHD_ECAPACITY;
+        q->res.t_done = now_s(S);
+        S->unfinished -= 1;
+        w = S->waiting.erase(w);
+      } else {
+        ++w;
+      }
+    }
+    S->cv_done.notify_all();
+  }
+  S->cv.notify_all();
+  return MHD_OK;
+}
+
+int mhd_server_set_bulk_cells(mhd_server* S, int64_t cells) {
+  if (!S || cells < 1) return mhd_rt::set_error(MHD_EINVAL, "mhd_server_set_bulk_cells: need cells >= 1");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->bulk_cells = cells;
   return MHD_OK;
 }
 

@@ -18,7 +18,8 @@ OPT = {"bc_x": 1, "bc_y": 2, "bc_z": 3, "chem": 4, "precision": 5, "regul_mode":
        "chem_lshield": 8, "chem_bdop": 9, "chem_xnorm": 10, "chem_taud": 11, "graph": 14,
        "heatcool": 15, "grav_g": 16, "ions": 17}
 STATUS = {0: "MHD_OK", 1: "MHD_PENDING", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA",
-          -4: "MHD_ENONPHYS", -5: "MHD_ETIMEOUT", -6: "MHD_ENOTFOUND", -7: "MHD_ECAPACITY"}
+          -4: "MHD_ENONPHYS", -5: "MHD_ETIMEOUT", -6: "MHD_ENOTFOUND", -7: "MHD_ECAPACITY",
+          -8: "MHD_ECANCELED"}
 F64, F32 = 0, 1
 
 
@@ -111,6 +112,12 @@ def lib():
         L.mhd_server_clock.argtypes = [vp]
         L.mhd_server_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(i)]
         L.mhd_server_set_policy.argtypes = [vp, i]
+        L.mhd_cancel.argtypes = [vp, C.c_int64]
+        L.mhd_server_pause.argtypes = [vp, i]
+        L.mhd_server_set_budget.argtypes = [vp, C.c_size_t]
+        L.mhd_server_set_bulk_cells.argtypes = [vp, C.c_int64]
+        L.mhd_batch_query.argtypes = [vp]
+        L.mhd_batch_set_priority.argtypes = [vp, i]
         _lib = L
     return _lib
 
@@ -381,6 +388,26 @@ class Server:
     def set_policy(self, policy):
         """Admission order: "fifo" (the default) or "smallest_work" (fewest cells x steps first)."""
         _check(self.L.mhd_server_set_policy(self.h, {"fifo": 0, "smallest_work": 1}[policy]))
+
+    def cancel(self, rid):
+        """Cancel a waiting or running request (its status becomes MHD_ECANCELED)."""
+        _check(self.L.mhd_cancel(self.h, int(rid)))
+
+    def pause(self, paused=True):
+        """Hold (True) or resume (False) the admission of waiting requests."""
+        _check(self.L.mhd_server_pause(self.h, int(bool(paused))))
+
+    def set_budget(self, hbm_budget_bytes):
+        """New HBM budget; waiting requests that can no longer fit fail with MHD_ECAPACITY."""
+        _check(self.L.mhd_server_set_budget(self.h, int(hbm_budget_bytes)))
+
+    def set_bulk_cells(self, cells):
+        """Requests of at least `cells` cells run in the low-priority bulk lane."""
+        _check(self.L.mhd_server_set_bulk_cells(self.h, int(cells)))
+
+    def drain_rc(self, timeout_s):
+        """mhd_server_drain's status (MHD_OK or MHD_ETIMEOUT) without raising."""
+        return self.L.mhd_server_drain(self.h, float(timeout_s))
 
     def submit(self, ic, nsteps, cfl=0.4, precision=1):
         """Queue a request built from an initial-condition dict; returns its id."""

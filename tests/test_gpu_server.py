@@ -65,3 +65,32 @@ def test_served_results_equal_solo_runs(M, policy):
         for f in ["rho", "E", "mom", "B", "rho_h2"]:
             assert np.array_equal(got[f], want[f]), (k, f)
     srv.close()
+
+
+def test_failed_device_allocation_and_running_cancel(M):
+    """A request whose device memory cannot be had when it is admitted ends with MHD_ENOMEM and
+    gives its budget back, and the server carries on: here the GPU's memory is first taken by the
+    test (about 1.5 GB left), and a 192^3 request (2.2 GB) is admitted against a budget that would
+    allow it.  Then a long request is cancelled while it runs: it ends with MHD_ECANCELED at the
+    end of a batched step, and a request behind it completes."""
+    import torch
+    srv = M.Server(1 << 40, 8)
+    free, _ = torch.cuda.mem_get_info()
+    filler = torch.empty(max(free - (3 << 29), 1), dtype=torch.uint8, device="cuda")
+    rid = srv.submit(I.turbulence(8, mach=2.0, seed=3, shape=(192, 192, 192)), nsteps=2)
+    srv.drain(120)
+    rc, res = srv.poll(rid)
+    assert rc == -2, rc  # MHD_ENOMEM
+    del filler
+    torch.cuda.empty_cache()
+    long_id = srv.submit(request_ic(0), nsteps=100000)
+    t0 = time.time()
+    while srv.poll(long_id)[1]["steps_done"] < 3 and time.time() - t0 < 60:
+        time.sleep(0.01)
+    srv.cancel(long_id)
+    after = srv.submit(request_ic(1), nsteps=3)
+    srv.drain(120)
+    rc, res = srv.poll(long_id)
+    assert rc == -8 and 3 <= res["steps_done"] < 100000
+    assert srv.poll(after)[0] == 0
+    srv.close()

@@ -60,3 +60,46 @@ def test_bad_arguments_are_rejected(M):
         s.step(0.4)  # no state loaded
     with pytest.raises(M.MHDError):
         s.set_option("precision", 7)
+
+
+def test_enqueue_only_step_reports_an_earlier_flagged_step(M):
+    """mhd_step with dt = NULL does not synchronise, but once a flagged step has finished on the
+    device the next such call returns the error (host-mapped copy of the step's flags)."""
+    import torch
+    ic = I.turbulence(8, mach=2.0, seed=64, shape=(8, 8, 8))
+    ic["rho"][2, 3, 4] = np.nan
+    s = M.from_ic(ic)
+    st = torch.cuda.Stream()
+    s.set_stream(st.cuda_stream)
+    s.step(0.4, sync=False)  # nothing has run yet when it is enqueued
+    st.synchronize()
+    with pytest.raises(M.MHDError) as e:
+        s.step(0.4, sync=False)
+    assert e.value.code in (-4, -1)
+    ok = M.from_ic(I.turbulence(8, mach=2.0, seed=65, shape=(8, 8, 8)))
+    ok.set_stream(st.cuda_stream)
+    for _ in range(3):
+        ok.step(0.4, sync=False)
+    st.synchronize()
+    ok.step(0.4, sync=False)  # a healthy sim keeps stepping
+    ok.sync()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_page_locked_host_buffers_equal_pageable(M, precision):
+    """set_state and get_state with page-locked host arrays (read and written in place by the
+    kernels) give the same bits as with pageable arrays (copied through the staging buffer)."""
+    import torch
+    ic = I.turbulence(8, mach=3.0, seed=66, shape=(10, 12, 14))
+    a = M.from_ic(ic, precision=precision)
+    b = M.Sim(14, 12, 10, ic["gamma"], ic["dx"], precision=precision, chem=1)
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(ic[k])).pin_memory()
+              for k in ["rho", "mom", "E", "B", "rho_h2"]}
+    b.set_state(*[pinned[k].numpy() for k in ["rho", "mom", "E", "B", "rho_h2"]])
+    for s in (a, b):
+        s.step(0.4)
+    out = {k: torch.empty(tuple(v.shape), dtype=torch.float64).pin_memory() for k, v in pinned.items()}
+    got = b.get_state(out={k: v.numpy() for k, v in out.items()})
+    want = a.get_state()
+    for k in ["rho", "mom", "E", "B", "rho_h2"]:
+        assert np.array_equal(np.asarray(got[k]), want[k]), k
