@@ -49,14 +49,16 @@ HBM_FALLBACK_GBS = 6800.0
 # the Riemann solve (Roe average, speeds and eigenvector rows 116; the three wave pairs'
 # domain-of-dependence averages with L q and R s 244) and the fluxes (25)
 FLOPS_PER_EULER_FACE = 577
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one x-direction Eulerian face launch
-# at 128^3, from one ncu capture of this kernel (set to None whenever the kernel changes)
-EULER_FACE_TRAFFIC_BYTES = 358.3e6
-# FP32 bulk: FP32 flops of one Eulerian face (fadd + fmul + 2 ffma executed, from one ncu capture
-# of kb_euler_pencil<float>, divided by the faces of the launch) and the DRAM bytes of one 256^3
-# launch; None until captured for the current kernel
-FP32_FLOPS_PER_EULER_FACE = None
-EULER_FACE_TRAFFIC_BYTES_FP32 = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one Eulerian face launch at 128^3,
+# the mean of the x, y and z launches of one ncu capture of this kernel (357.7, 256.3, 260.7 MB;
+# profiles/kb_metrics_turbulence_128_fp64.md; set to None whenever the kernel changes)
+EULER_FACE_TRAFFIC_BYTES = 291.6e6
+# FP32 bulk: FP32 flops of one Eulerian face (fadd + fmul + 2 ffma executed per face, 848-851 in
+# the three directions of one ncu capture of kb_euler_pencil<float> at 128^3) and the DRAM bytes of
+# one 256^3 launch: the mean of the 128^3 capture's x, y, z launches (143.3, 107.4, 111.9 MB) times
+# 8, the ratio of the faces processed (profiles/kb_metrics_turbulence_128_fp32bulk.md)
+FP32_FLOPS_PER_EULER_FACE = 849
+EULER_FACE_TRAFFIC_BYTES_FP32 = 120.9e6 * 8
 
 
 def hbm_peak():
@@ -357,14 +359,14 @@ def batched_leg(M, I, torch, steps=20, warm=3):
             "kernels": {k: v["ms_total"] / 2 for k, v in prof.items()}}
 
 
-def serving_leg(M, I, torch, duration=10.0, big=True, policy="fifo"):
+def serving_leg(M, I, torch, duration=10.0, big=True, policy="fifo", rate=20.0):
     """Config 5: Poisson arrivals (20 requests/s, seed 5) of turbulence runs, cubic n in
     {32..192} and 512 with probability 0.005 (when big), 20-200 steps, FP32 bulk, submitted in real
     time to the continuous-batching server.  Velocity fields: one cached solenoidal field per size,
     shifted periodically per request.  Besides p50/p99 time-to-result it reports the service time
     (admission to result) and the queueing delay (submission to admission) per size class, and the
     admission log's summary."""
-    arr = [r for r in I.serving_arrivals(big_prob=0.005 if big else 0.0) if r["t"] < duration]
+    arr = [r for r in I.serving_arrivals(rate=rate, big_prob=0.005 if big else 0.0) if r["t"] < duration]
     base = {}
     for n in sorted({r["n"] for r in arr}):
         base[n] = I.solenoidal_field((n, n, n), seed=n)
@@ -411,7 +413,7 @@ def serving_leg(M, I, torch, duration=10.0, big=True, policy="fifo"):
                  "queue_p50_s": float(np.median(v["queue_s"])),
                  "per_request_mcell_updates_s_p50": float(np.median(v["rate"]))}
              for k, v in sorted(classes.items())}
-    return {"workload": "serving_poisson_20rps_fp32bulk", "requests": len(ids), "completed": len(lat),
+    return {"workload": f"serving_poisson_{rate:g}rps_fp32bulk", "requests": len(ids), "completed": len(lat),
             "stream_s": duration, "big_512": bool(big), "requests_512": sum(1 for _, r in ids if r["n"] == 512),
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "value": work / (last - first) / 1e6, "unit": METRIC, "wall_s": wall,
@@ -422,6 +424,18 @@ def serving_leg(M, I, torch, duration=10.0, big=True, policy="fifo"):
             "failed": failed, "policy": policy}
 
 
+def steps_leg(M, I, torch, grid=128, precision=0, nsteps=4, graph=1):
+    """A plain run of nsteps steps of the turbulence box at grid^3 (no timing): the case the ncu
+    captures of profiles/ run, small enough for a multi-pass capture."""
+    ic = I.turbulence(grid, mach=5.0, beta=1.0, seed=1)
+    s = M.from_ic(ic, precision=precision, graph=graph)
+    for _ in range(nsteps):
+        s.step(CFL, sync=False)
+    s.sync()
+    return {"workload": f"mhd_turbulence_h2chem_{grid}^3_{'fp32bulk' if precision else 'fp64'}",
+            "steps": nsteps, "t": s.diagnostics()["t"]}
+
+
 def run_leg(args):
     """One secondary leg alone (profiling): prints its JSON object."""
     import torch
@@ -429,6 +443,10 @@ def run_leg(args):
     B.build()
     import paper_1608_08748_gb300 as M
     from paper_1608_08748_gb300 import inputs as I
+    if args.leg == "steps":
+        print(json.dumps({"steps": steps_leg(M, I, torch, args.grid, args.precision, args.nsteps,
+                                             args.graph)}), flush=True)
+        return
     fn = {"fp32": fp32_leg, "batched": batched_leg, "serving": serving_leg, "heatcool": heatcool_leg,
           "gravity": gravity_leg, "ions": ions_leg}[args.leg]
     kw = {"policy": args.serve_policy, "big": not args.no_serving_big} if args.leg == "serving" else {}
@@ -540,6 +558,9 @@ def run_ours(args):
         extras["fp32_bulk"] = fp32_leg(M, I, torch)
         extras["batched"] = batched_leg(M, I, torch)
         extras["serving"] = serving_leg(M, I, torch, big=not args.no_serving_big, policy=args.serve_policy)
+        # the same stream at a tenth of the rate, which the GPU sustains: latency is then service
+        # time, not queueing
+        extras["serving_sustained"] = serving_leg(M, I, torch, big=False, policy=args.serve_policy, rate=2.0)
         extras["heatcool"] = heatcool_leg(M, I, torch)
         extras["gravity"] = gravity_leg(M, I, torch)
         extras["ions"] = ions_leg(M, I, torch)
@@ -579,9 +600,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP32-bulk (256^3), batched-ensemble, serving, heating/cooling and gravity legs")
-    ap.add_argument("--leg", choices=["main", "fp32", "batched", "serving", "heatcool", "gravity", "ions"],
+    ap.add_argument("--leg", choices=["main", "fp32", "batched", "serving", "heatcool", "gravity", "ions", "steps"],
                     default="main",
-                    help="run one secondary leg alone (for profiling)")
+                    help="run one secondary leg alone (for profiling); 'steps' runs --nsteps plain steps "
+                         "of the turbulence box at --grid^3 in --precision (the ncu capture case)")
+    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--precision", type=int, choices=[0, 1], default=0)
+    ap.add_argument("--nsteps", type=int, default=4)
+    ap.add_argument("--graph", type=int, choices=[0, 1], default=1,
+                    help="steps leg: 1 replays the captured graph, 0 launches kernel by kernel")
     ap.add_argument("--serve-policy", choices=["fifo", "smallest_work"], default="fifo",
                     help="admission order of the serving leg")
     ap.add_argument("--no-serving-big", action="store_true",
