@@ -194,16 +194,6 @@ int mhd_profile(mhd_sim* s, double cfl, int steps, double* out_ms, int64_t* out_
 /* Number of kernel launches (not counting the copies of the RK register) in one mhd_step. */
 int mhd_launches_per_step(mhd_sim* s);
 
-/* Self-test of the device arithmetic helpers of the FP64 path, run on the current CUDA device: for
-   each of the n doubles x[i] (device memory), out[8 i + k] (device memory, 8 n doubles) receives
-   k = 0 |x| and 1 -x (sign bit), 2 x / 2 and 3 x / 4 (exponent field lowered; the product where it
-   is normal, zero, infinite or NaN, else the zero of the sign of x), 4 the ordered 64-bit key of x
-   (its bits stored in the double: signed order of the keys = order of the values, -0 below +0),
-   5 1/x, 6 1/sqrt(|x|) and 7 sqrt(|x|) by one Newton-Raphson step from the hardware seeds (within
-   2 ulp for normal nonzero arguments).  Synchronises; MHD_EINVAL for n < 0 or a null pointer with
-   n > 0. */
-int mhd_selftest_helpers(const double* x, int n, double* out);
-
 /* ---- Batched execution (many boxes, one launch per kernel class) ------------------------------
    A batch advances several simulations together: every kernel of the step is launched once over
    a table of tiles that covers all their boxes (uneven sizes allowed), and the step is captured in
@@ -338,6 +328,13 @@ int mhd_diagnostics_noalloc(const double* rho, const double* mx, const double* m
                             const double* mz, const double* E, const double* bx, const double* by,
                             const double* bz, int nx, int ny, int nz, int bc_x, int bc_y,
                             int bc_z, double* out, void* stream);
+
+/* Index checks (the paper has no counterpart: a debugging aid in place of a memory checker).  A
+   library built with -DMHD_CHECK (libmhd_check.so) tests every computed cell and lattice index of
+   its kernels against its array; a bad one is replaced by an in-bounds index and recorded here:
+   bit 0 a cell index, bit 1 a face or lattice index.  Synchronises the device; clear = 1 resets
+   the flags after reading them.  MHD_EINVAL from the plain library, which has no checks. */
+int mhd_check_flags(int clear, unsigned* flags);
 
 /* Measured FMA peak of the current GPU in TFLOP/s (an FMA counted as two flops): a grid of eight
    blocks of 256 threads per SM, each thread running eight independent chains of `iters` dependent

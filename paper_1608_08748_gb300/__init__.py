@@ -5,5 +5,5 @@ Python side (``mhd``) is argument marshalling only.  ``inputs`` builds seeded sy
 states.
 """
 from . import inputs  # noqa: F401
-from .mhd import (Batch, MHDError, Server, Sim, bytes_needed, from_ic, lib, probe_fma_peak, profile,  # noqa: F401
-                  selftest_helpers)
+from .mhd import (Batch, MHDError, Server, Sim, bytes_needed, from_ic, lib, log_steps, probe_fma_peak,  # noqa: F401
+                  profile)

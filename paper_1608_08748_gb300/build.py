@@ -18,10 +18,10 @@ HEADERS = ["mhd_device.cuh", "mhd_kernels.cuh", "mhd_runtime.cuh"]
 # removes ~15 % of its instructions); it then agrees with the FP64 oracle to ~1e-14 relative L1.
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(target: str = LIB) -> bool:
+    if not os.path.exists(target):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(target)
     deps = [os.path.join(SRC, f) for f in SOURCES + SOURCES_F32 + HEADERS] + [os.path.join(ROOT, "include", "mhd.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
@@ -35,10 +35,15 @@ def _compile(nvcc, src, obj, extra):
     return subprocess.Popen(cmd), cmd
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the translation units in parallel and link libmhd.so."""
-    if not force and not _stale():
-        return LIB
+LIB_CHECK = os.path.join(OUT_DIR, "libmhd_check.so")
+
+
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Compile the translation units in parallel and link libmhd.so (check=True: the index-checked
+    libmhd_check.so, compiled with -DMHD_CHECK)."""
+    target = LIB_CHECK if check else LIB
+    if not force and not _stale(target):
+        return target
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = os.environ.get("NVCC", "nvcc")
     tag = f".{os.getpid()}"
@@ -49,6 +54,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         # ulp, far inside its 1e-4 target); its FP64 parts (chemistry, CFL) are unaffected.
         extra = (["--fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
                  if f in SOURCES_F32 else ["--fmad=true"])
+        if check:
+            extra = extra + ["-DMHD_CHECK"]
+            obj = obj[:-2] + ".check.o"
         p, cmd = _compile(nvcc, os.path.join(SRC, f), obj, extra)
         if verbose:
             print(" ".join(cmd))
@@ -57,15 +65,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for p, cmd in jobs:
         if p.wait() != 0:
             raise subprocess.CalledProcessError(p.returncode, cmd)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = target + f".tmp{os.getpid()}"
     link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcufft"]
     if verbose:
         print(" ".join(link))
     subprocess.run(link, check=True)
     for o in objs:
         os.remove(o)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

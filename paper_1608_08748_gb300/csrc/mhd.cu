@@ -35,6 +35,8 @@ int fail(int code, const std::string& msg) {
 }  // namespace
 
 namespace mhd_rt {
+unsigned check_flags_f32(bool clear);      // mhd_f32.cu
+unsigned check_flags_gravity(bool clear);  // mhd_gravity.cu
 // record the message mhd_last_error() returns on this thread; returns code
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
 // the code of the last failure recorded on this thread (for calls that return a pointer)
@@ -42,22 +44,6 @@ int last_error_code() { return g_err_code; }
 }  // namespace mhd_rt
 
 namespace {
-
-// the helpers of the FP64 path on an array of doubles (mhd_selftest_helpers)
-__global__ void k_selftest_helpers(const double* __restrict__ x, int n, double* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double v = x[i], a = fabs(v);
-  double* o = out + 8 * (size_t)i;
-  o[0] = abs_b(v);
-  o[1] = neg_b(v);
-  o[2] = scale_down_b<1>(v);
-  o[3] = scale_down_b<2>(v);
-  o[4] = __longlong_as_double(okey(v));
-  o[5] = rcp_nr(v);
-  o[6] = rsqrt_nr(a);
-  o[7] = sqrt_nr(a);
-}
 
 size_t pool_size(const Geom& g, int precision, int chem) {
   (void)chem;
@@ -691,13 +677,16 @@ int mhd_get_potential(mhd_sim* S, double* out) {
   return grav_copy(S, out);
 }
 
-int mhd_selftest_helpers(const double* x, int n, double* out) {
-  if (n < 0 || (n > 0 && (!x || !out))) return fail(MHD_EINVAL, "mhd_selftest_helpers: bad argument");
-  if (n == 0) return MHD_OK;
-  k_selftest_helpers<<<(n + 255) / 256, 256>>>(x, n, out);
-  CK(cudaGetLastError());
+int mhd_check_flags(int clear, unsigned* flags) {
+  if (!flags || (clear != 0 && clear != 1)) return fail(MHD_EINVAL, "mhd_check_flags: need flags and clear in {0, 1}");
+#ifdef MHD_CHECK
   CK(cudaDeviceSynchronize());
+  *flags = check_flags_of_this_unit(clear != 0) | check_flags_f32(clear != 0) | check_flags_gravity(clear != 0);
   return MHD_OK;
+#else
+  *flags = 0;
+  return fail(MHD_EINVAL, "mhd_check_flags: this library was built without index checks");
+#endif
 }
 
 int mhd_launches_per_step(mhd_sim* S) {

@@ -76,11 +76,33 @@ __device__ __forceinline__ int wrap(int i, int n, int bc) {
 // Cell, face and lattice indices are 32-bit: mhd_create rejects grids whose (n+1)^3 lattice does
 // not fit (512^3 needs 1.35e8).
 typedef int idx_t;
+
+// Index-checked build (compiled with -DMHD_CHECK; build.build(check=True) makes libmhd_check.so):
+// every computed cell index is tested against the cells [0, N) and every face or lattice index
+// against [0, NF); a bad one sets a bit of this translation unit's flag word (1: cell, 2: lattice)
+// and is replaced by 0, so that the access stays inside its array.  mhd_check_flags reads the
+// words.  The plain build compiles the checks away.
+#ifdef MHD_CHECK
+static __device__ unsigned int g_check_flags;
+__device__ __forceinline__ idx_t checked_index(idx_t i, long long n, unsigned bit) {
+  if (i < 0 || (long long)i >= n) {
+    atomicOr(&g_check_flags, bit);
+    return 0;
+  }
+  return i;
+}
+#define MHD_CELL(g, i) ::mhd::checked_index((i), (g).N, 1u)
+#define MHD_LATTICE(g, i) ::mhd::checked_index((i), (g).NF, 2u)
+#else
+#define MHD_CELL(g, i) (i)
+#define MHD_LATTICE(g, i) (i)
+#endif
+
 __device__ __forceinline__ idx_t cidx(const Geom& g, int i, int j, int k) {
-  return (k * g.n[1] + j) * g.n[0] + i;
+  return MHD_CELL(g, (k * g.n[1] + j) * g.n[0] + i);
 }
 __device__ __forceinline__ idx_t fidx(const Geom& g, int i, int j, int k) {
-  return (k * (g.n[1] + 1) + j) * (g.n[0] + 1) + i;
+  return MHD_LATTICE(g, (k * (g.n[1] + 1) + j) * (g.n[0] + 1) + i);
 }
 // cell index of (c[0], c[1], c[2]) after the boundary map on each axis
 __device__ __forceinline__ idx_t cmap(const Geom& g, int c0, int c1, int c2) {

@@ -6,6 +6,9 @@
 #include "mhd_runtime.cuh"
 
 namespace mhd_rt {
+// index-check flags of the FP32-bulk kernels (MHD_CHECK builds)
+unsigned check_flags_f32(bool clear) { return check_flags_of_this_unit(clear); }
+
 template cudaError_t prepare_kernels<float>();
 template void launch_euler_stage<float>(Exec<float>&, cudaStream_t);
 template void launch_lag_stage<float>(Exec<float>&, cudaStream_t);

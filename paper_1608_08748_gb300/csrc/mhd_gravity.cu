@@ -12,6 +12,11 @@
 
 #include "mhd_runtime.cuh"
 
+namespace mhd_rt {
+// index-check flags of the Poisson-solve kernels (MHD_CHECK builds)
+unsigned check_flags_gravity(bool clear) { return check_flags_of_this_unit(clear); }
+}  // namespace mhd_rt
+
 using namespace mhd;
 using namespace mhd_rt;
 

@@ -202,7 +202,7 @@ __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
   const idx_t base = cidx(g, c0[0], c0[1], c0[2]);
   const idx_t stride = D == 0 ? 1 : (D == 1 ? g.n[0] : g.n[0] * g.n[1]);
   auto cell_at = [&](int i) -> idx_t {
-    if (inside) return base + i * stride;
+    if (inside) return MHD_CELL(g, base + i * stride);
     int cc[3] = {c[0], c[1], c[2]};
     cc[D] = i;
     return cmap(g, cc[0], cc[1], cc[2]);
@@ -229,30 +229,50 @@ __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
     gl = B.w.g[q];
     sl = B.w.sr[q];
   }
+  // the loads of a face are issued one face ahead, so that their latency overlaps the previous
+  // face's Riemann solve: the new stencil cell i + 2 and the right cell i (density, gamma,
+  // sqrt(rho), face field)
+  T nq[6], nr, ng, ns, nb;
+  {
+    const idx_t qn = cell_at(f0 + 2), cr = cell_at(f0);
+#pragma unroll
+    for (int v = 0; v < 6; ++v) nq[v] = qv[v][qn];
+    nr = B.s.rho[cr];
+    ng = B.w.g[cr];
+    ns = B.w.sr[cr];
+    nb = B.s.b[D][cr];
+  }
 #pragma unroll 1
   for (int k = 0; k < PENCIL; ++k) {
     if (k < nfp) {
       const int i = f0 + k;
       // the left cell's p, B_t1, B_t2 are the centre of the window before it slides
       const T pL = w[5][2], b1L = w[3][2], b2L = w[4][2];
-      const idx_t qn = cell_at(i + 2);
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
         w[v][0] = w[v][1];
         w[v][1] = w[v][2];
         w[v][2] = w[v][3];
         w[v][3] = w[v][4];
-        w[v][4] = qv[v][qn];
-        pr[v] = ppm_direct(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4]);  // cell i
+        w[v][4] = nq[v];
       }
-      const idx_t cr = cell_at(i);
-      const T rr = B.s.rho[cr], gr = B.w.g[cr], sr = B.w.sr[cr];
+      const T rr = nr, gr = ng, sr = ns, Bn = nb;
+      if (k + 1 < nfp) {
+        const idx_t qn = cell_at(i + 3), cr = cell_at(i + 1);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) nq[v] = qv[v][qn];
+        nr = B.s.rho[cr];
+        ng = B.w.g[cr];
+        ns = B.w.sr[cr];
+        nb = B.s.b[D][cr];
+      }
+#pragma unroll
+      for (int v = 0; v < 6; ++v) pr[v] = ppm_direct(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4]);  // cell i
       const T wl[6] = {rl, pL, gl, b1L, b2L, sl};
       const T wr[6] = {rr, w[5][2], gr, w[3][2], w[4][2], sr};
-      const T Bn = B.s.b[D][cr];
       T qs[6];
       riemann(wl, wr, Bn, pl, pr, tau_h, qs);
-      store_face_fluxes(B.fo[D], fbase + k * fstride, Bn, qs);
+      store_face_fluxes(B.fo[D], MHD_LATTICE(g, fbase + k * fstride), Bn, qs);
 #pragma unroll
       for (int v = 0; v < 6; ++v) pl[v] = pr[v];
       rl = rr;
@@ -482,7 +502,7 @@ __device__ __forceinline__ void lag_face(const Box<T>& B, idx_t t) {
     const idx_t stride = D == 0 ? 1 : (D == 1 ? g.n[0] : g.n[0] * g.n[1]);
     const idx_t cc = cidx(g, c[0], c[1], c[2]);
 #pragma unroll
-    for (int o = 0; o < 6; ++o) cell[o] = cc + (o - 3) * stride;
+    for (int o = 0; o < 6; ++o) cell[o] = MHD_CELL(g, cc + (o - 3) * stride);
   } else {
 #pragma unroll
     for (int o = 0; o < 6; ++o) {
@@ -602,7 +622,7 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
         const T E = left ? Pl.R : Pr.L;
         const T d = left ? Pl.d : Pr.d;
         const T q6 = left ? neg_b(Pl.q6) : Pr.q6;
-        out[k * fstride] = vn[k] * (E + shy[k] * (d + q6 * w[k]));
+        out[MHD_LATTICE(g, fbase + k * fstride) - fbase] = vn[k] * (E + shy[k] * (d + q6 * w[k]));
         Pl = Pr;
       }
     }

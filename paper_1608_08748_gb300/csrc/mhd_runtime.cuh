@@ -4,6 +4,7 @@
 // and sum rounded as written); the FP32-bulk instances in mhd_f32.cu (contraction allowed).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only; ranges cost nothing unless a profiler is attached
 
 #include <vector>
 
@@ -14,6 +15,35 @@ namespace mhd_rt {
 using namespace mhd;
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// The index-check flags of the translation unit that includes this header (MHD_CHECK builds; 0
+// otherwise), read and optionally cleared.  Each translation unit has its own device word.
+static inline unsigned check_flags_of_this_unit(bool clear) {
+#ifdef MHD_CHECK
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, ::mhd::g_check_flags, sizeof(v)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (clear) {
+    const unsigned z = 0;
+    cudaMemcpyToSymbol(::mhd::g_check_flags, &z, sizeof(z));
+  }
+  return v;
+#else
+  (void)clear;
+  return 0;
+#endif
+}
+
+// An NVTX range around the enqueueing of one stage of the step, so that a profiler can attribute
+// and filter the kernels by the paper's stages (ncu --nvtx --nvtx-include "Lagrangian stage/").
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // kernel classes with their own launch shape
 enum KClass { KC_PRIM = 0, KC_EFACE, KC_EDGES, KC_EUPD, KC_LFACE, KC_LUPD, KC_POST, NKC };
@@ -295,6 +325,7 @@ void launch_sweeps(Exec<T>& X, cudaStream_t st, F sw) {
 
 template <typename T>
 void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
+  NvtxRange range("Eulerian stage with Flux-CT (Sec. 2.4, 2.5)");
   // self-gravity: a box with a potential (such sims step alone, never in a batch)
   const bool grav = X.nb == 1 && X.h[0].phi != nullptr;
   for (int r = 0; r < 3; ++r) {
@@ -317,6 +348,7 @@ void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
 
 template <typename T>
 void launch_lag_stage(Exec<T>& X, cudaStream_t st) {
+  NvtxRange range("Lagrangian stage (Sec. 2.6)");
   for (int r = 0; r < 3; ++r) {
     launch_sweeps(X, st, [&](int d, cudaStream_t s) {
       if constexpr (lag_in_pencils<T>()) {
@@ -354,6 +386,7 @@ void launch_lag_stage(Exec<T>& X, cudaStream_t st) {
 // new state (cell_stages = do_reg = check = 0: only the CFL denominator)
 template <typename T>
 void launch_post(Exec<T>& X, cudaStream_t st, int cell_stages, int do_reg, int check) {
+  NvtxRange range("chemistry, heating/cooling, regularisation, CFL (Sec. 2.7-2.9, 2.3)");
   if (X.ions)
     launch_k(X, st, KC_POST, DOM_CELLS, kb_post<T, true>, cell_stages, do_reg, check);
   else
@@ -362,6 +395,7 @@ void launch_post(Exec<T>& X, cudaStream_t st, int cell_stages, int do_reg, int c
 
 template <typename T>
 void launch_step(Exec<T>& X, cudaStream_t st) {
+  NvtxRange range("mhd step");
   launch_small(X, st, 0);
   launch_euler_stage(X, st);
   launch_lag_stage(X, st);

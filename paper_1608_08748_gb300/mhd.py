@@ -88,7 +88,6 @@ def lib():
         L.mhd_launches_per_step.argtypes = [vp]
         L.mhd_get_potential.argtypes = [vp, vp]
         L.mhd_set_ions.argtypes = [vp, vp, i]
-        L.mhd_selftest_helpers.argtypes = [vp, i, vp]
         L.mhd_probe_fma_peak.argtypes = [i, i, C.POINTER(d)]
         L.mhd_get_ions.argtypes = [vp, vp, i]
         L.mhd_batch_create.restype = vp
@@ -274,16 +273,6 @@ def bytes_needed(nx, ny, nz, precision=0, chem=1):
     return lib().mhd_bytes_needed(nx, ny, nz, precision, chem)
 
 
-def selftest_helpers(x):
-    """Device self-test of the FP64 arithmetic helpers (mhd_selftest_helpers): an (n, 8) float64
-    array of |x|, -x, x/2, x/4, the ordered key of x (its bits), 1/x, 1/sqrt|x|, sqrt|x|."""
-    import torch
-    xd = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64).ravel()).cuda()
-    out = torch.empty((xd.numel(), 8), dtype=torch.float64, device=xd.device)
-    _check(lib().mhd_selftest_helpers(xd.data_ptr(), xd.numel(), out.data_ptr()))
-    return out.cpu().numpy()
-
-
 def probe_fma_peak(fp64=True, iters=None):
     """Measured FMA peak of the current GPU in TFLOP/s (mhd_probe_fma_peak), FP64 or FP32."""
     if iters is None:
@@ -291,6 +280,21 @@ def probe_fma_peak(fp64=True, iters=None):
     out = C.c_double(0.0)
     _check(lib().mhd_probe_fma_peak(int(bool(fp64)), int(iters), C.byref(out)))
     return out.value
+
+
+def log_steps(sim, cfl, steps, path):
+    """Advance `sim` by `steps` steps, appending one JSON line per step to `path`: the step number,
+    t, tau, the FP64 sums (rho, m, rho E, b), max |div b| h, the cumulative velocity-branch count of
+    the regularisation and the error flags (mhd_diagnostics after each step, which synchronises)."""
+    import json
+    with open(path, "a") as f:
+        for _ in range(steps):
+            tau = sim.step(cfl)
+            d = sim.diagnostics()
+            rec = {"step": int(d["steps"]), "t": d["t"], "tau": tau}
+            rec.update({k: d[k] for k in ["rho", "mx", "my", "mz", "E", "bx", "by", "bz", "max_div_b_h"]})
+            rec.update(vel_branch=int(d["vel_branch"]), error_flags=int(d["error_flags"]))
+            f.write(json.dumps(rec) + "\n")
 
 
 def from_ic(ic, **options):

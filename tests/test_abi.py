@@ -74,10 +74,6 @@ def test_argument_errors_are_reported_without_a_device(libmhd):
     assert libmhd.mhd_batch_create(None, 0) is None and "mhd_batch_create" in err()
     libmhd.mhd_server_set_policy.argtypes = [vp, i]
     assert libmhd.mhd_server_set_policy(None, 0) == EINVAL and "mhd_server_set_policy" in err()
-    libmhd.mhd_selftest_helpers.argtypes = [vp, i, vp]
-    assert libmhd.mhd_selftest_helpers(None, 5, None) == EINVAL and "mhd_selftest_helpers" in err()
-    assert libmhd.mhd_selftest_helpers(None, -1, None) == EINVAL
-    assert libmhd.mhd_selftest_helpers(None, 0, None) == 0  # nothing to do, no launch
 
 
 def test_binding_option_keys_match_the_header():

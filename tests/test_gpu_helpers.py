@@ -12,15 +12,40 @@ pytestmark = pytest.mark.gpu
 TINY = np.finfo(np.float64).tiny  # smallest normal double
 
 
+class _Selftest:
+    """The helpers run over an array on the device: an (n, 8) float64 array of |x|, -x, x/2, x/4,
+    the ordered key of x (its bits), 1/x, 1/sqrt|x|, sqrt|x| (tests/gpu_selftest/helpers_selftest.cu,
+    built here with nvcc for sm_103a; not part of libmhd.so)."""
+
+    def __init__(self, path):
+        import ctypes
+        self.L = ctypes.CDLL(path)
+        self.L.selftest_helpers.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+
+    def selftest_helpers(self, x):
+        import torch
+        xd = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64).ravel()).cuda()
+        out = torch.empty((xd.numel(), 8), dtype=torch.float64, device=xd.device)
+        rc = self.L.selftest_helpers(xd.data_ptr(), xd.numel(), out.data_ptr())
+        assert rc == 0, rc
+        return out.cpu().numpy()
+
+
 @pytest.fixture(scope="module")
-def M():
+def M(tmp_path_factory):
+    import os
+    import subprocess
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_1608_08748_gb300 import build as B
-    B.build()
-    import paper_1608_08748_gb300 as M
-    return M
+    here = os.path.dirname(os.path.abspath(__file__))
+    root = os.path.dirname(here)
+    lib = str(tmp_path_factory.mktemp("selftest") / "libhelpers_selftest.so")
+    subprocess.run([os.environ.get("NVCC", "nvcc"), "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                    "-std=c++17", "--fmad=true", "-Xcompiler", "-fPIC", "-shared",
+                    "-I", os.path.join(root, "paper_1608_08748_gb300", "csrc"), "-I", os.path.join(root, "include"),
+                    os.path.join(here, "gpu_selftest", "helpers_selftest.cu"), "-o", lib], check=True)
+    return _Selftest(lib)
 
 
 def inputs():

@@ -103,3 +103,18 @@ def test_page_locked_host_buffers_equal_pageable(M, precision):
     want = a.get_state()
     for k in ["rho", "mom", "E", "B", "rho_h2"]:
         assert np.array_equal(np.asarray(got[k]), want[k]), k
+
+
+def test_per_step_log(M, tmp_path):
+    """log_steps writes one JSON line per step with t, tau, the FP64 sums, max |div b| h, the
+    velocity-branch count and the error flags; mass is conserved to rounding along the log."""
+    import json
+    ic = I.turbulence(8, mach=2.0, seed=67, shape=(8, 10, 12))
+    s = M.from_ic(ic)
+    path = tmp_path / "steps.jsonl"
+    M.log_steps(s, 0.4, 3, str(path))
+    recs = [json.loads(x) for x in path.read_text().splitlines()]
+    assert [r["step"] for r in recs] == [1, 2, 3]
+    assert all(r["tau"] > 0 and r["error_flags"] == 0 for r in recs)
+    assert recs[0]["t"] < recs[1]["t"] < recs[2]["t"]
+    assert abs(recs[2]["rho"] - recs[0]["rho"]) <= 1e-12 * recs[0]["rho"]
