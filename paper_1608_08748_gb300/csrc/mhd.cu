@@ -243,6 +243,7 @@ size_t mhd_bytes_needed(int nx, int ny, int nz, int precision, int chem) {
   g.n[2] = nz;
   g.N = (long long)nx * ny * nz;
   g.NF = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+  set_divisors(g);
   return pool_size(g, precision, chem) + (size_t)g.N * 10 * 8 + sizeof(Scalars) +
          ((size_t)g.N / 256 + 2) * 9 * 8;
 }
@@ -267,6 +268,7 @@ mhd_sim* mhd_create(int nx, int ny, int nz, double gamma, double dx) {
   S->g.bc[0] = S->g.bc[1] = S->g.bc[2] = 0;
   S->g.N = (long long)nx * ny * nz;
   S->g.NF = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+  set_divisors(S->g);
   S->ph.gamma = gamma;
   S->ph.dx = dx;
   S->ph.ih = 1.0 / dx;

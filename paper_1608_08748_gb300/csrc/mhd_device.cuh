@@ -20,12 +20,38 @@ namespace mhd {
 
 // ------------------------------------------------------------------------------------------------
 // Geometry and parameters (passed by value to every kernel)
+// Division of a non-negative 32-bit index by an invariant divisor d >= 1 with a multiply-high, two
+// shifts and two additions instead of the integer division's dozen-odd instructions (the
+// round-up method with an add indicator of Granlund & Montgomery, 1994): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1 (below 2^32), and for every t < 2^32 the quotient is
+// (hi + ((t - hi) >> min(l, 1))) >> max(l - 1, 0) with hi = floor(m t / 2^32).
+struct FastDiv {
+  unsigned d, m;
+  int s1, s2;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  const unsigned long long m = (((1ull << 32) * ((1ull << l) - d)) / d) + 1;
+  return FastDiv{d, (unsigned)m, l < 1 ? l : 1, l > 1 ? l - 1 : 0};
+}
+
 struct Geom {
   int n[3];          // cells per axis
   int bc[3];         // 0 periodic, 1 outflow (zero-gradient)
   long long N;       // cells
   long long NF;      // (nx+1)(ny+1)(nz+1): size of face / edge scratch arrays
+  FastDiv dn[2];     // division by n_x, n_y (cell indices)
+  FastDiv dn1[2];    // division by n_x + 1, n_y + 1 (face and lattice indices)
 };
+
+// the divisors of a grid of nx x ny x nz cells
+inline void set_divisors(Geom& g) {
+  for (int d = 0; d < 2; ++d) {
+    g.dn[d] = make_fastdiv((unsigned)g.n[d]);
+    g.dn1[d] = make_fastdiv((unsigned)g.n[d] + 1u);
+  }
+}
 
 struct Phys {
   double gamma;      // scalar adiabatic index (chemistry off)
@@ -293,7 +319,16 @@ __device__ __forceinline__ double rsqrt_seed(double x) {
   return r;
 }
 
+// high 32 bits of the 64-bit product (the fast index divisions)
+__device__ __forceinline__ unsigned umulhi32(unsigned a, unsigned b) { return __umulhi(a, b); }
+
 // ---- end inline-PTX helpers ----
+
+// t / f.d for t < 2^32 (FastDiv)
+__device__ __forceinline__ unsigned fdiv(unsigned t, const FastDiv& f) {
+  const unsigned hi = umulhi32(f.m, t);
+  return (hi + ((t - hi) >> f.s1)) >> f.s2;
+}
 
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }

@@ -57,11 +57,16 @@ struct Tiles {
 enum { DOM_CELLS = 0, DOM_FACE_X = 1, DOM_FACE_Y = 2, DOM_FACE_Z = 3, DOM_LATTICE = 4,
        DOM_PENCIL_X = 5, DOM_PENCIL_Y = 6, DOM_PENCIL_Z = 7, NDOM = 8 };
 
-// Eulerian faces are solved in pencils of PENCIL consecutive faces along the sweep direction: the
-// thread carries the parabolas of the left cell from one face to the next, so every cell's
-// parabolas are built once per direction (plus one extra cell per pencil).
-constexpr int PENCIL = 8;
-__host__ __device__ __forceinline__ int pencil_segments(int n) { return (n + 1 + PENCIL - 1) / PENCIL; }
+// Faces are solved in pencils of pencil_len<T>() consecutive faces along the sweep direction: the
+// thread carries the parabolas (or the stencil) of the left cell from one face to the next, so
+// every cell's parabolas are built once per direction (plus one extra cell per pencil).  Measured
+// on the 256^3 FP32 and 128^3 FP64 steps: 12 faces for the float pencils (Eulerian faces 7.10 ms
+// against 7.40 with 8 and 7.15 with 16), 8 for the double ones (16.6 ms against 17.0 with 12 and
+// 17.6 with 16; their register files hold the stream of each face).
+template <typename T>
+__host__ __device__ constexpr int pencil_len() { return sizeof(T) == 4 ? 12 : 8; }
+template <typename T>
+__host__ __device__ __forceinline__ int pencil_segments(int n) { return (n + 1 + pencil_len<T>() - 1) / pencil_len<T>(); }
 
 // decode a cell index / a face index of direction D / a lattice index
 __device__ __forceinline__ void decode(idx_t t, int e0, int e1, int c[3]) {
@@ -69,6 +74,26 @@ __device__ __forceinline__ void decode(idx_t t, int e0, int e1, int c[3]) {
   idx_t r = t / e0;
   c[1] = (int)(r % e1);
   c[2] = (int)(r / e1);
+}
+// the same with the grid's precomputed divisors (t >= 0): a cell index (cells), a face index of
+// direction D (D = 0, 1, 2) or a lattice index (D = 3)
+template <int D>
+__device__ __forceinline__ void decode_fast(const Geom& g, idx_t t, int c[3]) {
+  const FastDiv f0 = D == 0 || D == 3 ? g.dn1[0] : g.dn[0];
+  const FastDiv f1 = D == 1 || D == 3 ? g.dn1[1] : g.dn[1];
+  const unsigned r = fdiv((unsigned)t, f0);
+  c[0] = (int)((unsigned)t - r * f0.d);
+  const unsigned q = fdiv(r, f1);
+  c[1] = (int)(r - q * f1.d);
+  c[2] = (int)q;
+}
+// a cell index with the precomputed divisors of n_x and n_y
+__device__ __forceinline__ void decode_cell(const Geom& g, idx_t t, int c[3]) {
+  const unsigned r = fdiv((unsigned)t, g.dn[0]);
+  c[0] = (int)((unsigned)t - r * g.dn[0].d);
+  const unsigned q = fdiv(r, g.dn[1]);
+  c[1] = (int)(r - q * g.dn[1].d);
+  c[2] = (int)q;
 }
 
 // pencil p of direction D -> (segment along D, the other two indices) in c.  In the FP64 x sweep
@@ -96,7 +121,7 @@ template <typename T, bool IONS>
 __device__ __forceinline__ void prim_cell(const Box<T>& B, idx_t c) {
   const Geom& g = B.g;
   int q[3];
-  decode(c, g.n[0], g.n[1], q);
+  decode_cell(g, c, q);
   T rho = B.s.rho[c];
   idx_t up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
 #pragma unroll
@@ -190,11 +215,11 @@ __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
   const Geom& g = B.g;
   int ext[3] = {g.n[0], g.n[1], g.n[2]};
   const int n = g.n[D], nf = n + 1;
-  ext[D] = pencil_segments(n);
+  ext[D] = pencil_segments<T>(n);
   int c[3];
   decode_pencil<T, D>(p, ext, c);
-  const int f0 = c[D] * PENCIL;
-  const int nfp = (f0 + PENCIL < nf ? f0 + PENCIL : nf) - f0;
+  const int f0 = c[D] * pencil_len<T>();
+  const int nfp = (f0 + pencil_len<T>() < nf ? f0 + pencil_len<T>() : nf) - f0;
   const T tau_h = (T)B.sc->tau_h;
   const bool inside = f0 >= 3 && f0 + nfp + 2 <= n;
   int c0[3] = {c[0], c[1], c[2]};
@@ -243,7 +268,7 @@ __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
     nb = B.s.b[D][cr];
   }
 #pragma unroll 1
-  for (int k = 0; k < PENCIL; ++k) {
+  for (int k = 0; k < pencil_len<T>(); ++k) {
     if (k < nfp) {
       const int i = f0 + k;
       // the left cell's p, B_t1, B_t2 are the centre of the window before it slides
@@ -283,7 +308,7 @@ __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
 }
 
 // Eulerian faces of direction D (Sec. 2.4): the face i_D - 1/2 lies between cells i_D - 1 and i_D.
-// One thread takes the faces i_D in [s PENCIL, min((s+1) PENCIL, n_D + 1)) of one pencil s (the
+// One thread takes the faces i_D in [s P, min((s+1) P, n_D + 1)), P = pencil_len<T>(), of one pencil s (the
 // other two indices in [0, n)); each cell's parabolas are built once and serve both its faces.
 // Per face: the PPM parabolas of (v_n, v_t1, v_t2, B_t1, B_t2, p) of the two cells, the Riemann
 // solve, and the non-advective fluxes with the two EMF contributions E = B x U (Sec. 2.5).  The
@@ -298,11 +323,11 @@ __device__ __forceinline__ void euler_pencil(const Box<T>& B, idx_t p) {
   const Geom& g = B.g;
   int ext[3] = {g.n[0], g.n[1], g.n[2]};
   const int nf = g.n[D] + 1;
-  ext[D] = pencil_segments(g.n[D]);
+  ext[D] = pencil_segments<T>(g.n[D]);
   int c[3];
   decode_pencil<T, D>(p, ext, c);
-  const int f0 = c[D] * PENCIL;
-  const int f1 = f0 + PENCIL < nf ? f0 + PENCIL : nf;
+  const int f0 = c[D] * pencil_len<T>();
+  const int f1 = f0 + pencil_len<T>() < nf ? f0 + pencil_len<T>() : nf;
   const T tau_h = (T)B.sc->tau_h;
   const T* qv[6] = {B.w.v[D], B.w.v[D1], B.w.v[D2], B.w.B[D1], B.w.B[D2], B.w.p};
   auto cell_at = [&](int i) {
@@ -362,9 +387,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) kb_euler_pencil(c
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
     idx_t p = tl.start[t_] + (idx_t)threadIdx.x;
-    idx_t total = (idx_t)(D == 0 ? pencil_segments(B.g.n[0]) : B.g.n[0]) *
-                      (D == 1 ? pencil_segments(B.g.n[1]) : B.g.n[1]) *
-                      (D == 2 ? pencil_segments(B.g.n[2]) : B.g.n[2]);
+    idx_t total = (idx_t)(D == 0 ? pencil_segments<T>(B.g.n[0]) : B.g.n[0]) *
+                      (D == 1 ? pencil_segments<T>(B.g.n[1]) : B.g.n[1]) *
+                      (D == 2 ? pencil_segments<T>(B.g.n[2]) : B.g.n[2]);
     if (p < total) euler_pencil<T, D>(B, p);
   }
 }
@@ -376,7 +401,7 @@ template <typename T>
 __device__ __forceinline__ void edges_point(const Box<T>& B, idx_t t) {
   const Geom& g = B.g;
   int c[3];
-  decode(t, g.n[0] + 1, g.n[1] + 1, c);
+  decode_fast<3>(g, t, c);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
@@ -429,7 +454,7 @@ template <typename T, bool GRAV>
 __device__ __forceinline__ void euler_update_cell(const Box<T>& B, idx_t c, int r) {
   const Geom& g = B.g;
   int q[3];
-  decode(c, g.n[0], g.n[1], q);
+  decode_cell(g, c, q);
   const T a = (T)RK3_A(r), bb = (T)RK3_B(r), gth = rk_gth(B, r);
   idx_t f0 = fidx(g, q[0], q[1], q[2]);
   idx_t fup[3] = {fidx(g, q[0] + 1, q[1], q[2]), fidx(g, q[0], q[1] + 1, q[2]), fidx(g, q[0], q[1], q[2] + 1)};
@@ -491,10 +516,8 @@ __global__ void __launch_bounds__(512) kb_euler_update(const Box<T>* __restrict_
 template <typename T, int D, bool IONS>
 __device__ __forceinline__ void lag_face(const Box<T>& B, idx_t t) {
   const Geom& g = B.g;
-  int ext[3] = {g.n[0], g.n[1], g.n[2]};
-  ext[D] += 1;
   int c[3];
-  decode(t, ext[0], ext[1], c);
+  decode_fast<D>(g, t, c);
   const T tau_h = (T)B.sc->tau_h;
   idx_t cell[6];
   if (c[D] >= 3 && c[D] + 2 < g.n[D]) {
@@ -550,7 +573,7 @@ __global__ void __launch_bounds__(256) kb_lag_face(const Box<T>* __restrict__ bo
   }
 }
 
-// The same fluxes for the faces i_D - 1/2, i_D in [s PENCIL, min((s+1) PENCIL, n_D + 1)), of one
+// The same fluxes for the faces i_D - 1/2, i_D in [s P, min((s+1) P, n_D + 1)), of one
 // pencil s: the face velocities first, then field by field the parabolas of the pencil's cells in
 // one PPMStream along D, each face taking the average of its upwind cell.
 template <typename T, int D, bool IONS>
@@ -558,11 +581,11 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
   const Geom& g = B.g;
   int ext[3] = {g.n[0], g.n[1], g.n[2]};
   const int nf = g.n[D] + 1;
-  ext[D] = pencil_segments(g.n[D]);
+  ext[D] = pencil_segments<T>(g.n[D]);
   int c[3];
   decode_pencil<T, D>(p, ext, c);
-  const int f0 = c[D] * PENCIL;
-  const int nfp = (f0 + PENCIL < nf ? f0 + PENCIL : nf) - f0;
+  const int f0 = c[D] * pencil_len<T>();
+  const int nfp = (f0 + pencil_len<T>() < nf ? f0 + pencil_len<T>() : nf) - f0;
   const T tau_h = (T)B.sc->tau_h;
   const T TWO_THIRDS = T(2.0 / 3.0);
   auto cell_at = [&](int i) {
@@ -577,7 +600,7 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
   // per face: v_n, and the average over the upwind fraction y = |v_n| tau / h written as
   // E + shy (d + sgn q6 w) with E = q^R of the left cell (v_n >= 0, sgn = -1) or q^L of the right
   // cell (sgn = +1), shy = sgn y / 2 and w = 1 - 2y/3 (the two forms of Sec. 2.4)
-  T vn[PENCIL], shy[PENCIL], w[PENCIL];
+  T vn[pencil_len<T>()], shy[pencil_len<T>()], w[pencil_len<T>()];
   // v_n = (v_l sqrt(rho_l) + v_r sqrt(rho_r)) / (sqrt(rho_l) + sqrt(rho_r)) from the per-cell
   // m / sqrt(rho) and rho / sqrt(rho) = sqrt(rho), each formed once and carried to the next face
   T al, bl;
@@ -588,7 +611,7 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
     bl = r0 * is0;
   }
 #pragma unroll
-  for (int k = 0; k < PENCIL; ++k) {
+  for (int k = 0; k < pencil_len<T>(); ++k) {
     vn[k] = T(0);
     shy[k] = T(0);
     w[k] = T(1);
@@ -615,7 +638,7 @@ __device__ __forceinline__ void lag_pencil(const Box<T>& B, idx_t p) {
     S.prime(a[cell_at(f0 - 3)], a[cell_at(f0 - 2)], a[cell_at(f0 - 1)], a[cell_at(f0)]);
     Para<T> Pl = S.next(a[cell_at(f0 + 1)]);  // cell f0 - 1
 #pragma unroll
-    for (int k = 0; k < PENCIL; ++k) {
+    for (int k = 0; k < pencil_len<T>(); ++k) {
       if (k < nfp) {
         const Para<T> Pr = S.next(a[cell_at(f0 + k + 2)]);  // cell f0 + k
         const bool left = !sign_bit_b(vn[k]);  // v_n = -0: a zero flux either way
@@ -634,9 +657,9 @@ __global__ void __launch_bounds__(256, 1) kb_lag_pencil(const Box<T>* __restrict
   MHD_TILE_LOOP(tl) {
     const Box<T>& B = boxes[tl.box[t_]];
     idx_t p = tl.start[t_] + (idx_t)threadIdx.x;
-    idx_t total = (idx_t)(D == 0 ? pencil_segments(B.g.n[0]) : B.g.n[0]) *
-                      (D == 1 ? pencil_segments(B.g.n[1]) : B.g.n[1]) *
-                      (D == 2 ? pencil_segments(B.g.n[2]) : B.g.n[2]);
+    idx_t total = (idx_t)(D == 0 ? pencil_segments<T>(B.g.n[0]) : B.g.n[0]) *
+                      (D == 1 ? pencil_segments<T>(B.g.n[1]) : B.g.n[1]) *
+                      (D == 2 ? pencil_segments<T>(B.g.n[2]) : B.g.n[2]);
     if (p < total) lag_pencil<T, D, IONS>(B, p);
   }
 }
@@ -646,7 +669,7 @@ template <typename T, bool IONS>
 __device__ __forceinline__ void lag_update_cell(const Box<T>& B, idx_t c, int r) {
   const Geom& g = B.g;
   int q[3];
-  decode(c, g.n[0], g.n[1], q);
+  decode_cell(g, c, q);
   const T a = (T)RK3_A(r), bb = (T)RK3_B(r), gth = rk_gth(B, r);
   idx_t f0 = fidx(g, q[0], q[1], q[2]);
   idx_t fup[3] = {fidx(g, q[0] + 1, q[1], q[2]), fidx(g, q[0], q[1] + 1, q[2]), fidx(g, q[0], q[1], q[2] + 1)};
@@ -694,7 +717,7 @@ __device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, int cell_sta
   const bool ions = IONS && ph.ions;
   const State<T>& s = B.s;
   int q[3];
-  decode(c, g.n[0], g.n[1], q);
+  decode_cell(g, c, q);
   const double tau = B.sc->tau;
   if ((cell_stages & 1) && ph.chem) {
     const ChemOut co = chem_cell<IONS>(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c],

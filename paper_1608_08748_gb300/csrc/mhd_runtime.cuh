@@ -142,9 +142,9 @@ long long domain_size(const Box<T>& B, int dom) {
     case DOM_FACE_X: return (long long)(g.n[0] + 1) * g.n[1] * g.n[2];
     case DOM_FACE_Y: return (long long)g.n[0] * (g.n[1] + 1) * g.n[2];
     case DOM_FACE_Z: return (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
-    case DOM_PENCIL_X: return (long long)pencil_segments(g.n[0]) * g.n[1] * g.n[2];
-    case DOM_PENCIL_Y: return (long long)g.n[0] * pencil_segments(g.n[1]) * g.n[2];
-    case DOM_PENCIL_Z: return (long long)g.n[0] * g.n[1] * pencil_segments(g.n[2]);
+    case DOM_PENCIL_X: return (long long)pencil_segments<T>(g.n[0]) * g.n[1] * g.n[2];
+    case DOM_PENCIL_Y: return (long long)g.n[0] * pencil_segments<T>(g.n[1]) * g.n[2];
+    case DOM_PENCIL_Z: return (long long)g.n[0] * g.n[1] * pencil_segments<T>(g.n[2]);
     default: return g.NF;
   }
 }

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <random>
+#include <vector>
 
 static inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
 static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
@@ -331,6 +332,36 @@ int main() {
       if (e > 1e-13) ++bad;
     }
     report("cfl", n, worst, bad);
+  }
+  // the index decoding's division by an invariant divisor (FastDiv, Granlund-Montgomery) against
+  // the integer division: every divisor up to 4096 and a spread of larger ones, with quotient
+  // boundaries, small and large dividends and random ones up to 2^32 - 1
+  {
+    long n = 0, bad = 0;
+    std::uniform_int_distribution<unsigned> Ut(0u, 0xffffffffu);
+    std::vector<unsigned> divs;
+    for (unsigned d = 1; d <= 4096; ++d) divs.push_back(d);
+    for (int k = 0; k < 2000; ++k) divs.push_back(1u + (unsigned)(g() % 0x7fffffffu));
+    for (unsigned d : {65535u, 65536u, 65537u, 1u << 20, (1u << 31) - 1u, 1u << 31, 0xffffffffu}) divs.push_back(d);
+    for (unsigned d : divs) {
+      const mhd::FastDiv f = mhd::make_fastdiv(d);
+      auto check = [&](unsigned t) {
+        ++n;
+        if (mhd::fdiv(t, f) != t / d) ++bad;
+      };
+      for (unsigned t = 0; t < 300; ++t) check(t);
+      for (unsigned k = 1; k < 40; ++k) {
+        const unsigned long long b = (unsigned long long)k * d;
+        if (b <= 0xffffffffull) {
+          check((unsigned)b);
+          if (b > 0) check((unsigned)(b - 1));
+        }
+      }
+      check(0xffffffffu);
+      check(0x7fffffffu);
+      for (int k = 0; k < 64; ++k) check(Ut(g));
+    }
+    report("fast_index_division", n, 0.0, bad);
   }
   return 0;
 }

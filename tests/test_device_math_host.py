@@ -61,11 +61,12 @@ template <int K> inline double scale_down_b(double x) {
 }
 template <int K> inline float scale_down_b(float x) { return x * (1.0f / (float)(1 << K)); }
 inline double rsqrt_seed(double x) { return seed_(1.0 / std::sqrt(ftz_(x))); }
+inline unsigned umulhi32(unsigned a, unsigned b) { return (unsigned)(((unsigned long long)a * b) >> 32); }
 '''
 
 BOUNDS = {"ppm_lean_close": 0, "ppm_stream_bits": 0, "ppm_fp32": 0, "riemann_fp64": 0, "riemann_fp32": 0,
           "chemistry": 0, "heatcool": 0, "chemistry_ions": 0, "heatcool_ions": 0, "ion_instances_without_ions_same_bits": 0, "cfl": 0,
-          "newton_raphson_ulp": 0}
+          "newton_raphson_ulp": 0, "fast_index_division": 0}
 
 
 def _cuda_include():
