@@ -203,6 +203,17 @@ __device__ __forceinline__ Para<T> ppm_direct(T qm2, T qm1, T qc, T qp1, T qp2) 
   return P;
 }
 
+// 2^(j/32) for j = 0 .. 31, correctly rounded (the table of the exponential exp_tang below)
+__device__ const double kExp2Frac32[32] = {
+    0x1.0000000000000p+0, 0x1.059b0d3158574p+0, 0x1.0b5586cf9890fp+0, 0x1.11301d0125b51p+0,
+    0x1.172b83c7d517bp+0, 0x1.1d4873168b9aap+0, 0x1.2387a6e756238p+0, 0x1.29e9df51fdee1p+0,
+    0x1.306fe0a31b715p+0, 0x1.371a7373aa9cbp+0, 0x1.3dea64c123422p+0, 0x1.44e086061892dp+0,
+    0x1.4bfdad5362a27p+0, 0x1.5342b569d4f82p+0, 0x1.5ab07dd485429p+0, 0x1.6247eb03a5585p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.71f75e8ec5f74p+0, 0x1.7a11473eb0187p+0, 0x1.82589994cce13p+0,
+    0x1.8ace5422aa0dbp+0, 0x1.93737b0cdc5e5p+0, 0x1.9c49182a3f090p+0, 0x1.a5503b23e255dp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b7f76f2fb5e47p+0, 0x1.c199bdd85529cp+0, 0x1.cb720dcef9069p+0,
+    0x1.d5818dcfba487p+0, 0x1.dfc97337b9b5fp+0, 0x1.ea4afa2a490dap+0, 0x1.f50765b6e4540p+0};
+
 // ---- begin inline-PTX helpers ----
 // Sign tests, absolute values, minima and comparisons of doubles on the integer pipes.  On sm_103
 // the FP64 pipe issues two instructions per clock per SM and the integer pipes 64, and the PPM
@@ -322,6 +333,28 @@ __device__ __forceinline__ double rsqrt_seed(double x) {
 // high 32 bits of the 64-bit product (the fast index divisions)
 __device__ __forceinline__ unsigned umulhi32(unsigned a, unsigned b) { return __umulhi(a, b); }
 
+// Device intrinsics, grouped here with the other device-only helpers.  The pieces of exp_tang below
+// that act on bit patterns: the range test of its argument (-707 <= x
+// <= -0 or +0 <= x < 707; NaNs and infinities fail), the low word of a double, 2^m y for y in
+// [0.5, 4) and |m| <= 1020 by an addition to the exponent field, and the table read.
+__device__ __forceinline__ bool exp_fast_range(double x) {
+  const unsigned long long ux = (unsigned long long)__double_as_longlong(x);
+  return ux <= 0xc086180000000000ull && (ux >= 0x8000000000000000ull || ux < 0x4086180000000000ull);
+}
+__device__ __forceinline__ int lo_word(double x) { return __double2loint(x); }
+__device__ __forceinline__ double scale_pow2(double y, int m) {
+  return __hiloint2double(__double2hiint(y) + (int)((unsigned)m << 20), __double2loint(y));
+}
+__device__ __forceinline__ double exp2_frac32(int j) { return __ldg(&kExp2Frac32[j]); }
+
+// FP32 operations rounded to nearest whatever the build's FP32 flags (the CFL screen's error bound
+// assumes them), and +inf
+__device__ __forceinline__ float fsqrt_rn(float x) { return __fsqrt_rn(x); }
+__device__ __forceinline__ float frsqrt_rn(float x) { return __frsqrt_rn(x); }
+__device__ __forceinline__ float fdiv_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fmul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
+
 // ---- end inline-PTX helpers ----
 
 // t / f.d for t < 2^32 (FastDiv)
@@ -361,6 +394,37 @@ __device__ __forceinline__ double rcp_t(double x) { return rcp_nr(x); }
 __device__ __forceinline__ float rcp_t(float x) { return 1.0f / x; }
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt_nr(x); }
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+
+// e^x in FP64 by the table-driven method of P. T. P. Tang (ACM TOMS 15, 144-157, 1989), for the
+// arguments of the H/H2 rates (x <= 0).  With k the integer nearest to 32 x / ln 2, k = 32 m + j
+// (0 <= j < 32) and r = x - k ln2/32 (|r| <= ln2/64), e^x = 2^m 2^(j/32) e^r; e^r - 1 is its
+// Taylor polynomial of degree 6 (the remainder r^7/7! stays below 4e-18), 2^(j/32) comes from a
+// table of correctly rounded doubles, and 2^m is added to the exponent field on the integer pipe.
+// ln2/32 is split in a 36-bit head, whose products with |k| < 2^15 are exact, and a tail.  The
+// result lies within 1.01 ulp of e^x (half an ulp of the table entry, scaled by e^r, and half an ulp
+// of the last rounding); it takes 11 FP64-pipe instructions.  Arguments outside
+// [-707, 707] (where 2^m or the result leaves the normal range), infinities and NaNs take the
+// library exp; the range test runs on the integer pipe.
+
+__device__ __forceinline__ double exp_tang(double x) {
+  if (!exp_fast_range(x)) return exp(x);
+  const double INV_L = 0x1.71547652b82fep+5;                 // 32 / ln 2
+  const double L_HI = 0x1.62e42fefa0000p-6, L_LO = 0x1.cf79abc9e3b3ap-45;  // ln2/32 = L_HI + L_LO
+  const double SHIFTER = 0x1.8p52;                           // adding it rounds to an integer
+  const double t = fma(x, INV_L, SHIFTER);
+  const double kd = t - SHIFTER;
+  const int k = lo_word(t);                                  // k in the low word, two's complement
+  const double r = fma(-kd, L_LO, fma(-kd, L_HI, x));
+  double p = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+  p = fma(r, p, 1.0 / 24.0);
+  p = fma(r, p, 1.0 / 6.0);
+  p = fma(r, p, 0.5);
+  p = fma(r, p, 1.0);
+  p = r * p;                                                 // e^r - 1
+  const double tj = exp2_frac32(k & 31);
+  const double y = fma(tj, p, tj);                           // 2^(j/32) e^r, in [0.98, 2.03)
+  return scale_pow2(y, k >> 5);
+}
 
 // Half the limited slope of Sec. 2.1 Step 1 for a cell with differences dn = q_0 - q_-1,
 // dp = q_1 - q_0 and s = q_1 - q_-1: the slope is min(|s|/2, 2|dp|, 2|dn|) with the sign of s where
@@ -712,6 +776,45 @@ __device__ __forceinline__ double cfl_denominator(double rho, double mx, double 
   return v + ((sB + sgp + Bm) + fs) * irs;
 }
 
+// The screen of the CFL maximum.  tau takes only the largest FP64 denominator over the cells, so a
+// cell whose denominator provably lies below an FP64 denominator already reached by another cell
+// cannot set it and need not be evaluated in FP64: tau stays bit for bit that of evaluating every
+// cell.  The proof is the FP32 estimate below, the same formula from FP32-rounded inputs (square
+// roots and 1/sqrt correctly rounded, sums and products rounded to nearest).  With u = 2^-24 a
+// first-order count of its relative error gives about 30 u: up to 23 u in gamma - 1 (the
+// cancellation in n_H = rho - rho_H2 - rho_H+ stays below 5 u rho, against numerator and
+// denominator of at least rho / 2 and 2 rho), 35 u in gamma p, half of that through the square
+// roots, 1.5 u through 1/sqrt(rho) and its square, a few u of sums.  FP32 squares that flush to
+// zero or lose bits below the normal range move |m| or |B| by less than 2^-62, which is below 2^-22
+// of the denominator (>= sqrt(gamma p / rho)) while rho >= 2^-40 and gamma p >= 2^-40.  The
+// screen allows 2^-12 (4096 u).  A cell outside those guards, or whose estimate overflows, gets
+// +inf and is always evaluated in FP64.
+__device__ __forceinline__ float cfl_estimate_f32(float rho, float mx, float my, float mz, float Bx,
+                                                  float By, float Bz, float eint, float gm1) {
+  const float gp = fmul_rn(fmul_rn(1.0f + gm1, gm1), eint);
+  if (!(rho >= 0x1p-40f) || !(gp >= 0x1p-40f)) return f_inf();
+  const float irs = frsqrt_rn(rho);
+  const float irho = irs * irs;
+  const float sgp = fsqrt_rn(gp);
+  const float B2 = Bx * Bx + By * By + Bz * Bz;
+  const float sB = fsqrt_rn(B2);
+  const float v = fsqrt_rn(mx * mx + my * my + mz * mz) * irho;
+  const float Bm = fmaxf(fabsf(Bx), fmaxf(fabsf(By), fabsf(Bz)));
+  const float fs = fsqrt_rn((gp + B2) + 2.0f * sgp * Bm);
+  return v + ((sB + sgp + Bm) + fs) * irs;
+}
+
+// gamma - 1 of the cell in FP32 for the screen: that of the ideal gas, or of the H/H2 (+ H+, e-)
+// mixture as (2 n_1 + 2 n_H2) / (3 n_1 + 5 n_H2) (gamma_eff below minus one); -1 where the
+// numerator falls below rho / 2 or the denominator below 2 rho (3 rho - rho_H2 / 2 + 3 rho_H+ for
+// physical abundances), which fails the screen's guard.
+__device__ __forceinline__ float gamma_minus_one_f32(bool chem, double gamma, float rho, float rh2, float rhp) {
+  if (!chem) return (float)(gamma - 1.0);
+  const float n1 = (rho - rh2 - rhp) + 2.0f * rhp, nH2 = 0.5f * rh2;
+  const float num = 2.0f * (n1 + nH2), den = 3.0f * n1 + 5.0f * nH2;
+  return (num >= 0.5f * rho && den >= 2.0f * rho) ? fdiv_rn(num, den) : -1.0f;
+}
+
 // Sec. 4.3 effective adiabatic index of the H/H2 mixture (no electrons)
 template <typename T>
 __device__ __forceinline__ T gamma_eff(T rho, T rh2) {
@@ -742,7 +845,8 @@ struct ChemConst {
 //   T = (gamma - 1) rho eps P0 / (n_particles k_B) with gamma - 1 = 2 n_particles / (3 n_1 + 5 n_H2)
 //     = 2 P0 rho eps / ((3 n_1 + 5 n_H2) k_B), n_1 = n_H + n_H+ + n_e, and T, 1/T from one
 //     reciprocal of the product;
-//   1/sqrt(1 + x) from one reciprocal square root; 1/x_norm and 1/b_doppler precomputed.
+//   1/sqrt(1 + x) from one reciprocal square root; 1/x_norm and 1/b_doppler precomputed;
+//   the exponentials of the H/H2 rates by exp_tang (their arguments are <= 0).
 struct ChemOut {
   double rh2, rhp;  // new rho_H2 and rho_H+
 };
@@ -806,16 +910,16 @@ __device__ __forceinline__ ChemOut chem_cell(const Phys& ph, double rho, double 
   const double s2 = sqrt_nr(t2);
   const double k1p = (3e-17 * s2) * rcp_nr(((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2));
   // exp of an argument below -746 is exactly 0 in double: skip the call in cold gas
-  const double k2 = gt_nn(neg_b(a2), 746.0) ? 0.0 : (hot2 ? 6.11e-14 : 2.67e-15) * exp(a2);
-  const double k3 = gt_nn(neg_b(a3), 746.0) ? 0.0 : (hot3 ? 5.22e-14 : 3.17e-15) * exp(a3);
+  const double k2 = gt_nn(neg_b(a2), 746.0) ? 0.0 : (hot2 ? 6.11e-14 : 2.67e-15) * exp_tang(a2);
+  const double k3 = gt_nn(neg_b(a3), 746.0) ? 0.0 : (hot3 ? 5.22e-14 : 3.17e-15) * exp_tang(a3);
   const double Ls = (ph.lshield > 0.0 ? ph.lshield : ph.dx) * ChemConst::PC;
   const double NH = nH * Ls, NH2 = nH2 * Ls;
-  const double fdust = exp(-(ph.taud * (NH + NH2)));
+  const double fdust = exp_tang(-(ph.taud * (NH + NH2)));
   const double x = NH2 * ph.ixnorm;
   const double u = 1.0 + x * ph.ibdop;
-  const double isx = rsqrt(1.0 + x);
+  const double isx = rsqrt_nr(1.0 + x);
   const double sx = (1.0 + x) * isx;
-  const double fsh = 0.965 * rcp_nr(u * u) + (0.035 * isx) * exp(-8.5e-4 * sx);
+  const double fsh = 0.965 * rcp_nr(u * u) + (0.035 * isx) * exp_tang(-8.5e-4 * sx);
   const double k4 = (3.3 * 1.7e-11) * fsh * fdust;
   const double C = k1p * n * nH;
   const double D = (k2 * nH + k3 * nH2) + k4;

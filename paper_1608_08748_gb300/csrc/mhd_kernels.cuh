@@ -703,81 +703,106 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 // Per cell, after the Lagrangian stage: chemistry (Sec. 2.7, FP64), heating/cooling (Sec. 2.8,
 // FP64, when on), regularisation (Sec. 2.9), the non-physical check, and the CFL denominator of the
 // new state for the next tau (Sec. 2.3).  cell_stages selects the per-cell stages (bit 0
 // chemistry, bit 1 heating/cooling; the full step runs both), do_reg the regularisation;
-// cell_stages = do_reg = 0 computes only the CFL denominator.  Returns the flags via the
-// warp-aggregated atomics of the caller.
+// cell_stages = do_reg = 0 computes only the CFL denominator.  All lanes of the warp call it (valid
+// marks those with a cell): the FP64 denominator is evaluated only where the FP32 screen
+// (cfl_estimate_f32) cannot exclude the cell from the maximum, against the largest estimate of the
+// warp and the FP64 maximum the box has reached so far; D stays 0 elsewhere.  Returns the flags via
+// the warp-aggregated atomics of the caller.
 template <typename T, bool IONS>
-__device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, int cell_stages, int do_reg,
-                                          double& D, int& bad, unsigned& vb) {
+__device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, bool valid, int cell_stages,
+                                          int do_reg, double& D, int& bad, unsigned& vb) {
   const Geom& g = B.g;
   const Phys& ph = B.ph;
   const bool ions = IONS && ph.ions;
   const State<T>& s = B.s;
-  int q[3];
-  decode_cell(g, c, q);
-  const double tau = B.sc->tau;
-  if ((cell_stages & 1) && ph.chem) {
-    const ChemOut co = chem_cell<IONS>(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c],
-                                       ions ? (double)s.rhp[c] : 0.0, tau);
-    s.rh2[c] = (T)co.rh2;
-    if (ions) s.rhp[c] = (T)co.rhp;
-  }
-  if ((cell_stages & 2) && ph.chem && ph.heatcool) {
-    const double d = heatcool_delta<IONS>(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c],
-                                          ions ? (double)s.rhp[c] : 0.0, tau);
-    s.E[c] = (T)((double)s.E[c] + d);
-    s.eint[c] = (T)((double)s.eint[c] + d);
-  }
-  idx_t up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
-  T Bc[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) Bc[d] = T(0.5) * (s.b[d][c] + s.b[d][up[d]]);
-  T rho = s.rho[c];
-  T m[3] = {s.m[0][c], s.m[1][c], s.m[2][c]};
-  T E = s.E[c], eint = s.eint[c];
-  if (do_reg) {
-    T m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
-    T kin = T(0.5) * m2 / rho;
-    T mag = T(0.5) * (Bc[0] * Bc[0] + Bc[1] * Bc[1] + Bc[2] * Bc[2]);
-    T e = E - kin - mag;
-    T f = e / E;
-    bool entropy_branch = f >= T(1e-3);
-    if (ph.regul_mode == 2) entropy_branch = !entropy_branch;
-    if (entropy_branch) {
-      if (ph.regul_mode != 0 || e > eint) eint = e;
-    } else {
-      T v2 = T(2) * (E - eint - mag) / rho;
-      if (v2 < T(0)) v2 = T(0);
-      T vnew = sqrt(v2);
-      T vold = sqrt(m2) / rho;
-      if (vold > T(0)) {
-        T scl = vnew / vold;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) m[d] = m[d] * scl;
-      }
-      vb = 1;
+  T rho = T(0), m[3] = {T(0), T(0), T(0)}, Bc[3] = {T(0), T(0), T(0)}, eint = T(0), rh2 = T(0), rhp = T(0);
+  float D32 = 0.0f;  // 0: no candidate
+  if (valid) {
+    int q[3];
+    decode_cell(g, c, q);
+    const double tau = B.sc->tau;
+    if ((cell_stages & 1) && ph.chem) {
+      const ChemOut co = chem_cell<IONS>(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c],
+                                         ions ? (double)s.rhp[c] : 0.0, tau);
+      s.rh2[c] = (T)co.rh2;
+      if (ions) s.rhp[c] = (T)co.rhp;
     }
-    s.eint[c] = eint;
+    if ((cell_stages & 2) && ph.chem && ph.heatcool) {
+      const double d = heatcool_delta<IONS>(ph, (double)s.rho[c], (double)s.eint[c], (double)s.rh2[c],
+                                            ions ? (double)s.rhp[c] : 0.0, tau);
+      s.E[c] = (T)((double)s.E[c] + d);
+      s.eint[c] = (T)((double)s.eint[c] + d);
+    }
+    idx_t up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]),
+                   cmap(g, q[0], q[1], q[2] + 1)};
 #pragma unroll
-    for (int d = 0; d < 3; ++d) s.m[d][c] = m[d];
-  }
-  T vals[10] = {rho, m[0], m[1], m[2], E, eint, ph.chem ? s.rh2[c] : T(0), s.b[0][c], s.b[1][c], s.b[2][c]};
+    for (int d = 0; d < 3; ++d) Bc[d] = T(0.5) * (s.b[d][c] + s.b[d][up[d]]);
+    rho = s.rho[c];
 #pragma unroll
-  for (int k = 0; k < 10; ++k)
-    if (!isfinite(vals[k])) bad = 1;
-  if (!(rho > T(0)) || !(eint > T(0))) bad = 1;
-  double gm = ph.chem ? gamma_eff((double)rho, (double)s.rh2[c]) : ph.gamma;
-  if (ions) {
-    const T rhp = s.rhp[c];
-    if (!isfinite(rhp)) bad = 1;
-    gm = gamma_eff((double)rho, (double)s.rh2[c], (double)rhp);
+    for (int d = 0; d < 3; ++d) m[d] = s.m[d][c];
+    T E = s.E[c];
+    eint = s.eint[c];
+    if (do_reg) {
+      T m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
+      T kin = T(0.5) * m2 / rho;
+      T mag = T(0.5) * (Bc[0] * Bc[0] + Bc[1] * Bc[1] + Bc[2] * Bc[2]);
+      T e = E - kin - mag;
+      T f = e / E;
+      bool entropy_branch = f >= T(1e-3);
+      if (ph.regul_mode == 2) entropy_branch = !entropy_branch;
+      if (entropy_branch) {
+        if (ph.regul_mode != 0 || e > eint) eint = e;
+      } else {
+        T v2 = T(2) * (E - eint - mag) / rho;
+        if (v2 < T(0)) v2 = T(0);
+        T vnew = sqrt(v2);
+        T vold = sqrt(m2) / rho;
+        if (vold > T(0)) {
+          T scl = vnew / vold;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) m[d] = m[d] * scl;
+        }
+        vb = 1;
+      }
+      s.eint[c] = eint;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) s.m[d][c] = m[d];
+    }
+    if (ph.chem) rh2 = s.rh2[c];
+    if (ions) rhp = s.rhp[c];
+    T vals[11] = {rho, m[0], m[1], m[2], E, eint, rh2, s.b[0][c], s.b[1][c], s.b[2][c], rhp};
+#pragma unroll
+    for (int k = 0; k < 11; ++k)
+      if (!isfinite(vals[k])) bad = 1;
+    if (!(rho > T(0)) || !(eint > T(0))) bad = 1;
+    if (!bad)
+      D32 = cfl_estimate_f32((float)rho, (float)m[0], (float)m[1], (float)m[2], (float)Bc[0], (float)Bc[1],
+                             (float)Bc[2], (float)eint,
+                             gamma_minus_one_f32(ph.chem, ph.gamma, (float)rho, (float)rh2, (float)rhp));
   }
-  if (!bad)  // FP64 CFL of the new state (FP32 fields widened)
+  // the screen: a finite estimate raised by 2^-12 below the largest finite estimate of the warp
+  // lowered by 2^-12 (whose cell is evaluated unless it is excluded too), or below the FP64 maximum
+  // reached so far, excludes the cell
+  const float wmax = warp_max_f(D32 <= 3.0e38f ? D32 : 0.0f);
+  const double reached = __longlong_as_double(*(volatile long long*)&B.sc->dmax);
+  const float bound = fmaxf(__double2float_rd(reached), wmax * (1.0f - 0x1p-12f));
+  if (valid && !bad && !(D32 * (1.0f + 0x1p-12f) < bound)) {
+    // FP64 CFL of the new state (FP32 fields widened)
+    double gm = ph.chem ? gamma_eff((double)rho, (double)rh2) : ph.gamma;
+    if (ions) gm = gamma_eff((double)rho, (double)rh2, (double)rhp);
     D = cfl_denominator((double)rho, (double)m[0], (double)m[1], (double)m[2], (double)Bc[0],
                         (double)Bc[1], (double)Bc[2], gm * ((gm - 1.0) * (double)eint));
+  }
 }
 
 template <typename T, bool IONS>
@@ -789,9 +814,9 @@ __global__ void __launch_bounds__(512) kb_post(const Box<T>* __restrict__ boxes,
     double D = 0.0;
     int bad = 0;
     unsigned vb = 0;
-    if (c < B.g.N) post_cell<T, IONS>(B, c, cell_stages, do_reg, D, bad, vb);
+    post_cell<T, IONS>(B, c, c < B.g.N, cell_stages, do_reg, D, bad, vb);
     if (!check) bad = 0;
-    D = warp_max(D);
+    if (__any_sync(0xffffffffu, D > 0.0)) D = warp_max(D);
     int anybad = __any_sync(0xffffffffu, bad);
     unsigned nvb = __popc(__ballot_sync(0xffffffffu, vb));
     if ((threadIdx.x & 31) == 0) {

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <random>
 #include <vector>
 
@@ -313,6 +314,81 @@ int main() {
       if (e > 2.0) ++bad;
     }
     report("newton_raphson_ulp", n, worst, bad);
+  }
+  // 5e. the table-driven exponential of the chemistry rates (Tang's method) against e^x in long
+  // double: within 1.01 ulp (half an ulp of the table entry, scaled by e^r <= 1.011, and half an ulp
+  // of the last rounding) over the rates' argument range [-746, 0] (dense near 0 and over whole
+  // decades of small arguments), the ends of its fast range and the library tail below it
+  {
+    const long n = 2000000;
+    long bad = 0;
+    double worst = 0;
+    auto ulp_err = [](double y, long double e) -> double {
+      if (e == 0.0L) return y == 0.0 ? 0.0 : 1e300;
+      const double ulp = std::ldexp(1.0, std::max(std::ilogb((double)e), -1022) - 52);
+      return (double)(std::fabs((long double)y - e) / ulp);
+    };
+    const double special[] = {0.0, -0.0, -5e-324, -1e-300, -1e-17, -0.010830424696249145,
+                              -0.010830424696249146, -0.5, -1.0, -707.0, -706.9999999999999,
+                              -707.0000000000001, -708.0, -708.4, -745.0, -745.13, -746.0, 1.0, 706.9};
+    long cases = 0;
+    for (double x : special) {
+      const double e = ulp_err(exp_tang(x), expl((long double)x));
+      worst = std::max(worst, e);
+      if (e > 1.01) ++bad;
+      ++cases;
+    }
+    for (long it = 0; it < n; ++it) {
+      const int kind = (int)(it % 4);
+      const double x = kind == 0 ? -746.0 * U01(g)
+                     : kind == 1 ? -U01(g)
+                     : kind == 2 ? -std::ldexp(1.0 + U01(g), -(int)(60 * U01(g)))
+                                 : -20.0 * U01(g);
+      const double e = ulp_err(exp_tang(x), expl((long double)x));
+      worst = std::max(worst, e);
+      if (e > 1.01) ++bad;
+      ++cases;
+    }
+    report("exp_tang_ulp", cases, worst, bad);
+  }
+  // 5f. the FP32 estimate of the CFL screen against the FP64 denominator of the same cell: within
+  // 64 u (u = 2^-24; the screen allows 4096 u) wherever the guards pass, on densities, momenta,
+  // fields and internal energies over many decades, zero components, the ideal gas with gamma - 1
+  // down to 1e-4, and the H/H2 (+ H+) mixture with some unphysical abundances; the guards must pass
+  // on at least half of the cases
+  {
+    const long n = 1000000;
+    long bad = 0, passed = 0;
+    double worst = 0;
+    auto logu = [&](double lo, double hi) { return std::exp(std::log(lo) + (std::log(hi) - std::log(lo)) * U01(g)); };
+    for (long it = 0; it < n; ++it) {
+      const int kind = (int)(it % 4);
+      const bool chem = (it / 4) % 2;
+      const double rho = kind == 0 ? logu(1e-13, 1e13) : logu(1e-3, 1e3);
+      double m[3], Bv[3];
+      for (int d = 0; d < 3; ++d) {
+        m[d] = U01(g) < 0.1 ? 0.0 : U(g) * (kind == 1 ? logu(1e-30, 1e10) : logu(1e-3, 1e3));
+        Bv[d] = U01(g) < 0.2 ? 0.0 : U(g) * (kind == 2 ? logu(1e-30, 1e10) : logu(1e-3, 1e3));
+      }
+      const double eint = rho * (kind == 3 ? logu(1e-16, 1e8) : logu(1e-4, 1e4));
+      const double fhp = it % 3 == 0 ? 0.0 : 0.1 * U01(g);
+      double rh2 = rho * U01(g) * (1.0 - fhp);
+      const double rhp = rho * fhp;
+      if (it % 97 == 0) rh2 = rho * (1.0 + 0.5 * U01(g));  // more H2 than gas
+      const double gamma = chem ? 5.0 / 3.0 : 1.0 + logu(1e-4, 0.67);
+      const float gm1 = gamma_minus_one_f32(chem, gamma, (float)rho, (float)rh2, (float)rhp);
+      const float D32 = cfl_estimate_f32((float)rho, (float)m[0], (float)m[1], (float)m[2], (float)Bv[0],
+                                         (float)Bv[1], (float)Bv[2], (float)eint, gm1);
+      if (!(D32 <= 3.0e38f)) continue;
+      ++passed;
+      const double gm = chem ? gamma_eff(rho, rh2, rhp) : gamma;
+      const double D = cfl_denominator(rho, m[0], m[1], m[2], Bv[0], Bv[1], Bv[2], gm * ((gm - 1.0) * eint));
+      const double e = (std::isfinite(D) && D > 0.0) ? std::fabs((double)D32 - D) / D : 1e300;
+      worst = std::max(worst, e);
+      if (e > 0x1p-18) ++bad;
+    }
+    report("cfl_screen_bound", passed, worst, bad);
+    report("cfl_screen_guard_share", n, (double)passed / n, passed < n / 2 ? 1 : 0);
   }
   // 6. CFL denominator (FP64) against the oracle's
   {

@@ -10,8 +10,11 @@ streamed ones equal the five-point ones bit for bit, the Riemann solve (Sec. 2.4
 oracle's in FP64 and 1e-4 in FP32, the chemistry (Sec. 2.7, App. D; with and without reactions 5-8)
 within 1e-12, the heating/cooling change (Sec. 2.8; with and without Gamma_5 and Lambda_6-8) within
 1e-12 of the gross heating plus cooling, the Newton-Raphson reciprocal, reciprocal square root
-and square root within 2 ulp of the correctly rounded values, and the CFL
-denominator (Sec. 2.3) within 1e-13.  The host build uses -ffp-contract=off like the oracle; the
+and square root within 2 ulp of the correctly rounded values, the CFL
+denominator (Sec. 2.3) within 1e-13, the table-driven exponential of the chemistry within 1.01 ulp of
+e^x (long-double reference), and the FP32 estimate of the CFL screen within 64 u (u = 2^-24) of the
+FP64 denominator wherever its guards pass, on inputs over many decades, with and without the H/H2
+mixture's gamma.  The host build uses -ffp-contract=off like the oracle; the
 GPU build contracts to FMA, whose effect the GPU parity tests bound."""
 import os
 import shutil
@@ -62,11 +65,26 @@ template <int K> inline double scale_down_b(double x) {
 template <int K> inline float scale_down_b(float x) { return x * (1.0f / (float)(1 << K)); }
 inline double rsqrt_seed(double x) { return seed_(1.0 / std::sqrt(ftz_(x))); }
 inline unsigned umulhi32(unsigned a, unsigned b) { return (unsigned)(((unsigned long long)a * b) >> 32); }
+// exp_tang's bit-pattern pieces and the FP32 operations rounded to nearest (host floats are IEEE
+// single with subnormals; 1/sqrt through double, rounded once more)
+inline bool exp_fast_range(double x) {
+  const unsigned long long ux = (unsigned long long)bits_(x);
+  return ux <= 0xc086180000000000ull && (ux >= 0x8000000000000000ull || ux < 0x4086180000000000ull);
+}
+inline int lo_word(double x) { return (int)(unsigned)((unsigned long long)bits_(x) & 0xffffffffull); }
+inline double scale_pow2(double y, int m) { return from_bits_(bits_(y) + (long long)m * (1LL << 52)); }
+inline double exp2_frac32(int j) { return kExp2Frac32[j]; }
+inline float fsqrt_rn(float x) { return std::sqrt(x); }
+inline float frsqrt_rn(float x) { return (float)(1.0 / std::sqrt((double)x)); }
+inline float fdiv_rn(float a, float b) { return a / b; }
+inline float fmul_rn(float a, float b) { return a * b; }
+inline float f_inf() { return std::numeric_limits<float>::infinity(); }
 '''
 
 BOUNDS = {"ppm_lean_close": 0, "ppm_stream_bits": 0, "ppm_fp32": 0, "riemann_fp64": 0, "riemann_fp32": 0,
           "chemistry": 0, "heatcool": 0, "chemistry_ions": 0, "heatcool_ions": 0, "ion_instances_without_ions_same_bits": 0, "cfl": 0,
-          "newton_raphson_ulp": 0, "fast_index_division": 0}
+          "newton_raphson_ulp": 0, "fast_index_division": 0, "exp_tang_ulp": 0, "cfl_screen_bound": 0,
+          "cfl_screen_guard_share": 0}
 
 
 def _cuda_include():
