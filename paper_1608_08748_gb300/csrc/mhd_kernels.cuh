@@ -122,17 +122,24 @@ __device__ __forceinline__ void prim_cell(const Box<T>& B, idx_t c) {
   const Geom& g = B.g;
   int q[3];
   decode_cell(g, c, q);
-  T rho = B.s.rho[c];
+  const T rho = B.s.rho[c];
   idx_t up[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
+  T Bc[3], m[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) B.w.B[d][c] = T(0.5) * (B.s.b[d][c] + B.s.b[d][up[d]]);
+  for (int d = 0; d < 3; ++d) {
+    Bc[d] = T(0.5) * (B.s.b[d][c] + B.s.b[d][up[d]]);
+    m[d] = B.s.m[d][c];
+  }
+  const T eint = B.s.eint[c];
   // gamma_eff in the bulk type: the FP32-bulk path's fluxes are FP32
   T gmt = !B.ph.chem ? (T)B.ph.gamma
           : (IONS && B.ph.ions) ? gamma_eff(rho, B.s.rh2[c], B.s.rhp[c]) : gamma_eff(rho, B.s.rh2[c]);
   const T irho = rcp_t(rho);  // one reciprocal for the three velocities
 #pragma unroll
-  for (int d = 0; d < 3; ++d) B.w.v[d][c] = B.s.m[d][c] * irho;
-  B.w.p[c] = (gmt - T(1)) * B.s.eint[c];
+  for (int d = 0; d < 3; ++d) B.w.B[d][c] = Bc[d];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) B.w.v[d][c] = m[d] * irho;
+  B.w.p[c] = (gmt - T(1)) * eint;
   B.w.g[c] = gmt;
   B.w.sr[c] = sqrt_t(rho);
 }
@@ -402,9 +409,11 @@ __device__ __forceinline__ void edges_point(const Box<T>& B, idx_t t) {
   const Geom& g = B.g;
   int c[3];
   decode_fast<3>(g, t, c);
+  T e[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    e[d] = T(0);
     if (c[d] >= g.n[d]) continue;
     int a[3] = {c[0], c[1], c[2]};
     a[d2] = wrap(c[d2], g.n[d2], g.bc[d2]);
@@ -416,8 +425,11 @@ __device__ __forceinline__ void edges_point(const Box<T>& B, idx_t t) {
     int blo[3] = {c[0], c[1], c[2]};
     blo[d1] = wrap(c[d1] - 1, g.n[d1], g.bc[d1]);
     T f2 = B.fo[d2].f[6][fidx(g, blo[0], blo[1], blo[2])] + B.fo[d2].f[6][fidx(g, b[0], b[1], b[2])];
-    B.e[d][t] = T(0.25) * (f1 + f2);
+    e[d] = T(0.25) * (f1 + f2);
   }
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (c[d] < g.n[d]) B.e[d][t] = e[d];
 }
 
 template <typename T>
@@ -431,17 +443,22 @@ __global__ void __launch_bounds__(512) kb_edges(const Box<T>* __restrict__ boxes
 
 // SSP-RK3 combination of Sec. 2.2 for one value: a Q^n + b Q + g tau R, with g tau R = gth S for a
 // flux-difference sum S (R = S / h, gth = g tau / h once per thread).  The first substage has
-// a = 0, b = g = 1: it stores Q^n (the stage's start value, the Q it reads) in the RK register and
-// returns Q + gth S; later substages read the register.  (The FP64 update kernels are bound by the
-// FP64 pipe, so the constants are folded.)
+// a = 0, b = g = 1 and returns Q + gth S; its caller stores Q^n (the stage's start value, the Q it
+// read) in the RK register, which later substages read as q0.  (The FP64 update kernels are bound
+// by the FP64 pipe, so the constants are folded.)
 template <typename T>
-__device__ __forceinline__ T rk_combine(T* qn, T q, T a, T b, T gthS, int r) {
-  if (r == 0) {
-    *qn = q;
-    return q + gthS;
-  }
-  return (a * *qn + b * q) + gthS;
+__device__ __forceinline__ T rk_value(T q, T q0, T a, T b, T gthS, int r) {
+  return r == 0 ? q + gthS : (a * q0 + b * q) + gthS;
 }
+
+// The cell kernels (primitives, edge EMFs, and the two updates in FP32) issue every load of a cell
+// before its first store.  A thread stores only its own cell (or edge), which no load of the kernel
+// reads, so the order is free; the compiler cannot prove that (all fields are plain pointers), and
+// a store between two loads costs the thread one DRAM latency per stored field.  The FP64 updates
+// keep the order field by field: holding all their loads would double their registers and halve
+// the resident warps, and at the FP64 path's sizes that costs more than the latencies.
+template <typename T>
+__host__ __device__ constexpr bool update_loads_first() { return sizeof(T) == 4; }
 // g tau / h of substage r
 template <typename T>
 __device__ __forceinline__ T rk_gth(const Box<T>& B, int r) {
@@ -477,7 +494,7 @@ __device__ __forceinline__ void euler_update_cell(const Box<T>& B, idx_t c, int 
   if (GRAV) {
     // self-gravity (Sec. 2): -rho grad Phi and -rho v . grad Phi, central differences of the
     // potential of the step (periodic box); a separate instance, so that the update without
-    // gravity keeps its registers (42 against 62 in FP32)
+    // gravity keeps its registers
     const idx_t dn[3] = {cmap(g, q[0] - 1, q[1], q[2]), cmap(g, q[0], q[1] - 1, q[2]), cmap(g, q[0], q[1], q[2] - 1)};
     const idx_t upc[3] = {cmap(g, q[0] + 1, q[1], q[2]), cmap(g, q[0], q[1] + 1, q[2]), cmap(g, q[0], q[1], q[2] + 1)};
     const T rho = B.s.rho[c];
@@ -490,14 +507,48 @@ __device__ __forceinline__ void euler_update_cell(const Box<T>& B, idx_t c, int 
   }
   T* qq[5] = {B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint};
   T* q0[5] = {B.s0.m[0], B.s0.m[1], B.s0.m[2], B.s0.E, B.s0.eint};
-#pragma unroll
-  for (int v = 0; v < 5; ++v) qq[v][c] = rk_combine(q0[v] + c, qq[v][c], a, bb, gth * Rv[v], r);
   // Flux-CT: d b_d / dt = -(curl E)_d on the face i_d - 1/2 of this cell
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
+  auto curl_of = [&](int d) {
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-    T curl = (B.e[d1][fup[d2]] - B.e[d1][f0]) - (B.e[d2][fup[d1]] - B.e[d2][f0]);
-    B.s.b[d][c] = rk_combine(B.s0.b[d] + c, B.s.b[d][c], a, bb, gth * curl, r);
+    return (B.e[d1][fup[d2]] - B.e[d1][f0]) - (B.e[d2][fup[d1]] - B.e[d2][f0]);
+  };
+  if constexpr (update_loads_first<T>()) {
+    T qv[5], q0v[5], bv[3], b0v[3], curl[3];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      qv[v] = qq[v][c];
+      q0v[v] = r ? q0[v][c] : T(0);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      bv[d] = B.s.b[d][c];
+      b0v[d] = r ? B.s0.b[d][c] : T(0);
+      curl[d] = curl_of(d);
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      if (r == 0) q0[v][c] = qv[v];
+      qq[v][c] = rk_value(qv[v], q0v[v], a, bb, gth * Rv[v], r);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (r == 0) B.s0.b[d][c] = bv[d];
+      B.s.b[d][c] = rk_value(bv[d], b0v[d], a, bb, gth * curl[d], r);
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const T qv = qq[v][c], q0v = r ? q0[v][c] : T(0);
+      if (r == 0) q0[v][c] = qv;
+      qq[v][c] = rk_value(qv, q0v, a, bb, gth * Rv[v], r);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T curl = curl_of(d);
+      const T bv = B.s.b[d][c], b0v = r ? B.s0.b[d][c] : T(0);
+      if (r == 0) B.s0.b[d][c] = bv;
+      B.s.b[d][c] = rk_value(bv, b0v, a, bb, gth * curl, r);
+    }
   }
 }
 
@@ -676,13 +727,40 @@ __device__ __forceinline__ void lag_update_cell(const Box<T>& B, idx_t c, int r)
   T* qq[8] = {B.s.rho, B.s.m[0], B.s.m[1], B.s.m[2], B.s.E, B.s.eint, B.s.rh2, B.s.rhp};
   T* q0[8] = {B.s0.rho, B.s0.m[0], B.s0.m[1], B.s0.m[2], B.s0.E, B.s0.eint, B.s0.rh2, B.s0.rhp};
   const int nv = B.nv;
-#pragma unroll
-  for (int v = 0; v < (IONS ? 8 : 7); ++v) {
-    if (v >= nv) break;
+  constexpr int NV = IONS ? 8 : 7;
+  auto sum_of = [&](int v) {
     T acc = T(-0.0);  // -0 + x is x: the first addition folds away
 #pragma unroll
     for (int d = 0; d < 3; ++d) acc = acc + (B.fo[d].f[v][f0] - B.fo[d].f[v][fup[d]]);
-    qq[v][c] = rk_combine(q0[v] + c, qq[v][c], a, bb, gth * acc, r);
+    return acc;
+  };
+  if constexpr (update_loads_first<T>()) {
+    T acc[NV], qv[NV], q0v[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      acc[v] = qv[v] = q0v[v] = T(0);
+      if (v < nv) {
+        acc[v] = sum_of(v);
+        qv[v] = qq[v][c];
+        if (r) q0v[v] = q0[v][c];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      if (v < nv) {
+        if (r == 0) q0[v][c] = qv[v];
+        qq[v][c] = rk_value(qv[v], q0v[v], a, bb, gth * acc[v], r);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      if (v >= nv) break;
+      const T acc = sum_of(v);
+      const T qv = qq[v][c], q0v = r ? q0[v][c] : T(0);
+      if (r == 0) q0[v][c] = qv;
+      qq[v][c] = rk_value(qv, q0v, a, bb, gth * acc, r);
+    }
   }
 }
 
