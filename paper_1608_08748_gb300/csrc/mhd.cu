@@ -653,12 +653,12 @@ int mhd_stage(mhd_sim* S, int which, double tau) {
   if (S->precision) {
     launch_small(S->x32, S->stream, 0);
     if (which == 1) launch_euler_stage(S->x32, S->stream);
-    if (which == 2) launch_lag_stage(S->x32, S->stream);
+    if (which == 2) launch_lag_stage(S->x32, S->stream, false);
     if (which >= 3) launch_post(S->x32, S->stream, cell_stages, which == 4, 1);
   } else {
     launch_small(S->x64, S->stream, 0);
     if (which == 1) launch_euler_stage(S->x64, S->stream);
-    if (which == 2) launch_lag_stage(S->x64, S->stream);
+    if (which == 2) launch_lag_stage(S->x64, S->stream, false);
     if (which >= 3) launch_post(S->x64, S->stream, cell_stages, which == 4, 1);
   }
   CK(cudaGetLastError());
@@ -693,9 +693,9 @@ int mhd_check_flags(int clear, unsigned* flags) {
 
 int mhd_launches_per_step(mhd_sim* S) {
   if (!valid(S)) return fail(MHD_EINVAL, "mhd_launches_per_step: null sim");
-  // begin + 3 x (primitives, 3 faces, edges, update) + 3 x (3 faces, update) + post + end (the
-  // first update of each stage stores its RK register Q^n)
-  return 1 + 3 * 6 + 3 * 4 + 1 + 1;
+  // begin + 3 x (primitives, 3 faces, edges, update) + 3 x (3 faces) + 2 updates + the last
+  // update with the post stage + end (the first update of each stage stores its RK register Q^n)
+  return 1 + 3 * 6 + 3 * 3 + 2 + 1 + 1;
 }
 
 int mhd_profile(mhd_sim* S, double cfl, int steps, double* out_ms, int64_t* out_launches) {

@@ -11,7 +11,7 @@ unsigned check_flags_f32(bool clear) { return check_flags_of_this_unit(clear); }
 
 template cudaError_t prepare_kernels<float>();
 template void launch_euler_stage<float>(Exec<float>&, cudaStream_t);
-template void launch_lag_stage<float>(Exec<float>&, cudaStream_t);
+template void launch_lag_stage<float>(Exec<float>&, cudaStream_t, bool);
 template void launch_step<float>(Exec<float>&, cudaStream_t);
 template void launch_post<float>(Exec<float>&, cudaStream_t, int, int, int);
 template cudaError_t launch_cfl<float>(Exec<float>&, cudaStream_t);

@@ -883,6 +883,21 @@ __device__ __forceinline__ void post_cell(const Box<T>& B, idx_t c, bool valid, 
   }
 }
 
+// the warp's share of the post stage's box scalars: the largest FP64 CFL denominator, the
+// non-physical flag and the count of velocity-branch regularisations
+template <typename T>
+__device__ __forceinline__ void post_warp_reduce(const Box<T>& B, double D, int bad, unsigned vb, int check) {
+  if (!check) bad = 0;
+  if (__any_sync(0xffffffffu, D > 0.0)) D = warp_max(D);
+  int anybad = __any_sync(0xffffffffu, bad);
+  unsigned nvb = __popc(__ballot_sync(0xffffffffu, vb));
+  if ((threadIdx.x & 31) == 0) {
+    if (D > 0.0) atomicMax(&B.sc->dmax, (unsigned long long)__double_as_longlong(D));
+    if (anybad) atomicOr(&B.sc->flags, 1);
+    if (nvb) atomicAdd(&B.sc->vel_branch, (unsigned long long)nvb);
+  }
+}
+
 template <typename T, bool IONS>
 __global__ void __launch_bounds__(512) kb_post(const Box<T>* __restrict__ boxes, Tiles tl, int cell_stages,
                                                int do_reg, int check) {
@@ -893,15 +908,27 @@ __global__ void __launch_bounds__(512) kb_post(const Box<T>* __restrict__ boxes,
     int bad = 0;
     unsigned vb = 0;
     post_cell<T, IONS>(B, c, c < B.g.N, cell_stages, do_reg, D, bad, vb);
-    if (!check) bad = 0;
-    if (__any_sync(0xffffffffu, D > 0.0)) D = warp_max(D);
-    int anybad = __any_sync(0xffffffffu, bad);
-    unsigned nvb = __popc(__ballot_sync(0xffffffffu, vb));
-    if ((threadIdx.x & 31) == 0) {
-      if (D > 0.0) atomicMax(&B.sc->dmax, (unsigned long long)__double_as_longlong(D));
-      if (anybad) atomicOr(&B.sc->flags, 1);
-      if (nvb) atomicAdd(&B.sc->vel_branch, (unsigned long long)nvb);
-    }
+    post_warp_reduce(B, D, bad, vb, check);
+  }
+}
+
+// The last Lagrangian substage (r = 2) and the post stage of a step in one pass.  A cell's update
+// reads the face fluxes and the cell's own fields, and its post stage reads only the cell's own
+// fields and the face field b, which neither changes; so one thread takes both, in program order,
+// and the update's HBM traffic overlaps the post stage's FP64 work.
+template <typename T, bool IONS>
+__global__ void __launch_bounds__(512) kb_lag_update_post(const Box<T>* __restrict__ boxes, Tiles tl,
+                                                          int cell_stages, int do_reg, int check) {
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    idx_t c = tl.start[t_] + (idx_t)threadIdx.x;
+    const bool valid = c < B.g.N;
+    if (valid) lag_update_cell<T, IONS>(B, c, 2);
+    double D = 0.0;
+    int bad = 0;
+    unsigned vb = 0;
+    post_cell<T, IONS>(B, c, valid, cell_stages, do_reg, D, bad, vb);
+    post_warp_reduce(B, D, bad, vb, check);
   }
 }
 

@@ -355,8 +355,10 @@ void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
   }
 }
 
+// fuse_last: the last substage's update is left to the fused update and post stage of the step
+// (launch_lag_post)
 template <typename T>
-void launch_lag_stage(Exec<T>& X, cudaStream_t st) {
+void launch_lag_stage(Exec<T>& X, cudaStream_t st, bool fuse_last) {
   NvtxRange range("Lagrangian stage (Sec. 2.6)");
   for (int r = 0; r < 3; ++r) {
     launch_sweeps(X, st, [&](int d, cudaStream_t s) {
@@ -384,6 +386,7 @@ void launch_lag_stage(Exec<T>& X, cudaStream_t st) {
         }
       }
     });
+    if (r == 2 && fuse_last) break;
     if (X.ions)
       launch_k(X, st, KC_LUPD, DOM_CELLS, kb_lag_update<T, true>, r);
     else
@@ -402,13 +405,24 @@ void launch_post(Exec<T>& X, cudaStream_t st, int cell_stages, int do_reg, int c
     launch_k(X, st, KC_POST, DOM_CELLS, kb_post<T, false>, cell_stages, do_reg, check);
 }
 
+// the last Lagrangian update with the post stage (kb_lag_update_post; the post stage's launch
+// shape)
+template <typename T>
+void launch_lag_post(Exec<T>& X, cudaStream_t st, int cell_stages, int do_reg, int check) {
+  NvtxRange range("last Lagrangian update + chemistry, heating/cooling, regularisation, CFL");
+  if (X.ions)
+    launch_k(X, st, KC_POST, DOM_CELLS, kb_lag_update_post<T, true>, cell_stages, do_reg, check);
+  else
+    launch_k(X, st, KC_POST, DOM_CELLS, kb_lag_update_post<T, false>, cell_stages, do_reg, check);
+}
+
 template <typename T>
 void launch_step(Exec<T>& X, cudaStream_t st) {
   NvtxRange range("mhd step");
   launch_small(X, st, 0);
   launch_euler_stage(X, st);
-  launch_lag_stage(X, st);
-  launch_post(X, st, 3, 1, 1);
+  launch_lag_stage(X, st, true);
+  launch_lag_post(X, st, 3, 1, 1);
   launch_small(X, st, 1);
 }
 
@@ -538,7 +552,7 @@ cudaError_t diag_partial(mhd_sim* S, Box<T>& B) {
 #ifndef MHD_RT_F32_TU
 extern template cudaError_t prepare_kernels<float>();
 extern template void launch_euler_stage<float>(Exec<float>&, cudaStream_t);
-extern template void launch_lag_stage<float>(Exec<float>&, cudaStream_t);
+extern template void launch_lag_stage<float>(Exec<float>&, cudaStream_t, bool);
 extern template void launch_step<float>(Exec<float>&, cudaStream_t);
 extern template void launch_post<float>(Exec<float>&, cudaStream_t, int, int, int);
 extern template cudaError_t launch_cfl<float>(Exec<float>&, cudaStream_t);
