@@ -280,6 +280,7 @@ mhd_sim* mhd_create(int nx, int ny, int nz, double gamma, double dx) {
   S->ph.ibdop = 1.0 / 3.0;
   S->ph.ixnorm = 1.0 / 5e14;
   S->ph.taud = 1e-21;
+  mhd::set_shielding(S->ph);
   S->ph.heatcool = 0;
   S->ph.grav_g = 0.0;
   S->ph.ions = 0;
@@ -366,6 +367,7 @@ int mhd_set_option(mhd_sim* S, int key, double v) {
     case MHD_OPT_CHEM_LSHIELD:
       if (v < 0.0) return fail(MHD_EINVAL, "shielding length must be >= 0");
       S->ph.lshield = v;
+      mhd::set_shielding(S->ph);
       break;
     case MHD_OPT_CHEM_BDOP:
       if (!(v > 0.0)) return fail(MHD_EINVAL, "Doppler parameter must be > 0");
@@ -376,10 +378,12 @@ int mhd_set_option(mhd_sim* S, int key, double v) {
       if (!(v > 0.0)) return fail(MHD_EINVAL, "x normaliser must be > 0");
       S->ph.xnorm = v;
       S->ph.ixnorm = 1.0 / v;
+      mhd::set_shielding(S->ph);
       break;
     case MHD_OPT_CHEM_TAUD:
       if (v < 0.0) return fail(MHD_EINVAL, "dust opacity must be >= 0");
       S->ph.taud = v;
+      mhd::set_shielding(S->ph);
       break;
     case MHD_OPT_GRAPH:
       S->use_graph = v != 0.0;

@@ -61,6 +61,7 @@ struct Phys {
   double lshield;    // shielding length, code units
   double bdop, xnorm, taud;
   double ibdop, ixnorm;  // 1 / bdop, 1 / xnorm
+  double taud_ls, ls_ixnorm;  // taud L_s and L_s / xnorm, L_s the shielding length in cm (set_shielding)
   int heatcool;          // Sec. 2.8 heating/cooling stage on (needs chem)
   double grav_g;         // gravitational constant in code units (0: no self-gravity)
   int ions;              // reactions 5-8 with H+ and electrons on (needs chem)
@@ -840,13 +841,23 @@ struct ChemConst {
   static constexpr double KMS = 1.0e5;               // cm / s
 };
 
-// The App. D formulas in FP64 with few divisions (the rates agree with a term-by-term evaluation to
-// about 1e-14 relative):
+// the per-box products of the shielding length L_s = (lshield > 0 ? lshield : dx) pc (App. D column
+// densities N = n L_s): set on the host whenever lshield, xnorm, taud or dx change
+inline void set_shielding(Phys& ph) {
+  const double Ls = (ph.lshield > 0.0 ? ph.lshield : ph.dx) * ChemConst::PC;
+  ph.taud_ls = ph.taud * Ls;
+  ph.ls_ixnorm = Ls * ph.ixnorm;
+}
+
+// The App. D formulas in FP64 with few FP64 instructions (the rates agree with a term-by-term
+// evaluation to about 1e-14 relative):
 //   T = (gamma - 1) rho eps P0 / (n_particles k_B) with gamma - 1 = 2 n_particles / (3 n_1 + 5 n_H2)
-//     = 2 P0 rho eps / ((3 n_1 + 5 n_H2) k_B), n_1 = n_H + n_H+ + n_e, and T, 1/T from one
+//     = (2 P0 / k_B) rho eps / (3 n_1 + 5 n_H2), n_1 = n_H + n_H+ + n_e, and T, 1/T from one
 //     reciprocal of the product;
-//   1/sqrt(1 + x) from one reciprocal square root; 1/x_norm and 1/b_doppler precomputed;
-//   the exponentials of the H/H2 rates by exp_tang (their arguments are <= 0).
+//   1/sqrt(1 + x) from one reciprocal square root; 1/x_norm, 1/b_doppler and the products with the
+//   shielding length precomputed; one reciprocal for k1' and 1/u^2 (of their denominators' product);
+//   the exponentials of the H/H2 rates by exp_tang (their arguments are <= 0); the arguments of
+//   reactions 2 and 3 not formed in gas cold enough for their exponentials to be 0.
 struct ChemOut {
   double rh2, rhp;  // new rho_H2 and rho_H+
 };
@@ -894,33 +905,40 @@ __device__ __forceinline__ ChemOut chem_cell(const Phys& ph, double rho, double 
   // gets the same bits from either instance (rhp = 0 then adds exactly nothing)
   double nH = rho - rh2;
   if (IONS) nH = nH - rhp;
-  const double nH2 = 0.5 * rh2, n = rho;
-  const double num = (2.0 * P0) * eint;
+  const double nH2 = scale_down_b<1>(rh2), n = rho;
+  const double num = (2.0 * P0 / ChemConst::KB) * eint;
   double den3 = fma(3.0, nH, 5.0 * nH2);  // 3 n_1 + 5 n_H2 with n_1 = n_H + n_H+ + n_e
   if (IONS) den3 = fma(6.0, rhp, den3);
-  const double den = den3 * ChemConst::KB;
-  const double r = rcp_nr(num * den);
-  const double T = (num * num) * r, iT = (den * den) * r;
-  // App. D rates
+  const double r = rcp_nr(num * den3);
+  const double T = (num * num) * r, iT = (den3 * den3) * r;
+  // App. D rates; the branch tests and clamps compare on the integer pipe (T >= 0; a2, a3 < 0)
   const double t2 = T * 0.01;
-  // the branch tests and clamps compare on the integer pipe (T >= 0; a2, a3 < 0)
   const bool hot2 = gt_nn(T, 7390.0), hot3 = gt_nn(T, 7291.0);
-  const double a2 = hot2 ? -2.93e4 * iT : -((6750.0 * iT) * (6750.0 * iT));
-  const double a3 = hot3 ? -3.22e4 * iT : -(4060.0 * iT) - (7500.0 * iT) * (7500.0 * iT);
-  const double s2 = sqrt_nr(t2);
-  const double k1p = (3e-17 * s2) * rcp_nr(((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2));
-  // exp of an argument below -746 is exactly 0 in double: skip the call in cold gas
-  const double k2 = gt_nn(neg_b(a2), 746.0) ? 0.0 : (hot2 ? 6.11e-14 : 2.67e-15) * exp_tang(a2);
-  const double k3 = gt_nn(neg_b(a3), 746.0) ? 0.0 : (hot3 ? 5.22e-14 : 3.17e-15) * exp_tang(a3);
-  const double Ls = (ph.lshield > 0.0 ? ph.lshield : ph.dx) * ChemConst::PC;
-  const double NH = nH * Ls, NH2 = nH2 * Ls;
-  const double fdust = exp_tang(-(ph.taud * (NH + NH2)));
-  const double x = NH2 * ph.ixnorm;
+  // reactions 2 and 3: exp of an argument below -746 is exactly 0 in double, and the cold branches'
+  // arguments -(6750 / T)^2 and -4060 / T - (7500 / T)^2 lie below -746.6 for T <= 247 and below
+  // -747 for T <= 277, so there the rates are 0 without forming them (warps of cold cells skip)
+  double k2 = 0.0, k3 = 0.0;
+  if (gt_nn(T, 247.0)) {
+    const double a2 = hot2 ? -2.93e4 * iT : -((6750.0 * iT) * (6750.0 * iT));
+    if (!gt_nn(neg_b(a2), 746.0)) k2 = (hot2 ? 6.11e-14 : 2.67e-15) * exp_tang(a2);
+  }
+  if (gt_nn(T, 277.0)) {
+    const double a3 = hot3 ? -3.22e4 * iT : -(4060.0 * iT) - (7500.0 * iT) * (7500.0 * iT);
+    if (!gt_nn(neg_b(a3), 746.0)) k3 = (hot3 ? 5.22e-14 : 3.17e-15) * exp_tang(a3);
+  }
+  // shielding: f_dust = exp(-taud (N_H + N_H2)), x = N_H2 / x_norm, N = n L_s
+  const double fdust = exp_tang(-(ph.taud_ls * (nH + nH2)));
+  const double x = nH2 * ph.ls_ixnorm;
   const double u = 1.0 + x * ph.ibdop;
   const double isx = rsqrt_nr(1.0 + x);
   const double sx = (1.0 + x) * isx;
-  const double fsh = 0.965 * rcp_nr(u * u) + (0.035 * isx) * exp_tang(-8.5e-4 * sx);
-  const double k4 = (3.3 * 1.7e-11) * fsh * fdust;
+  const double s2 = sqrt_nr(t2);
+  const double d1 = ((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2), u2 = u * u;
+  const double rd = rcp_nr(d1 * u2);  // 1 / (d1 u^2): d1, u^2 >= 1
+  const double k1p = (3e-17 * s2) * (u2 * rd);
+  // k4 = 3.3 1.7e-11 f_sh f_dust with f_sh = 0.965 / u^2 + 0.035 exp(-8.5e-4 sqrt(1 + x)) / sqrt(1 + x)
+  const double k4 = fdust * fma(3.3 * 1.7e-11 * 0.965, d1 * rd,
+                                ((3.3 * 1.7e-11 * 0.035) * isx) * exp_tang(-8.5e-4 * sx));
   const double C = k1p * n * nH;
   const double D = (k2 * nH + k3 * nH2) + k4;
   const double ts = tau * T0;

@@ -207,6 +207,7 @@ int main() {
     ph.taud = 1e-21;
     ph.ibdop = 1.0 / ph.bdop;
     ph.ixnorm = 1.0 / ph.xnorm;
+    set_shielding(ph);
     ph.heatcool = 1;
     const long n = 300000;
     long bad = 0;
