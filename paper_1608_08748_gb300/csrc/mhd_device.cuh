@@ -491,17 +491,25 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
       qL = qLp;
       qR = qRp;
     } else if (gt_nn(num_s, ad20)) {
-      // eta by the Newton-Raphson reciprocal in FP64 (den is nonzero here)
-      T eta;
-      if constexpr (sizeof(T) == 8)
-        eta = num * rcp_nr(T(3) * s0);
-      else
-        eta = num / (T(3) * s0);
-      T hb = T(20) * (eta - T(0.05));
-      hb = hb < T(1) ? hb : T(1);
-      if (hb > T(0)) {
-        qL = hb * qLp + (T(1) - hb) * qL;
-        qR = hb * qRp + (T(1) - hb) * qR;
+      if constexpr (sizeof(T) == 8) {
+        // hbar = 20 (eta - 1/20) = 20 num / (3 s0) - 1 by the Newton-Raphson reciprocal (den is
+        // nonzero here).  hbar lies in (0, 1] here up to rounding: the clamp and the test compare
+        // on the integer pipe (a negative hbar orders below both 1 and 0), and the blend
+        // hbar q' + (1 - hbar) q is taken as q + hbar (q' - q)
+        T hb = fma(T(20) * num, rcp_nr(T(3) * s0), T(-1));
+        hb = min_nn(hb, T(1));
+        if (gt_nn(hb, T(0))) {
+          qL = fma(hb, qLp - qL, qL);
+          qR = fma(hb, qRp - qR, qR);
+        }
+      } else {
+        const T eta = num / (T(3) * s0);
+        T hb = T(20) * (eta - T(0.05));
+        hb = hb < T(1) ? hb : T(1);
+        if (hb > T(0)) {
+          qL = hb * qLp + (T(1) - hb) * qL;
+          qR = hb * qRp + (T(1) - hb) * qR;
+        }
       }
     }
   }
