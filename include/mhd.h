@@ -180,8 +180,10 @@ enum mhd_kernel_class {
   MHD_K_EDGES = 2,       /* App. C edge EMFs */
   MHD_K_EULER_UPDATE = 3,/* finite-volume + Flux-CT + RK update */
   MHD_K_LAG_FACE = 4,    /* Lagrangian face fluxes, all three directions */
-  MHD_K_LAG_UPDATE = 5,  /* Lagrangian update */
-  MHD_K_POST = 6,        /* chemistry + regularisation + CFL of the new state */
+  MHD_K_LAG_UPDATE = 5,  /* Lagrangian update (first and second substages in a step) */
+  MHD_K_POST = 6,        /* the third substage's Lagrangian update with the chemistry, regularisation
+                            and CFL of the new state (one kernel in a step; the post stage alone for
+                            mhd_stage and after a load) */
   MHD_K_SMALL = 7,       /* single-thread bookkeeping kernels (step begin and end) */
   MHD_K_NCLASSES = 8
 };
@@ -191,7 +193,8 @@ enum mhd_kernel_class {
    number of launches.  The steps advance the state like mhd_step.  Arrays have MHD_K_NCLASSES
    entries. */
 int mhd_profile(mhd_sim* s, double cfl, int steps, double* out_ms, int64_t* out_launches);
-/* Number of kernel launches (not counting the copies of the RK register) in one mhd_step. */
+/* Number of kernel launches in one mhd_step (the first update of each stage stores its RK register,
+   so no copy kernels). */
 int mhd_launches_per_step(mhd_sim* s);
 
 /* ---- Batched execution (many boxes, one launch per kernel class) ------------------------------
