@@ -10,7 +10,10 @@ root), built from tests/gpu_selftest/screen_selftest.cu:
   stays below an FP64 denominator already reached; with the estimate this close, no skipped cell
   can hold the maximum, so tau equals that of evaluating every cell.  Flushed subnormal squares,
   densities and internal energies over many decades, zero components and unphysical abundances
-  are among the inputs."""
+  are among the inputs;
+- end to end, tau of steps whose maximum is held by one cell and falls fast equal to the oracle's
+  (FP64 within 1e-11, FP32 within 1e-4), and a batch holding that box stepping as its boxes do
+  alone."""
 import numpy as np
 import pytest
 
@@ -121,3 +124,75 @@ def test_cfl_screen_estimate_within_64u(S):
     assert np.all(np.isfinite(exact[screened]) & (exact[screened] > 0))
     rel = np.abs(est[screened] - exact[screened]) / exact[screened]
     assert rel.max() <= 64 * U, rel.max()
+
+
+# ------------------------------------------------------------------------------------------------
+# The screened maximum end to end (Sec. 2.3), where one cell holds it and it falls fast.  A
+# low-density cell at the background's pressure and velocity sets the maximum (its sound speed is
+# 10 times the background's) and fills with denser fluid within a few steps: the oracle's tau grows
+# by 1.79, 1.41, 1.25 and 1.17 over the first four steps.  One warp holds the maximum, every other
+# warp's estimates lie far below it, and the box's running maximum starts from zero each step.
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1608_08748_gb300 import build as B
+    B.build()
+    import paper_1608_08748_gb300 as M
+    return M
+
+
+def _low_density_cell(n=16, v=3.0, rlow=0.01):
+    from paper_1608_08748_gb300 import inputs as I
+    B = (0.5, 0.3, 0.2)
+    ic = I.uniform(n, n, n, rho=1.0, p=1.0, v=(v, 0.0, 0.0), B=B, dx=1.0 / n)
+    g = ic["gamma"]
+    k = (n // 2, n // 2, n // 2)
+    ic["rho"][k] = rlow
+    ic["mom"][0][k] = rlow * v
+    ic["E"][k] = 1.0 / (g - 1.0) + 0.5 * rlow * v * v + 0.5 * sum(b * b for b in B)
+    return ic
+
+
+def test_cfl_maximum_held_by_one_falling_cell(M, oracle_mod):
+    from test_gpu_parity import compare
+    ic = _low_density_cell()
+    o = oracle_mod.run(ic)
+    g = M.from_ic(ic)
+    taus = []
+    for _ in range(5):
+        dg, do = g.step(0.4), o.step(0.4)
+        assert abs(dg - do) <= 1e-11 * do, (dg, do)
+        taus.append(do)
+    assert all(taus[i + 1] / taus[i] > 8.0 / 7.0 for i in range(3)), taus
+    compare(g.get_state(), o.get_state())
+
+
+def test_cfl_maximum_of_one_cell_fp32_and_batched(M, oracle_mod):
+    ic = _low_density_cell()
+    o = oracle_mod.run(ic)
+    g32 = M.from_ic(ic, precision=1)
+    for _ in range(5):
+        dg, do = g32.step(0.4), o.step(0.4)
+        assert abs(dg - do) <= 1e-4 * do, (dg, do)
+    # per-box maxima in a batch: the box with the falling maximum beside a uniform box, both as they
+    # step alone
+    from paper_1608_08748_gb300 import inputs as I
+    from paper_1608_08748_gb300.mhd import Batch
+    ics = [ic, I.uniform(12, 10, 8, rho=1.0, p=2.0, v=(0.5, 0.1, 0.0), B=(0.2, 0.0, 0.1), dx=1.0 / 12)]
+    solo = [M.from_ic(x) for x in ics]
+    for s in solo:
+        for _ in range(5):
+            s.step(0.4)
+    sims = [M.from_ic(x) for x in ics]
+    b = Batch(sims)
+    for _ in range(5):
+        b.step(0.4)
+    b.sync()
+    for a, s in zip(sims, solo):
+        sa, ss = a.get_state(), s.get_state()
+        for k in ("rho", "mom", "E", "B"):
+            assert np.array_equal(sa[k], ss[k]), k
+        assert a.diagnostics()["t"] == s.diagnostics()["t"]
