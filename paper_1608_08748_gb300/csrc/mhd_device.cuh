@@ -406,7 +406,6 @@ __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
 // of the last rounding); it takes 11 FP64-pipe instructions.  Arguments outside
 // [-707, 707] (where 2^m or the result leaves the normal range), infinities and NaNs take the
 // library exp; the range test runs on the integer pipe.
-
 __device__ __forceinline__ double exp_tang(double x) {
   if (!exp_fast_range(x)) return exp(x);
   const double INV_L = 0x1.71547652b82fep+5;                 // 32 / ln 2
