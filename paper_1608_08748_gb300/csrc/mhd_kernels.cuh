@@ -735,24 +735,33 @@ __device__ __forceinline__ void lag_update_cell(const Box<T>& B, idx_t c, int r)
     return acc;
   };
   if constexpr (update_loads_first<T>()) {
-    T acc[NV], qv[NV], q0v[NV];
+    // the fields in two halves, each with its loads before its stores: all seven at once spilled at
+    // the 64 registers the compiler chose (1.34 against 1.25 ms per 256^3 step)
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      acc[v] = qv[v] = q0v[v] = T(0);
-      if (v < nv) {
-        acc[v] = sum_of(v);
-        qv[v] = qq[v][c];
-        if (r) q0v[v] = q0[v][c];
+    for (int h = 0; h < 2; ++h) {
+      constexpr int H = (NV + 1) / 2;
+      T acc[H], qv[H], q0v[H];
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        const int v = h * H + i;
+        acc[i] = qv[i] = q0v[i] = T(0);
+        if (v < NV && v < nv) {
+          acc[i] = sum_of(v);
+          qv[i] = qq[v][c];
+          if (r) q0v[i] = q0[v][c];
+        }
       }
-    }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      if (v < nv) {
-        if (r == 0) q0[v][c] = qv[v];
-        qq[v][c] = rk_value(qv[v], q0v[v], a, bb, gth * acc[v], r);
+      for (int i = 0; i < H; ++i) {
+        const int v = h * H + i;
+        if (v < NV && v < nv) {
+          if (r == 0) q0[v][c] = qv[i];
+          qq[v][c] = rk_value(qv[i], q0v[i], a, bb, gth * acc[i], r);
+        }
       }
     }
   } else {
+
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       if (v >= nv) break;

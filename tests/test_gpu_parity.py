@@ -84,6 +84,34 @@ def test_single_stage(M, oracle_mod, stage):
     compare(g.get_state(), o.get_state(), tol=1e-13)
 
 
+# non-default App. D shielding parameters, set through mhd_set_option after the sim is created (the
+# device takes the shielding length's products with the dust opacity and 1/x_norm from the host)
+SHIELDING = {"chem_lshield": 0.3, "chem_taud": 5e-22, "chem_xnorm": 1e14, "chem_bdop": 2.0}
+
+
+def test_chemistry_with_shielding_options(M, oracle_mod):
+    ic = I.turbulence(12, mach=4.0, seed=3, shape=(10, 11, 13))
+    g = M.from_ic(ic, **SHIELDING)
+    o = oracle_mod.run(ic, **SHIELDING)
+    for _ in range(2):
+        g.step(0.4)
+        o.step(0.4)
+    tau = o.tau(0.4)
+    g.stage(3, tau)
+    o.stage(3, tau)
+    compare(g.get_state(), o.get_state(), tol=1e-13)
+    for _ in range(3):
+        dg, do = g.step(0.4), o.step(0.4)
+        assert abs(dg - do) <= 1e-11 * do, (dg, do)
+    compare(g.get_state(), o.get_state())
+    g32 = M.from_ic(ic, precision=1, **SHIELDING)
+    o2 = oracle_mod.run(ic, **SHIELDING)
+    for _ in range(3):
+        g32.step(0.4)
+        o2.step(0.4)
+    compare(g32.get_state(), o2.get_state(), tol=1e-4)
+
+
 def test_uniform_state(M, oracle_mod):
     ic = I.uniform(9, 7, 5, rho=1.3, p=0.7, v=(0.3, -0.2, 0.1), B=(0.5, 0.4, -0.3), dx=0.1)
     g, o = run_pair(M, oracle_mod, ic, steps=3)
