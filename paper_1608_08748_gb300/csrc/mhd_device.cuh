@@ -859,8 +859,8 @@ inline void set_shielding(Phys& ph) {
 // The App. D formulas in FP64 with few FP64 instructions (the rates agree with a term-by-term
 // evaluation to about 1e-14 relative):
 //   T = (gamma - 1) rho eps P0 / (n_particles k_B) with gamma - 1 = 2 n_particles / (3 n_1 + 5 n_H2)
-//     = (2 P0 / k_B) rho eps / (3 n_1 + 5 n_H2), n_1 = n_H + n_H+ + n_e, and T, 1/T from one
-//     reciprocal of the product;
+//     = (2 P0 / k_B) rho eps / (3 n_1 + 5 n_H2), n_1 = n_H + n_H+ + n_e, and T, 1/T and sqrt(T)
+//     from one reciprocal square root of the product;
 //   1/sqrt(1 + x) from one reciprocal square root; 1/x_norm, 1/b_doppler and the products with the
 //   shielding length precomputed; one reciprocal for k1' and 1/u^2 (of their denominators' product);
 //   the exponentials of the H/H2 rates by exp_tang (their arguments are <= 0); the arguments of
@@ -916,10 +916,12 @@ __device__ __forceinline__ ChemOut chem_cell(const Phys& ph, double rho, double 
   const double num = (2.0 * P0 / ChemConst::KB) * eint;
   double den3 = fma(3.0, nH, 5.0 * nH2);  // 3 n_1 + 5 n_H2 with n_1 = n_H + n_H+ + n_e
   if (IONS) den3 = fma(6.0, rhp, den3);
-  const double r = rcp_nr(num * den3);
-  const double T = (num * num) * r, iT = (den3 * den3) * r;
+  // T = num / den3 and its square root from one reciprocal square root q = 1 / sqrt(num den3):
+  // sqrt(T) = num q, T = (num q)^2, 1/T = (den3 q)^2
+  const double q = rsqrt_nr(num * den3);
+  const double sT = num * q, dq = den3 * q;
+  const double T = sT * sT, iT = dq * dq;
   // App. D rates; the branch tests and clamps compare on the integer pipe (T >= 0; a2, a3 < 0)
-  const double t2 = T * 0.01;
   const bool hot2 = gt_nn(T, 7390.0), hot3 = gt_nn(T, 7291.0);
   // reactions 2 and 3: exp of an argument below -746 is exactly 0 in double, and the cold branches'
   // arguments -(6750 / T)^2 and -4060 / T - (7500 / T)^2 lie below -746.6 for T <= 247 and below
@@ -939,10 +941,10 @@ __device__ __forceinline__ ChemOut chem_cell(const Phys& ph, double rho, double 
   const double u = 1.0 + x * ph.ibdop;
   const double isx = rsqrt_nr(1.0 + x);
   const double sx = (1.0 + x) * isx;
-  const double s2 = sqrt_nr(t2);
-  const double d1 = ((1.0 + 0.4 * s2) + 0.2 * t2) + 0.08 * (t2 * t2), u2 = u * u;
+  // k1' = 3e-17 s / (1 + 0.4 s + 0.2 t + 0.08 t^2) with t = T / 100, s = sqrt(t) = sqrt(T) / 10
+  const double d1 = fma(fma(0.08 * 1e-4, T, 0.2 * 1e-2), T, fma(0.4 * 0.1, sT, 1.0)), u2 = u * u;
   const double rd = rcp_nr(d1 * u2);  // 1 / (d1 u^2): d1, u^2 >= 1
-  const double k1p = (3e-17 * s2) * (u2 * rd);
+  const double k1p = (3e-17 * 0.1 * sT) * (u2 * rd);
   // k4 = 3.3 1.7e-11 f_sh f_dust with f_sh = 0.965 / u^2 + 0.035 exp(-8.5e-4 sqrt(1 + x)) / sqrt(1 + x)
   const double k4 = fdust * fma(3.3 * 1.7e-11 * 0.965, d1 * rd,
                                 ((3.3 * 1.7e-11 * 0.035) * isx) * exp_tang(-8.5e-4 * sx));
