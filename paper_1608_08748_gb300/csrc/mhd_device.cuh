@@ -387,7 +387,9 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return fma(y, e * fma(0.375, e, 0.5), y);
 }
 __device__ __forceinline__ double sqrt_nr(double x) {
-  return x >= 2.2250738585072014e-308 ? x * rsqrt_nr(x) : sqrt(x);
+  // the range test on the integer pipe (x >= 0 or NaN here; -0 and negative x take the library)
+  if (__builtin_expect(!gt_nn(2.2250738585072014e-308, x), 1)) return x * rsqrt_nr(x);
+  return sqrt(x);
 }
 // bulk-type forms: FP64 by the steps above; FP32 by the plain operations (the FP32 build already
 // takes the hardware-approximate division and square root)
