@@ -735,8 +735,9 @@ __device__ __forceinline__ void lag_update_cell(const Box<T>& B, idx_t c, int r)
     return acc;
   };
   if constexpr (update_loads_first<T>()) {
-    // the fields in two halves, each with its loads before its stores: all seven at once spilled at
-    // the 64 registers the compiler chose (1.34 against 1.25 ms per 256^3 step)
+    // the fields in two halves, each with its loads before its stores: all seven at once kept 21
+    // values and the flux sums live at the 64 registers the compiler chose, and measured slower
+    // (1.34 against 1.25 ms per 256^3 step)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       constexpr int H = (NV + 1) / 2;
