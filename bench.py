@@ -50,15 +50,15 @@ HBM_FALLBACK_GBS = 6800.0
 # domain-of-dependence averages with L q and R s 244) and the fluxes (25)
 FLOPS_PER_EULER_FACE = 577
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one Eulerian face launch at 128^3,
-# the mean of the x, y and z launches of one ncu capture of this kernel (357.7, 256.4, 260.5 MB;
+# the mean of the x, y and z launches of one ncu capture of this kernel (358.1, 256.2, 260.9 MB;
 # profiles/kb_metrics_turbulence_128_fp64.md; set to None whenever the kernel changes)
-EULER_FACE_TRAFFIC_BYTES = 291.5e6
+EULER_FACE_TRAFFIC_BYTES = 291.7e6
 # FP32 bulk: FP32 flops of one Eulerian face (fadd + fmul + 2 ffma executed per face, 830-832 in
 # the three directions of one ncu capture of kb_euler_pencil<float> at 128^3) and the DRAM bytes of
-# one 256^3 launch: the mean of the 128^3 capture's x, y, z launches (172.6, 107.8, 112.4 MB) times
+# one 256^3 launch: the mean of the 128^3 capture's x, y, z launches (172.6, 107.6, 112.3 MB) times
 # 8, the ratio of the faces processed (profiles/kb_metrics_turbulence_128_fp32bulk.md)
 FP32_FLOPS_PER_EULER_FACE = 830
-EULER_FACE_TRAFFIC_BYTES_FP32 = 130.9e6 * 8
+EULER_FACE_TRAFFIC_BYTES_FP32 = 130.8e6 * 8
 
 
 def hbm_peak():
