@@ -143,65 +143,58 @@ struct Para {
   T L, R, d, q6;
 };
 
+// The limited slope of Sec. 2.1 Step 1 (the FP32 Eulerian pencils).  Selects, not branches, and
+// fmin for the minima (the operands are never NaN): the FP32 pencils are bound by instruction issue.
 template <typename T>
 __device__ __forceinline__ T slope_m(T qm, T q0, T qp) {
   T dq = T(0.5) * (qp - qm);
   T dp = qp - q0, dn = q0 - qm;
-  if (dp * dn > T(0)) {
-    T a = fabs(dq), b = T(2) * fabs(dp), c = T(2) * fabs(dn);
-    T mn = a < b ? a : b;
-    mn = mn < c ? mn : c;
-    return copysign(mn, dq);
-  }
-  return T(0);
+  const T mn = fmin(fmin(fabs(dq), T(2) * fabs(dp)), T(2) * fabs(dn));
+  return dp * dn > T(0) ? copysign(mn, dq) : T(0);
 }
 
-// Steps 1-5 from q_{i-2} .. q_{i+2} evaluated as written: the FP32 Eulerian pencils take this form
-// (their bound is instruction issue, and this one has the fewest branches there); ppm_lean below
-// serves the other parabolas.
+// Steps 1-5 for cell i, evaluated as written, from q_{i-1}, q_i, q_{i+1}, the slopes of cells i - 1,
+// i, i + 1 and the second differences D+ = q_{i+2} - 2 q_{i+1} + q_i, D- = q_i - 2 q_{i-1} + q_{i-2}:
+// the FP32 Eulerian pencils take this form, carrying each slope to the next two cells (their bound
+// is instruction issue, and the form has no branches: the tests of Steps 2 and 4 are selects, the
+// division of eta is taken where it is not used, and the blend is q + hbar (q' - q)); ppm_lean
+// below serves the other parabolas.
 template <typename T>
-__device__ __forceinline__ Para<T> ppm_direct(T qm2, T qm1, T qc, T qp1, T qp2) {
+__device__ __forceinline__ Para<T> ppm_carried(T qm1, T qc, T qp1, T dmm, T dm0, T dmp, T Dp, T Dm) {
   const T SIXTH = T(1.0 / 6.0);
-  T dmm = slope_m(qm2, qm1, qc);
-  T dm0 = slope_m(qm1, qc, qp1);
-  T dmp = slope_m(qc, qp1, qp2);
   T qL = T(0.5) * (qm1 + qc) - (dm0 - dmm) * SIXTH;
   T qR = T(0.5) * (qc + qp1) - (dmp - dm0) * SIXTH;
   T dq = qR - qL;
   T q6 = T(6) * (qc - T(0.5) * (qL + qR));
-  if ((qL - qc) * (qc - qR) <= T(0)) {
-    qL = qc;
-    qR = qc;
-  } else if (dq * q6 > dq * dq) {
-    qL = T(3) * qc - T(2) * qR;
-  } else if (dq * q6 < -(dq * dq)) {
-    qR = T(3) * qc - T(2) * qL;
+  {
+    const bool ext = (qL - qc) * (qc - qR) <= T(0);
+    const bool up = dq * q6 > dq * dq, dn = dq * q6 < -(dq * dq);
+    const T cL = T(3) * qc - T(2) * qR, cR = T(3) * qc - T(2) * qL;
+    const T nL = ext ? qc : (up ? cL : qL);
+    qR = ext ? qc : (!up && dn ? cR : qR);
+    qL = nL;
   }
   T qLp = qc - T(0.25) * dm0, qRp = qc + T(0.25) * dm0;
-  T Dp = qp2 - T(2) * qp1 + qc;
-  T Dm = qc - T(2) * qm1 + qm2;
   T dq2 = qp1 - qm1;
-  T ap = fabs(qp1), am = fabs(qm1);
-  T mn = ap < am ? ap : am;
-  T sum = ap + am;
-  mn = mn < sum ? mn : sum;
-  T hb = T(0);
-  if (!(fabs(dq2) - T(0.01) * mn <= T(0) || Dp * Dm > T(0))) {
-    T eta = -(Dp - Dm) / (T(3) * dq2);
-    hb = T(20) * (eta - T(0.05));
-  } else {
-    hb = T(20) * (T(0) - T(0.05));
-  }
-  hb = hb < T(1) ? hb : T(1);
-  hb = hb > T(0) ? hb : T(0);
-  qL = hb * qLp + (T(1) - hb) * qL;
-  qR = hb * qRp + (T(1) - hb) * qR;
+  // min(|q_{i+1}|, |q_{i-1}|, |q_{i+1}| + |q_{i-1}|) is the smaller of the first two
+  const T mn = fmin(fabs(qp1), fabs(qm1));
+  const bool det = !(fabs(dq2) - T(0.01) * mn <= T(0) || Dp * Dm > T(0));
+  const T eta = (Dm - Dp) / (T(3) * dq2);  // discarded where det is false (dq2 may be 0 there)
+  const T hb = det ? fmax(fmin(T(20) * (eta - T(0.05)), T(1)), T(0)) : T(0);
+  qL = fma(hb, qLp - qL, qL);
+  qR = fma(hb, qRp - qR, qR);
   Para<T> P;
   P.L = qL;
   P.R = qR;
   P.d = qR - qL;
   P.q6 = T(6) * (qc - T(0.5) * (qL + qR));
   return P;
+}
+// the same parabola from q_{i-2} .. q_{i+2}
+template <typename T>
+__device__ __forceinline__ Para<T> ppm_direct(T qm2, T qm1, T qc, T qp1, T qp2) {
+  return ppm_carried(qm1, qc, qp1, slope_m(qm2, qm1, qc), slope_m(qm1, qc, qp1), slope_m(qc, qp1, qp2),
+                     qp2 - T(2) * qp1 + qc, qc - T(2) * qm1 + qm2);
 }
 
 // 2^(j/32) for j = 0 .. 31, correctly rounded (the table of the exponential exp_tang below)
@@ -254,7 +247,7 @@ __device__ __forceinline__ double min_nn(double a, double b) {
       "setp.lt.s64 p, ia, ib;\n\tselp.b64 %0, %1, %2, p;\n\t}" : "=d"(r) : "d"(a), "d"(b));
   return r;
 }
-__device__ __forceinline__ float min_nn(float a, float b) { return a < b ? a : b; }
+__device__ __forceinline__ float min_nn(float a, float b) { return fminf(a, b); }  // one FMNMX
 // the larger of a, b >= 0
 __device__ __forceinline__ double max_nn(double a, double b) {
   double r;
@@ -477,7 +470,15 @@ __device__ __forceinline__ Para<T> ppm_limit(T qL, T qR, T qc, T h0, T Dp, T Dm,
   }
   // Step 4: discontinuity detector
   const T mn = min_nn(abs_b(qp1), abs_b(qm1));
-  if (gt_nn(abs_b(s0), T(0.01) * mn) && !same_sign(Dp, Dm)) {
+  if constexpr (sizeof(T) == 4) {
+    // FP32 (bound by instruction issue): selects, not branches; eta is divided out everywhere and
+    // discarded where the detector is off (s0 may be 0 there), and the blend is q + hbar (q' - q)
+    const bool det = gt_nn(abs_b(s0), T(0.01) * mn) && !same_sign(Dp, Dm);
+    const T eta = (Dm - Dp) / (T(3) * s0);
+    const T hb = det ? fmaxf(fminf(T(20) * (eta - T(0.05)), T(1)), T(0)) : T(0);
+    qL = fma(hb, (qc - T(0.5) * h0) - qL, qL);
+    qR = fma(hb, (qc + T(0.5) * h0) - qR, qR);
+  } else if (gt_nn(abs_b(s0), T(0.01) * mn) && !same_sign(Dp, Dm)) {
     // eta = num / den with den = 3 s0 != 0 here; num_s = num sgn(den)
     const T num = Dm - Dp;
     const T num_s = sign_bit_b(s0) ? neg_b(num) : num;
@@ -665,14 +666,13 @@ __device__ __forceinline__ void riemann(const T wl[6], const T wr[6], T Bn, cons
     dcs = xpos ? big : other;
     dfc = xpos ? other : big;
   } else {
-    if (X >= T(0)) {
-      dcs = T(0.5) * ((X + sq) - bp2r);
-      if (dcs < T(0)) dcs = T(0);
-      dfc = dcs > T(0) ? c2 * bp2r / dcs : T(0);
-    } else {
-      dfc = T(0.5) * ((bp2r - X) + sq);
-      dcs = dfc > T(0) ? c2 * bp2r / dfc : T(0);
-    }
+    // the same selects in FP32, where they save the branch
+    const bool xpos = X >= T(0);
+    T big = T(0.5) * ((fabs(X) + sq) - (xpos ? bp2r : -bp2r));
+    big = fmax(big, T(0));
+    const T other = big > T(0) ? c2 * bp2r / big : T(0);
+    dcs = xpos ? big : other;
+    dfc = xpos ? other : big;
   }
   const T cf2 = c2 + dfc;
   const T rc = rsqrt_t(c2), rcf = rsqrt_t(cf2);

@@ -213,9 +213,11 @@ __device__ __forceinline__ void store_face_fluxes(const FaceOut<T>& fo, idx_t f,
 // The FP32 Eulerian pencil: the five-cell stencil of each of the six primitives slides along the
 // pencil in registers (register moves; the loop over the faces stays rolled, since eight unrolled
 // copies of the Riemann solve overflow the instruction cache), and the left cell's density, gamma
-// and sqrt(rho) are carried from the previous face: ten loads per face instead of forty-three.  Where all cells f0 - 3 .. f1 + 1 of the pencil lie
-// inside the grid they are addressed as base + i * stride without the boundary map.  Each value is
-// the same as the five-point form's (the same ppm_direct of the same five numbers).
+// and sqrt(rho) are carried from the previous face: ten loads per face instead of forty-three.
+// Each cell's limited slope is formed once and carried to the parabolas of the next two cells
+// (ppm_carried; the same operations on the same numbers as the five-point ppm_direct).  Where all
+// cells f0 - 3 .. f1 + 1 of the pencil lie inside the grid they are addressed as base + i * stride
+// without the boundary map.
 template <typename T, int D>
 __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
   constexpr int D1 = (D + 1) % 3, D2 = (D + 2) % 3;
@@ -252,8 +254,13 @@ __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
     for (int v = 0; v < 6; ++v) w[v][o] = qv[v][q];
   }
   Para<T> pl[6], pr[6];
+  T sa[6], sb[6];  // the slopes of cells i - 1 and i, carried to the parabola of cell i
 #pragma unroll
-  for (int v = 0; v < 6; ++v) pl[v] = ppm_direct(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4]);  // cell f0 - 1
+  for (int v = 0; v < 6; ++v) {
+    pl[v] = ppm_direct(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4]);  // cell f0 - 1
+    sa[v] = slope_m(w[v][1], w[v][2], w[v][3]);
+    sb[v] = slope_m(w[v][2], w[v][3], w[v][4]);
+  }
   T rl, gl, sl;  // density, gamma and sqrt(rho) of the face's left cell
   {
     const idx_t q = cell_at(f0 - 1);
@@ -299,7 +306,13 @@ __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
         nb = B.s.b[D][cr];
       }
 #pragma unroll
-      for (int v = 0; v < 6; ++v) pr[v] = ppm_direct(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4]);  // cell i
+      for (int v = 0; v < 6; ++v) {  // cell i
+        const T sc = slope_m(w[v][2], w[v][3], w[v][4]);
+        pr[v] = ppm_carried(w[v][1], w[v][2], w[v][3], sa[v], sb[v], sc, w[v][4] - T(2) * w[v][3] + w[v][2],
+                            w[v][2] - T(2) * w[v][1] + w[v][0]);
+        sa[v] = sb[v];
+        sb[v] = sc;
+      }
       const T wl[6] = {rl, pL, gl, b1L, b2L, sl};
       const T wr[6] = {rr, w[5][2], gr, w[3][2], w[4][2], sr};
       T qs[6];
