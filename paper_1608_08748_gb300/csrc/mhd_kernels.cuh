@@ -319,7 +319,11 @@ __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
       riemann(wl, wr, Bn, pl, pr, tau_h, qs);
       store_face_fluxes(B.fo[D], MHD_LATTICE(g, fbase + k * fstride), Bn, qs);
 #pragma unroll
-      for (int v = 0; v < 6; ++v) pl[v] = pr[v];
+      for (int v = 0; v < 6; ++v) {
+        pl[v].R = pr[v].L + pr[v].d;  // q^R of cell i again, so that it need not live across the solve
+        pl[v].d = pr[v].d;
+        pl[v].q6 = pr[v].q6;
+      }
       rl = rr;
       gl = gr;
       sl = sr;
