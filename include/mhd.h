@@ -78,7 +78,7 @@ enum mhd_option {
                                 the Eulerian stage adds -rho grad Phi and -rho v . grad Phi (central
                                 differences).  Such a sim steps without graph capture and cannot
                                 join a batch. */
-  MHD_OPT_IONS = 17          /* 0 off (default); 1 reactions 5-8 of Sec. 4.3 / App. D with H+ and
+  MHD_OPT_IONS = 17,         /* 0 off (default); 1 reactions 5-8 of Sec. 4.3 / App. D with H+ and
                                 electrons (needs MHD_OPT_CHEM = 1): one more advected density
                                 rho_H+ = n_H+ (code density units; n_e = n_H+, neutral
                                 n_H = rho - rho_H2 - rho_H+), gamma_eff counting H, H+ and e as
@@ -88,6 +88,13 @@ enum mhd_option {
                                 first.  With MHD_OPT_HEATCOOL, Gamma_5 - Lambda_6 - Lambda_7 -
                                 Lambda_8 join the heating/cooling.  mhd_set_state zeroes rho_H+;
                                 mhd_set_ions loads it. */
+  MHD_OPT_X_STAGE = 18       /* 0 (default): the FP32-bulk x sweep reads its pencils' cells from
+                                global memory; 1: it brings the six window primitives of its rows
+                                into shared memory by bulk asynchronous copies where every box's
+                                nx is a multiple of 4 (the results are the same bit for bit; on
+                                GB300 this measured slower, since the shared memory takes L1
+                                capacity from the sweep's other, strided loads).  A batch stages
+                                only if all its members ask for it. */
 };
 
 enum mhd_dtype { MHD_F64 = 0, MHD_F32 = 1 };
@@ -115,7 +122,9 @@ typedef struct mhd_diag {
   double tau_next;      /* tau / CFL of the current state: dx / max denominator (Sec. 2.3) */
   int64_t steps;        /* steps taken since the last set_state */
   int64_t vel_branch;   /* cells that took the velocity branch of the regularisation, cumulative */
-  int32_t error_flags;  /* bit 0: non-physical state seen by the last step's checks */
+  int32_t error_flags;  /* bit 0: non-physical state seen by the last step's checks; bit 1: tau <= 0;
+                           bit 2: a bulk copy of the FP32 x sweep's rows into shared memory did not
+                           complete within its bounded wait (the kernel left the step; MHD_ECUDA) */
 } mhd_diag;
 
 typedef struct mhd_sim mhd_sim;
@@ -156,7 +165,8 @@ int mhd_get_ions(mhd_sim* s, double* rho_hp, int on_device);
    step that has finished on the device by then flagged a non-physical state; a flagged step still
    in flight surfaces at a later mhd_step or at the next synchronising call (mhd_sync,
    mhd_diagnostics, mhd_step with dt_taken).  With dt_taken != NULL it waits for the step and
-   reports MHD_ENONPHYS. */
+   reports MHD_ENONPHYS.  A bulk copy that did not complete in a step's bounded wait is reported the
+   same way, as MHD_ECUDA. */
 int mhd_step(mhd_sim* s, double cfl, double* dt_taken);
 /* Steps until t_end (the last step truncated to t_end) or max_steps. */
 int mhd_advance(mhd_sim* s, double cfl, double t_end, int max_steps, int* steps_done);

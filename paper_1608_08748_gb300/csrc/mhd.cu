@@ -100,6 +100,7 @@ int rebuild_exec(mhd_sim* S, Box<T>& B, Exec<T>& X) {
   exec_free(X);
   X.prof = &S->prof;
   cudaError_t e = exec_init(X, std::vector<Box<T>>{B});
+  X.x_stage = S->x_stage != 0;
   if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("executor set-up: ") + cudaGetErrorString(e));
   return MHD_OK;
 }
@@ -400,6 +401,10 @@ int mhd_set_option(mhd_sim* S, int key, double v) {
       if (v != 0.0 && v != 1.0) return fail(MHD_EINVAL, "ions must be 0 (off) or 1 (on)");
       S->ph.ions = (int)v;
       break;
+    case MHD_OPT_X_STAGE:
+      if (v != 0.0 && v != 1.0) return fail(MHD_EINVAL, "x staging must be 0 (off) or 1 (on)");
+      S->x_stage = (int)v;
+      break;
     default:
       return fail(MHD_EINVAL, "unknown option key " + std::to_string(key));
   }
@@ -594,6 +599,7 @@ int mhd_step(mhd_sim* S, double cfl, double* dt_taken) {
     const int hf = *(volatile int*)S->hflags_host;
     if (hf & 1) return fail(MHD_ENONPHYS, "non-physical state after an earlier step (rho, rho eps <= 0 or non-finite)");
     if (hf & 2) return fail(MHD_EINVAL, "tau <= 0 in an earlier step");
+    if (hf & 4) return fail(MHD_ECUDA, "a bulk copy into shared memory did not complete in an earlier step");
   }
   if ((rc = enqueue_step(S)) != MHD_OK) return rc;
   if (dt_taken) {
@@ -601,6 +607,7 @@ int mhd_step(mhd_sim* S, double cfl, double* dt_taken) {
     *dt_taken = S->sc_host->tau;
     if (S->sc_host->flags & 1) return fail(MHD_ENONPHYS, "non-physical state (rho, rho eps <= 0 or non-finite)");
     if (S->sc_host->flags & 2) return fail(MHD_EINVAL, "tau <= 0");
+    if (S->sc_host->flags & 4) return fail(MHD_ECUDA, "a bulk copy into shared memory did not complete");
   }
   return MHD_OK;
 }
@@ -628,6 +635,10 @@ int mhd_advance(mhd_sim* S, double cfl, double t_end, int max_steps, int* steps_
       rc = fail(MHD_EINVAL, "tau <= 0");
       break;
     }
+    if (S->sc_host->flags & 4) {
+      rc = fail(MHD_ECUDA, "a bulk copy into shared memory did not complete");
+      break;
+    }
   }
   if (steps_done) *steps_done = k;
   return rc;
@@ -638,6 +649,7 @@ int mhd_sync(mhd_sim* S) {
   int rc = read_scalars(S);
   if (rc != MHD_OK) return rc;
   if (S->sc_host->flags & 1) return fail(MHD_ENONPHYS, "non-physical state (rho, rho eps <= 0 or non-finite)");
+  if (S->sc_host->flags & 4) return fail(MHD_ECUDA, "a bulk copy into shared memory did not complete");
   return MHD_OK;
 }
 
@@ -802,6 +814,8 @@ int batch_init(mhd_batch* b) {
   X.prof = &b->prof;
   cudaError_t e = exec_init(X, boxes);
   if (e != cudaSuccess) return fail(MHD_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+  X.x_stage = !b->sims.empty();
+  for (mhd_sim* S : b->sims) X.x_stage = X.x_stage && S->x_stage != 0;
   return MHD_OK;
 }
 
@@ -1009,8 +1023,10 @@ int mhd_batch_sync(mhd_batch* b) {
   int bad = 0;
   for (mhd_sim* S : b->sims) {
     CK(cudaMemcpy(S->sc_host, S->sc, sizeof(Scalars), cudaMemcpyDeviceToHost));
-    if (S->sc_host->flags & 1) bad = 1;
+    if (S->sc_host->flags & 1) bad |= 1;
+    if (S->sc_host->flags & 4) bad |= 4;
   }
+  if (bad & 4) return fail(MHD_ECUDA, "a bulk copy into shared memory did not complete in a batch member");
   if (bad) return fail(MHD_ENONPHYS, "non-physical state in a batch member");
   return MHD_OK;
 }

@@ -115,6 +115,47 @@ __device__ __forceinline__ void decode_pencil(idx_t p, const int ext[3], int c[3
 
 #define MHD_TILE_LOOP(tl) for (int t_ = blockIdx.x; t_ < (tl).n; t_ += gridDim.x)
 
+// Bulk asynchronous copies from global into shared memory (the copy engine moves the bytes; the
+// issuing thread spends one instruction per copy) completed on an mbarrier.  Both addresses are
+// 16-byte aligned and the size a multiple of 16 bytes; every wait on the barrier is bounded.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// the one arrival of a phase, announcing the bytes its copies will deliver
+__device__ __forceinline__ void mbar_arrive_expect(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+// waits for the phase of the given parity, for about a second at most; false if it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (unsigned it = 0; it < (1u << 26); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - t0 > 2000000000ll) break;
+  }
+  return false;
+}
+// the error flag of a bulk copy that did not complete in time (bit 2 of Scalars::flags)
+constexpr int FLAG_COPY_TIMEOUT = 4;
+
 // ------------------------------------------------------------------------------------------------
 // primitives of one cell (IONS: the kernel may see boxes with H+, whose gamma_eff counts it)
 template <typename T, bool IONS>
@@ -218,8 +259,14 @@ __device__ __forceinline__ void store_face_fluxes(const FaceOut<T>& fo, idx_t f,
 // (ppm_carried; the same operations on the same numbers as the five-point ppm_direct).  Where all
 // cells f0 - 3 .. f1 + 1 of the pencil lie inside the grid they are addressed as base + i * stride
 // without the boundary map.
-template <typename T, int D>
-__device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
+//
+// STG (the x sweep only): the six window primitives of the pencil's row are read from shared memory,
+// srow[v * fs + x] for x in [0, n_x), where the block staged them (euler_x_staged); the boundary map
+// then only wraps or clamps x within the row.
+template <typename T, int D, bool STG = false>
+__device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p, const T* srow = nullptr,
+                                                    int fs = 0) {
+  static_assert(!STG || D == 0, "rows are staged for the x sweep only");
   constexpr int D1 = (D + 1) % 3, D2 = (D + 2) % 3;
   const Geom& g = B.g;
   int ext[3] = {g.n[0], g.n[1], g.n[2]};
@@ -246,12 +293,25 @@ __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
   const idx_t fbase = fidx(g, cf[0], cf[1], cf[2]);
   const idx_t fstride = D == 0 ? 1 : (D == 1 ? (idx_t)(g.n[0] + 1) : (idx_t)(g.n[0] + 1) * (g.n[1] + 1));
   const T* qv[6] = {B.w.v[D], B.w.v[D1], B.w.v[D2], B.w.B[D1], B.w.B[D2], B.w.p};
+  // the six window primitives of cell i along the pencil
+  auto load6 = [&](int i, T out[6]) {
+    if constexpr (STG) {
+      const int x = inside ? i : wrap(i, n, g.bc[0]);
+#pragma unroll
+      for (int v = 0; v < 6; ++v) out[v] = srow[v * fs + x];
+    } else {
+      const idx_t q = cell_at(i);
+#pragma unroll
+      for (int v = 0; v < 6; ++v) out[v] = qv[v][q];
+    }
+  };
   T w[6][5];  // cells j - 2 .. j + 2 of the parabola of cell j
 #pragma unroll
   for (int o = 0; o < 5; ++o) {
-    const idx_t q = cell_at(f0 - 3 + o);
+    T col[6];
+    load6(f0 - 3 + o, col);
 #pragma unroll
-    for (int v = 0; v < 6; ++v) w[v][o] = qv[v][q];
+    for (int v = 0; v < 6; ++v) w[v][o] = col[v];
   }
   Para<T> pl[6], pr[6];
   T sa[6], sb[6];  // the slopes of cells i - 1 and i, carried to the parabola of cell i
@@ -273,9 +333,8 @@ __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
   // sqrt(rho), face field)
   T nq[6], nr, ng, ns, nb;
   {
-    const idx_t qn = cell_at(f0 + 2), cr = cell_at(f0);
-#pragma unroll
-    for (int v = 0; v < 6; ++v) nq[v] = qv[v][qn];
+    const idx_t cr = cell_at(f0);
+    load6(f0 + 2, nq);
     nr = B.s.rho[cr];
     ng = B.w.g[cr];
     ns = B.w.sr[cr];
@@ -297,9 +356,8 @@ __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p) {
       }
       const T rr = nr, gr = ng, sr = ns, Bn = nb;
       if (k + 1 < nfp) {
-        const idx_t qn = cell_at(i + 3), cr = cell_at(i + 1);
-#pragma unroll
-        for (int v = 0; v < 6; ++v) nq[v] = qv[v][qn];
+        const idx_t cr = cell_at(i + 1);
+        load6(i + 3, nq);
         nr = B.s.rho[cr];
         ng = B.w.g[cr];
         ns = B.w.sr[cr];
@@ -403,6 +461,64 @@ __device__ __forceinline__ void euler_pencil(const Box<T>& B, idx_t p) {
     fo.f[6][f] = Bt2 * Vn - Bn * Vt2;
 #pragma unroll
     for (int v = 0; v < 6; ++v) pl[v] = pr[v];
+  }
+}
+
+// The FP32 x sweep with the window primitives of its rows staged in shared memory.  A tile is
+// blockDim.x consecutive x pencils (the segments of a row fastest), so its pencils lie in rows
+// r_lo .. r_hi of the box (row r = k n_y + j, the cells r n_x .. r n_x + n_x - 1).  The six window
+// primitives of those rows are brought into shared memory by bulk copies, one per row and
+// primitive, issued by the lanes of the first warp; the threads then read their windows there
+// instead of with global loads whose lanes lie 12 cells apart (12 cache lines per warp load).  Rows
+// need n_x a multiple of 4 (16-byte rows) and the launch's dynamic shared memory to hold them
+// (16 bytes of barrier, then [primitive][row][x]): the launcher takes this kernel only where every
+// box qualifies, and a tile that does not (which the launcher rules out) is flagged, not solved.
+// The results are those of kb_euler_pencil<T, 0> bit for bit.  It is opt-in (MHD_OPT_X_STAGE): on
+// GB300 the x sweep measured slower with it (119 against 111 us per 128^3 launch), since the shared
+// memory takes L1 capacity from the sweep's other strided accesses (L1 hit rate 38 -> 16 %), and
+// staging all ten input fields as well (72 KB per block) kept the concurrent y and z sweeps' blocks
+// off the SMs.
+template <typename T>
+__global__ void __launch_bounds__(256, 2) kb_euler_x_staged(const Box<T>* __restrict__ boxes, Tiles tl) {
+  extern __shared__ __align__(16) unsigned char stream_smem_raw[];
+  T* rows = reinterpret_cast<T*>(stream_smem_raw + 16);
+  const unsigned bar = smem_u32(stream_smem_raw), rows_s = smem_u32(rows);
+  const unsigned cap = dynamic_smem_bytes();
+  if (threadIdx.x == 0 && cap >= 16) mbar_init(bar);
+  __syncthreads();
+  unsigned parity = 0;
+  MHD_TILE_LOOP(tl) {
+    const Box<T>& B = boxes[tl.box[t_]];
+    const int nx = B.g.n[0], S = pencil_segments<T>(nx);
+    const idx_t total = (idx_t)S * B.g.n[1] * B.g.n[2];
+    const idx_t p0 = tl.start[t_], p = p0 + (idx_t)threadIdx.x;
+    const idx_t pe = p0 + (idx_t)blockDim.x < total ? p0 + (idx_t)blockDim.x : total;
+    const int r_lo = p0 / S, nrows = (int)((pe - 1) / S) - r_lo + 1;
+    const unsigned bytes = (unsigned)nrows * 6u * (unsigned)nx * (unsigned)sizeof(T);
+    if (nx % 4 != 0 || 16u + bytes > cap) {  // the same for every thread of the block
+      if (threadIdx.x == 0) atomicOr(&B.sc->flags, FLAG_COPY_TIMEOUT);
+      continue;
+    }
+    __syncthreads();  // every thread is done with the previous tile's rows
+    if (threadIdx.x < 32) {
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect(bar, bytes);
+      }
+      const T* src[6] = {B.w.v[0], B.w.v[1], B.w.v[2], B.w.B[1], B.w.B[2], B.w.p};
+      for (int q = (int)threadIdx.x; q < 6 * nrows; q += 32) {
+        const int v = q / nrows, lr = q - v * nrows;
+        bulk_copy_g2s(rows_s + (unsigned)((v * nrows + lr) * nx) * (unsigned)sizeof(T),
+                      src[v] + (size_t)(r_lo + lr) * nx, (unsigned)nx * (unsigned)sizeof(T), bar);
+      }
+    }
+    const bool ok = mbar_wait_bounded(bar, parity);
+    parity ^= 1u;
+    if (__syncthreads_or(!ok)) {  // a copy did not arrive in time: flag it and leave
+      if (threadIdx.x == 0) atomicOr(&B.sc->flags, FLAG_COPY_TIMEOUT);
+      return;
+    }
+    if (p < total) euler_pencil_window<T, 0, true>(B, p, rows + (int)(p / S - r_lo) * nx, nrows * nx);
   }
 }
 

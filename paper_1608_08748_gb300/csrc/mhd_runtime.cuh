@@ -126,6 +126,7 @@ struct Exec {
   int nsm = 152;
   Profiler* prof = nullptr;
   bool ions = false;      // some box has H+ (reactions 5-8): the kernels with the ion code
+  bool x_stage = false;   // the FP32 x sweep may stage its rows in shared memory (kb_euler_x_staged)
   // The three directional sweeps of a stage are independent (each reads the cells and writes its
   // own face arrays): the y and z sweeps run on two side streams forked from and joined to the
   // launching stream, so that each sweep's tail overlaps the others' work.  In a captured step the
@@ -217,12 +218,32 @@ void default_cfgs(Exec<T>& X) {
   }
 }
 
+// The FP32 x sweep stages the window primitives of its tiles' rows in dynamic shared memory
+// (kb_euler_x_staged): 16 bytes of barrier and six primitives of at most (block - 1) / S + 2 rows
+// of n_x cells (S pencils per row).  It needs every box's n_x to be a multiple of 4 and the largest
+// box's rows to fit in kXStageMax; 0 otherwise, and the launch takes the direct kernel.
+constexpr size_t kXStageMax = 200 * 1024;
+template <typename T>
+size_t euler_x_stage_bytes(const Exec<T>& X, int block) {
+  size_t m = 0;
+  for (int b = 0; b < X.nb; ++b) {
+    const int nx = X.h[b].g.n[0];
+    if (nx % 4 != 0) return 0;
+    const size_t rows = (size_t)((block - 1) / pencil_segments<T>(nx) + 2);
+    const size_t need = 16 + rows * 6 * (size_t)nx * sizeof(T);
+    m = need > m ? need : m;
+  }
+  return m <= kXStageMax ? m : 0;
+}
+
 // Kernel attributes of the current device: dynamic shared memory above the 48 KB default for the
 // Eulerian pencils that stream their parabolas (up to 256 threads per block).  A kernel template
 // instantiated in two translation units is two kernels, so this is instantiated where the launches
 // of T are (the float launchers live in their own translation unit).
 template <typename T>
 cudaError_t prepare_kernels() {
+  if constexpr (euler_pencil_smem<T>() == 0)
+    return cudaFuncSetAttribute(kb_euler_x_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXStageMax);
   if constexpr (euler_pencil_smem<T>() > 0) {
     const int bytes = (int)(256 * euler_pencil_smem<T>());
     cudaError_t e = cudaFuncSetAttribute(kb_euler_pencil<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -295,6 +316,14 @@ void launch_ks(Exec<T>& X, cudaStream_t st, int kc, int dom, size_t smem_per_thr
   PScope p(X.prof, st, PROF_KC_BASE + kc);  // the profiler records the kernel class
   kernel<<<grid_of(t, c, X.nsm), c.block, smem_per_thread * c.block, st>>>(X.d, t, args...);
 }
+// the same with the block's dynamic shared memory given in bytes
+template <typename T, typename K, typename... A>
+void launch_kb(Exec<T>& X, cudaStream_t st, int kc, int dom, size_t bytes, K kernel, A... args) {
+  const LaunchCfg& c = X.cfg[kc];
+  Tiles t = tiles_of(X, dom, c.block);
+  PScope p(X.prof, st, PROF_KC_BASE + kc);
+  kernel<<<grid_of(t, c, X.nsm), c.block, bytes, st>>>(X.d, t, args...);
+}
 template <typename T, typename K, typename... A>
 void launch_k(Exec<T>& X, cudaStream_t st, int kc, int dom, K kernel, A... args) {
   launch_ks(X, st, kc, dom, 0, kernel, args...);
@@ -343,7 +372,16 @@ void launch_euler_stage(Exec<T>& X, cudaStream_t st) {
     else
       launch_k(X, st, KC_PRIM, DOM_CELLS, kb_prim<T, false>);
     launch_sweeps(X, st, [&](int d, cudaStream_t s) {
-      if (d == 0) launch_ks(X, s, KC_EFACE, DOM_PENCIL_X, euler_pencil_smem<T>(), kb_euler_pencil<T, 0>);
+      if (d == 0) {
+        if constexpr (!euler_streams<T>()) {
+          const size_t xs = X.x_stage ? euler_x_stage_bytes(X, X.cfg[KC_EFACE].block) : 0;
+          if (xs > 0) {
+            launch_kb(X, s, KC_EFACE, DOM_PENCIL_X, xs, kb_euler_x_staged<T>);
+            return;
+          }
+        }
+        launch_ks(X, s, KC_EFACE, DOM_PENCIL_X, euler_pencil_smem<T>(), kb_euler_pencil<T, 0>);
+      }
       if (d == 1) launch_ks(X, s, KC_EFACE, DOM_PENCIL_Y, euler_pencil_smem<T>(), kb_euler_pencil<T, 1>);
       if (d == 2) launch_ks(X, s, KC_EFACE, DOM_PENCIL_Z, euler_pencil_smem<T>(), kb_euler_pencil<T, 2>);
     });
@@ -451,6 +489,7 @@ struct mhd_sim {
   Phys ph;
   int precision = 0;
   int use_graph = 1;
+  int x_stage = 0;  // MHD_OPT_X_STAGE
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;

@@ -16,7 +16,7 @@ from . import build as _build
 
 OPT = {"bc_x": 1, "bc_y": 2, "bc_z": 3, "chem": 4, "precision": 5, "regul_mode": 7,
        "chem_lshield": 8, "chem_bdop": 9, "chem_xnorm": 10, "chem_taud": 11, "graph": 14,
-       "heatcool": 15, "grav_g": 16, "ions": 17}
+       "heatcool": 15, "grav_g": 16, "ions": 17, "x_stage": 18}
 STATUS = {0: "MHD_OK", 1: "MHD_PENDING", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA",
           -4: "MHD_ENONPHYS", -5: "MHD_ETIMEOUT", -6: "MHD_ENOTFOUND", -7: "MHD_ECAPACITY",
           -8: "MHD_ECANCELED"}
