@@ -53,12 +53,12 @@ FLOPS_PER_EULER_FACE = 577
 # the mean of the x, y and z launches of one ncu capture of this kernel (358.1, 256.2, 260.9 MB;
 # profiles/kb_metrics_turbulence_128_fp64.md; set to None whenever the kernel changes)
 EULER_FACE_TRAFFIC_BYTES = 291.7e6
-# FP32 bulk: FP32 flops of one Eulerian face (fadd + fmul + 2 ffma executed per face, 796-801 in
+# FP32 bulk: FP32 flops of one Eulerian face (fadd + fmul + 2 ffma executed per face, 795-796 in
 # the three directions of one ncu capture of kb_euler_pencil<float> at 128^3) and the DRAM bytes of
-# one 256^3 launch: the mean of the 128^3 capture's x, y, z launches (180.6, 111.2, 115.9 MB) times
+# one 256^3 launch: the mean of the 128^3 capture's x, y, z launches (175.7, 110.0, 114.0 MB) times
 # 8, the ratio of the faces processed (profiles/kb_metrics_turbulence_128_fp32bulk.md)
-FP32_FLOPS_PER_EULER_FACE = 800
-EULER_FACE_TRAFFIC_BYTES_FP32 = 135.9e6 * 8
+FP32_FLOPS_PER_EULER_FACE = 796
+EULER_FACE_TRAFFIC_BYTES_FP32 = 133.2e6 * 8
 
 
 def hbm_peak():
