@@ -512,10 +512,14 @@ __global__ void __launch_bounds__(256, 2) kb_euler_x_staged(const Box<T>* __rest
                       src[v] + (size_t)(r_lo + lr) * nx, (unsigned)nx * (unsigned)sizeof(T), bar);
       }
     }
-    const bool ok = mbar_wait_bounded(bar, parity);
+    const unsigned phase = parity;
     parity ^= 1u;
-    if (__syncthreads_or(!ok)) {  // a copy did not arrive in time: flag it and leave
+    const bool ok = mbar_wait_bounded(bar, phase);
+    if (__syncthreads_or(!ok)) {
+      // a copy did not arrive in time: flag it, give the copies in flight one more bounded wait,
+      // and leave
       if (threadIdx.x == 0) atomicOr(&B.sc->flags, FLAG_COPY_TIMEOUT);
+      mbar_wait_bounded(bar, phase);
       return;
     }
     if (p < total) euler_pencil_window<T, 0, true>(B, p, rows + (int)(p / S - r_lo) * nx, nrows * nx);
