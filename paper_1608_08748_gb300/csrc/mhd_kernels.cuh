@@ -261,7 +261,7 @@ __device__ __forceinline__ void store_face_fluxes(const FaceOut<T>& fo, idx_t f,
 // without the boundary map.
 //
 // STG (the x sweep only): the six window primitives of the pencil's row are read from shared memory,
-// srow[v * fs + x] for x in [0, n_x), where the block staged them (euler_x_staged); the boundary map
+// srow[v * fs + x] for x in [0, n_x), where the block staged them (kb_euler_x_staged); the boundary map
 // then only wraps or clamps x within the row.
 template <typename T, int D, bool STG = false>
 __device__ __forceinline__ void euler_pencil_window(const Box<T>& B, idx_t p, const T* srow = nullptr,
