@@ -115,3 +115,18 @@ def test_bulk_copy_wait_is_bounded(bulk):
     assert not out.any()
     src, out, status = _bulk(bulk, 1024, 0)  # the context still works
     assert status == 1 and np.array_equal(src, out)
+
+
+def test_x_stage_option_values(M):
+    """MHD_OPT_X_STAGE takes 0 or 1; anything else is MHD_EINVAL and leaves the sim usable."""
+    ic = I.turbulence(8, mach=1.0, beta=1.0, seed=43, shape=(8, 8, 16))
+    s = M.from_ic(ic, precision=1)
+    for bad in (2, -1, 0.5):
+        with pytest.raises(M.MHDError) as e:
+            s.set_option("x_stage", bad)
+        assert "EINVAL" in str(e.value)
+    s.set_option("x_stage", 1)
+    s.step(0.4)
+    s.set_option("x_stage", 0)
+    s.step(0.4)
+    s.close()
