@@ -99,6 +99,30 @@ int main() {
     }
     report("ppm_stream_bits", n, 0.0, bad);
   }
+  // 2b. the FP32 pencils' parabolas with each cell's slope carried to the next two cells (the order
+  // of the Eulerian window) equal the five-point ppm_direct bit for bit
+  {
+    long n = 0, bad = 0;
+    for (int line = 0; line < 5000; ++line) {
+      float q[40];
+      const int kind = line % 4;
+      for (int i = 0; i < 40; ++i)
+        q[i] = (float)(kind == 0 ? U(g) : kind == 1 ? std::sin(0.2 * i + line) :
+                       kind == 2 ? (i < 20 ? 1.0 : 0.125) + 1e-3 * U(g) : std::round(3 * U(g)) / 3);
+      float sa = slope_m(q[0], q[1], q[2]), sb = slope_m(q[1], q[2], q[3]);  // cells 1 and 2
+      for (int j = 2; j < 38; ++j) {
+        const float sc = slope_m(q[j], q[j + 1], q[j + 2]);
+        const Para<float> a = ppm_carried(q[j - 1], q[j], q[j + 1], sa, sb, sc,
+                                          q[j + 2] - 2.0f * q[j + 1] + q[j], q[j] - 2.0f * q[j - 1] + q[j - 2]);
+        const Para<float> b = ppm_direct(q[j - 2], q[j - 1], q[j], q[j + 1], q[j + 2]);
+        sa = sb;
+        sb = sc;
+        ++n;
+        if (std::memcmp(&a, &b, sizeof(a)) != 0) ++bad;
+      }
+    }
+    report("ppm_carried_bits", n, 0.0, bad);
+  }
   // 3. FP32 parabolas of the FP32-bulk path against the FP64 oracle
   {
     const long n = 200000;
